@@ -1,0 +1,60 @@
+"""Shared test helpers: running the oracle to a time, error norms, mesh utilities."""
+
+from __future__ import annotations
+
+import math
+from typing import Dict
+
+import numpy as np
+
+
+def run_to_time(o, params: Dict, T: float, max_steps: int = 100000) -> int:
+    """fill -> cfl -> step until t = T (the last step shortened to land on T)."""
+    t = 0.0
+    n = 0
+    while t < T - 1e-14 and n < max_steps:
+        o.fill_ghosts()
+        dt = float(o.cfl(params)[0])
+        if t + dt > T:
+            dt = T - t
+            o.cfl(dict(params, dt_override=dt))
+        o.step(params)
+        t += dt
+        n += 1
+    return n
+
+
+def l1(a: np.ndarray, b: np.ndarray) -> float:
+    return float(np.abs(a - b).mean())
+
+
+def per_var_rel_max(a: np.ndarray, b: np.ndarray) -> np.ndarray:
+    """max |a-b| per variable divided by max |b| of that variable (1 if b == 0 there)."""
+    nv = a.shape[1]
+    out = np.zeros(nv)
+    for v in range(nv):
+        scale = float(np.abs(b[:, v]).max())
+        out[v] = float(np.abs(a[:, v] - b[:, v]).max()) / (scale if scale > 0 else 1.0)
+    return out
+
+
+def per_var_rel_l1(a: np.ndarray, b: np.ndarray) -> np.ndarray:
+    """mean |a-b| per variable divided by mean |b| of that variable (1 if b == 0 there)."""
+    nv = a.shape[1]
+    out = np.zeros(nv)
+    for v in range(nv):
+        scale = float(np.abs(b[:, v]).mean())
+        out[v] = float(np.abs(a[:, v] - b[:, v]).mean()) / (scale if scale > 0 else 1.0)
+    return out
+
+
+def assemble_uniform(mesh, U: np.ndarray, var: int) -> np.ndarray:
+    """Single-level, single-problem mesh data of one variable as a (nz, ny, nx) array."""
+    nb = mesh.nb
+    pr = mesh.problems[0]
+    nz = pr.nbase[2] * nb if mesh.ndim == 3 else 1
+    out = np.zeros((nz, pr.nbase[1] * nb, pr.nbase[0] * nb))
+    bz = nb if mesh.ndim == 3 else 1
+    for b, (p, lv, i, j, k) in enumerate(mesh.leaves):
+        out[k * bz:(k + 1) * bz, j * nb:(j + 1) * nb, i * nb:(i + 1) * nb] = U[b, var]
+    return out
