@@ -1,0 +1,206 @@
+/*
+ * map.h -- C ABI of the GB300 EGLM-MHD block-pool step.
+ *
+ * The library advances the EGLM-MHD equations (Jiang, Fang & Chen, arXiv:1204.5849,
+ * Sec. 2, eqs. MHD-1..MHD-5) on a pool of equal-shape blocks (Sec. 4.1) on one GPU:
+ * ghost fill (Sec. 4.3), the MMC / TVD-LF / WENO-RK2 update (Sec. 3.1-3.3, Sec. 3.7),
+ * resistivity (Sec. 3.5), the GLM psi source and damping (Sec. 2), the global CFL
+ * reduction (Sec. 3.7), the refinement estimator (Sec. 4.5) and regrid.
+ *
+ * Conventions
+ *  - Every call returns a map_status (0 = MAP_OK, negative = error); no call aborts or
+ *    throws.  map_last_error() gives a one-line description of the last failure.
+ *  - A pool is not thread-safe: calls on one pool must be serialised by the caller.
+ *  - Asynchronous calls are ordered on the pool's stream (map_create_pool's stream, or
+ *    map_set_stream's).  Calls that hand results to the host synchronise that stream.
+ *  - Host arrays are caller-owned and only read or written during the call.
+ *  - Variables are always the 9 conserved quantities in this order:
+ *      rho, rho*vx, rho*vy, rho*vz, Bx, By, Bz, e, psi
+ *    (three vector components in 2D as well; psi is the GLM potential, Sec. 2).
+ *  - Block interior data crosses the ABI as FP64 [9][nz][nb][nb] (x fastest), nz = nb in
+ *    3D and 1 in 2D, whatever the pool precision.
+ */
+#ifndef MAP_GB300_H
+#define MAP_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  MAP_OK = 0,
+  MAP_EINVAL = -1,        /* bad argument, bad tree (unbalanced, overlapping, incomplete) */
+  MAP_ENOMEM = -2,        /* device or host allocation failed / capacity exceeded */
+  MAP_ECUDA = -3,         /* a CUDA runtime call failed (text in map_last_error) */
+  MAP_ENONFINITE = -4,    /* device error word: a non-finite value in a leaf cell */
+  MAP_ENEGPRES = -5,      /* device error word: rho <= 0 or p < 0 in a leaf cell */
+  MAP_ETIMEOUT = -6,      /* device error word: a bounded device wait gave up */
+  MAP_EUNSUPPORTED = -7,  /* combination not built (e.g. block size) */
+  MAP_ESTATE = -8         /* call out of order (no tree, no dt yet, ...) */
+} map_status;
+
+enum { MAP_FP64 = 0, MAP_FP32_FIX64 = 1 };   /* pool precision */
+enum { MAP_MMC = 0, MAP_LF = 1, MAP_WENO = 2 };
+enum { MAP_MINMOD = 0, MAP_VANLEER = 1 };
+enum { MAP_BC_PERIODIC = 0, MAP_BC_OUTFLOW = 1 };
+enum { MAP_CH_AUTO = 0, MAP_CH_PAPER = 1, MAP_CH_FIXED = 2 };
+enum { MAP_CP_FROM_CD = 0, MAP_CP_FIXED = 1 };
+
+/* One independent domain (problem): base tiling in blocks, physical box, boundary kind
+ * of the low/high face per dimension.  At level L the domain is tiled by nbase*2^L
+ * blocks per dimension. */
+typedef struct {
+  int nbase[3];
+  double lo[3], hi[3];
+  int bc[3][2];
+} map_problem_desc;
+
+typedef struct {
+  int ndim;           /* 2 or 3 */
+  int nb;             /* cells per block edge: 8 or 16 */
+  int n_ghost;        /* must be 2 */
+  int precision;      /* MAP_FP64 or MAP_FP32_FIX64 */
+  int max_blocks;     /* capacity: leaves + their parents over the pool's life */
+  int n_problems;
+  const map_problem_desc* problems;  /* n_problems entries, copied */
+  void* ext_buffer;   /* optional device buffer for the three state buffers (e.g. a torch
+                         tensor's data_ptr), caller-owned, 256-byte aligned, at least
+                         3 * max_blocks * 9 * (nb+4)^ndim * element size bytes; NULL =
+                         the library allocates */
+  size_t ext_bytes;
+} map_pool_desc;
+
+/* A leaf block: problem index, level and integer block coordinates at that level. */
+typedef struct {
+  int problem, level;
+  int ijk[3];
+} map_block_desc;
+
+/* Method parameters (Sec. 2, Sec. 3). */
+typedef struct {
+  double gamma;       /* adiabatic index */
+  double c_cfl;       /* CFL safety coefficient (Sec. 3.7) */
+  int ch_mode;        /* MAP_CH_AUTO: c_h = alpha_g; MAP_CH_PAPER: c_h = c_cfl min dx / dt
+                         (Sec. 2, c_h formula); MAP_CH_FIXED: c_h = ch */
+  double ch;
+  int cp_mode;        /* MAP_CP_FROM_CD: c_p = sqrt(-dt c_h^2 / ln c_d) (Sec. 2); else cp */
+  double c_d, cp;
+  double eta;         /* uniform resistivity (Sec. 3.5); 0 = ideal */
+  int eglm;           /* 1: EGLM non-conservative sources; 0: GLM */
+  int scheme;         /* MAP_MMC, MAP_LF, MAP_WENO */
+  int limiter;        /* MAP_MINMOD, MAP_VANLEER */
+  double dt_override; /* > 0: use this dt instead of the CFL dt */
+  double fp64_fix_tau;/* FP32 pools: recompute p in FP64 where e_int < tau * e */
+} map_params;
+
+/* Refinement estimator parameters (Sec. 4.5). */
+typedef struct {
+  int var_mask;       /* 1 rho, 2 p, 4 |J| dx / (|B| + eps_b) */
+  double thr;         /* refine if the block maximum exceeds thr */
+  double coarsen_thr; /* may coarsen if the block maximum is below coarsen_thr */
+  double bias;        /* B = 0.6 */
+  double filter;      /* F = 0.05 */
+  double eps_rho, eps_p, eps_b;
+  double ratio, xi;   /* R^(xi (L-1)) level factor */
+  int max_level;
+} map_refine_params;
+
+typedef struct map_pool map_pool;
+
+/* Create a pool.  stream: a cudaStream_t the library uses but does not own; NULL makes
+ * the library create (and later destroy) a non-blocking stream of its own.  The pool's
+ * three state buffers (two ping-pong states and a Runge-Kutta stage) hold max_blocks
+ * blocks each.  *out receives the pool.  Errors: MAP_EINVAL (bad desc),
+ * MAP_EUNSUPPORTED (nb/ndim not built), MAP_ENOMEM, MAP_ECUDA. */
+int map_create_pool(const map_pool_desc* d, void* stream, map_pool** out);
+
+/* Free library-owned device memory and the pool.  NULL is accepted. */
+int map_destroy_pool(map_pool* pool);
+
+/* Replace the stream used by later calls (NULL = a stream owned by the library).
+ * Synchronises the old stream first. */
+int map_set_stream(map_pool* pool, void* stream);
+
+/* Set the block tree from its leaves (Sec. 4.1).  The library adds every parent, orders
+ * blocks along the Morton curve, validates the tree (coordinates in range, no leaf inside
+ * another, every parent complete, 2:1 balance across faces, edges and corners) and builds
+ * the neighbour / ghost-fill tables on the host.  Leaf data is undefined until written.
+ * Leaf index l of later calls is the position in this array.  Errors: MAP_EINVAL,
+ * MAP_ENOMEM (more blocks than max_blocks). */
+int map_set_tree(map_pool* pool, const map_block_desc* leaves, int n);
+
+/* Copy one leaf's interior from / to the host (FP64 [9][nz][nb][nb]).  read synchronises. */
+int map_write_block(map_pool* pool, int leaf, const double* u);
+int map_read_block(map_pool* pool, int leaf, double* u_out);
+
+/* All leaves at once, in leaf order: n_leaves x [9][nz][nb][nb] FP64 host arrays.
+ * Use pinned host memory for full copy bandwidth.  read synchronises. */
+int map_write_leaves(map_pool* pool, const double* u);
+int map_read_leaves(map_pool* pool, double* u_out);
+
+/* Ghost fill (Sec. 4.3), asynchronous: parents become the mean of their children
+ * (bottom-up), then level by level from the coarsest: same-level copy from the
+ * neighbour block holding the cell (edges and corners included), periodic wrap or
+ * zero-gradient outflow at the domain boundary, conservative minmod prolongation from
+ * the coarser leaf where the neighbour level does not exist. */
+int map_fill_ghosts(map_pool* pool);
+
+/* Global CFL reduction (Sec. 3.7): alpha_g per problem (max over leaf cells and
+ * directions of |v_d| + c_f,d), dt = c_cfl min dx / (ndim alpha_g) (and the diffusive
+ * limit c_cfl dx^2 / (2 ndim eta) when eta > 0), c_h, c_p, and the psi damping factor,
+ * all kept on the device.  Copies dt to dt_out[n_problems] and synchronises.  Errors:
+ * MAP_ENONFINITE if a dt is not finite and positive. */
+int map_cfl_dt(map_pool* pool, const map_params* p, double* dt_out);
+
+/* One step (asynchronous, no host synchronisation, no allocation): the scheme update
+ * of every leaf with the device-resident dt of the last map_cfl_dt (or
+ * p->dt_override), sources, psi damping; WENO refills ghosts between its stages.  Ghosts
+ * must be filled before the call. */
+int map_step(map_pool* pool, const map_params* p);
+
+/* nsteps x (ghost fill, dt on the device, step), asynchronous: the batched form.  The
+ * step kernel also reduces alpha_g of the new state (the next dt) and the FP64
+ * conservation sums of the new state, so a separate CFL pass runs only before the first
+ * step after the state changed outside this call.  The step sequence is captured once per
+ * starting buffer into a CUDA graph and replayed.  map_get_speeds reads the last dt. */
+int map_advance(map_pool* pool, const map_params* p, int nsteps);
+
+/* Device error word accumulated by the steps since the last check (ρ <= 0, p < 0,
+ * non-finite), read and cleared; synchronises.  MAP_OK, MAP_ENONFINITE or MAP_ENEGPRES. */
+int map_check(map_pool* pool);
+
+/* Refinement flags (Sec. 4.5): per leaf +1 refine, 0 keep, -1 may coarsen, from the
+ * block maximum of the estimator over the interior and the first ghost ring.  Ghosts
+ * must be filled.  flags_out[n_leaves]; est_out[n_leaves] may be NULL.  Synchronises. */
+int map_flag_refine(map_pool* pool, const map_params* p, const map_refine_params* r,
+                    int8_t* flags_out, double* est_out);
+
+/* Replace the tree by a new leaf set (each new leaf: unchanged, a child of an old leaf,
+ * or a parent of old leaves).  Kept leaves copy, new children are prolonged from their
+ * old parent (Sec. 4.3 formula on the interior), new parents take the restriction of
+ * their old children.  Ghosts of the old tree must be filled.  Leaf indices follow the
+ * new array.  Errors: MAP_EINVAL. */
+int map_regrid(map_pool* pool, const map_block_desc* new_leaves, int n);
+
+/* FP64 conservation sums: sums_out[n_problems][9] = sum over leaf cells of U * cell
+ * volume.  Synchronises. */
+int map_conservation(map_pool* pool, double* sums_out);
+
+/* Per problem: dt, c_h, c_p, psi damping factor, alpha_g of the last CFL reduction
+ * (out[n_problems][5]).  Synchronises. */
+int map_get_speeds(map_pool* pool, double* out);
+
+/* Number of kernels the library launched since the pool was created (graph replays
+ * count each kernel in the graph). */
+long long map_kernel_launches(const map_pool* pool);
+
+/* Last error text of the pool (or of the last failed create when pool is NULL). */
+const char* map_last_error(const map_pool* pool);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

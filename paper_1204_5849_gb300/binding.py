@@ -1,0 +1,274 @@
+"""Thin ctypes binding of the C ABI in include/map.h (argument marshalling only).
+
+Every step of the method runs inside libmapgb300.so on the GPU.  There is no CPU
+fallback: if the library is missing or no CUDA device is present, calls raise.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Dict, Optional, Sequence
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libmapgb300.so")
+
+MAP_OK = 0
+STATUS = {0: "MAP_OK", -1: "MAP_EINVAL", -2: "MAP_ENOMEM", -3: "MAP_ECUDA", -4: "MAP_ENONFINITE",
+          -5: "MAP_ENEGPRES", -6: "MAP_ETIMEOUT", -7: "MAP_EUNSUPPORTED", -8: "MAP_ESTATE"}
+MAP_FP64, MAP_FP32_FIX64 = 0, 1
+SCHEMES = {"mmc": 0, "lf": 1, "weno": 2}
+LIMITERS = {"minmod": 0, "vanleer": 1}
+CH_MODES = {"auto": 0, "paper": 1, "fixed": 2}
+CP_MODES = {"cd": 0, "fixed": 1}
+REFINE_VARS = {"rho": 1, "p": 2, "j": 4}
+
+
+class map_problem_desc(C.Structure):
+    _fields_ = [("nbase", C.c_int * 3), ("lo", C.c_double * 3), ("hi", C.c_double * 3),
+                ("bc", (C.c_int * 2) * 3)]
+
+
+class map_pool_desc(C.Structure):
+    _fields_ = [("ndim", C.c_int), ("nb", C.c_int), ("n_ghost", C.c_int), ("precision", C.c_int),
+                ("max_blocks", C.c_int), ("n_problems", C.c_int),
+                ("problems", C.POINTER(map_problem_desc)), ("ext_buffer", C.c_void_p),
+                ("ext_bytes", C.c_size_t)]
+
+
+class map_block_desc(C.Structure):
+    _fields_ = [("problem", C.c_int), ("level", C.c_int), ("ijk", C.c_int * 3)]
+
+
+class map_params(C.Structure):
+    _fields_ = [("gamma", C.c_double), ("c_cfl", C.c_double), ("ch_mode", C.c_int),
+                ("ch", C.c_double), ("cp_mode", C.c_int), ("c_d", C.c_double), ("cp", C.c_double),
+                ("eta", C.c_double), ("eglm", C.c_int), ("scheme", C.c_int), ("limiter", C.c_int),
+                ("dt_override", C.c_double), ("fp64_fix_tau", C.c_double)]
+
+
+class map_refine_params(C.Structure):
+    _fields_ = [("var_mask", C.c_int), ("thr", C.c_double), ("coarsen_thr", C.c_double),
+                ("bias", C.c_double), ("filter", C.c_double), ("eps_rho", C.c_double),
+                ("eps_p", C.c_double), ("eps_b", C.c_double), ("ratio", C.c_double),
+                ("xi", C.c_double), ("max_level", C.c_int)]
+
+
+class MapError(RuntimeError):
+    def __init__(self, code: int, what: str, msg: str):
+        super().__init__(f"{what}: {STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+# name -> (restype, argtypes)
+_SIGS = {
+    "map_create_pool": (C.c_int, [C.POINTER(map_pool_desc), C.c_void_p, C.POINTER(C.c_void_p)]),
+    "map_destroy_pool": (C.c_int, [C.c_void_p]),
+    "map_set_stream": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "map_set_tree": (C.c_int, [C.c_void_p, C.POINTER(map_block_desc), C.c_int]),
+    "map_write_block": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
+    "map_read_block": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
+    "map_write_leaves": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "map_read_leaves": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "map_fill_ghosts": (C.c_int, [C.c_void_p]),
+    "map_cfl_dt": (C.c_int, [C.c_void_p, C.POINTER(map_params), C.c_void_p]),
+    "map_step": (C.c_int, [C.c_void_p, C.POINTER(map_params)]),
+    "map_advance": (C.c_int, [C.c_void_p, C.POINTER(map_params), C.c_int]),
+    "map_check": (C.c_int, [C.c_void_p]),
+    "map_flag_refine": (C.c_int, [C.c_void_p, C.POINTER(map_params), C.POINTER(map_refine_params),
+                                  C.c_void_p, C.c_void_p]),
+    "map_regrid": (C.c_int, [C.c_void_p, C.POINTER(map_block_desc), C.c_int]),
+    "map_conservation": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "map_get_speeds": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "map_kernel_launches": (C.c_longlong, [C.c_void_p]),
+    "map_last_error": (C.c_char_p, [C.c_void_p]),
+}
+
+
+def load(path: str = LIB_PATH):
+    """Load libmapgb300.so; raise if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise RuntimeError(f"{path} is missing: build it with __graft_entry__.build()")
+        L = C.CDLL(path)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def exported_symbols():
+    return list(_SIGS)
+
+
+def _ptr(a: np.ndarray):
+    return C.c_void_p(a.ctypes.data)
+
+
+def make_params(p: Dict) -> map_params:
+    return map_params(float(p.get("gamma", 5 / 3)), float(p.get("c_cfl", 0.4)),
+                      CH_MODES[p.get("ch_mode", "auto")], float(p.get("ch", 0.0)),
+                      CP_MODES[p.get("cp_mode", "cd")], float(p.get("c_d", 0.18)),
+                      float(p.get("cp", 0.0)), float(p.get("eta", 0.0)), int(p.get("eglm", 1)),
+                      SCHEMES[p.get("scheme", "mmc")], LIMITERS[p.get("limiter", "minmod")],
+                      float(p.get("dt_override", 0.0)), float(p.get("fp64_fix_tau", 1e-2)))
+
+
+def make_refine(r: Dict) -> map_refine_params:
+    mask = 0
+    for v in r.get("vars", ("rho", "p")):
+        mask |= REFINE_VARS[v]
+    return map_refine_params(mask, float(r.get("thr", 0.2)), float(r.get("coarsen", 0.1)),
+                             float(r.get("bias", 0.6)), float(r.get("filter", 0.05)),
+                             float(r.get("eps_rho", 1e-12)), float(r.get("eps_p", 1e-12)),
+                             float(r.get("eps_b", 0.1)), float(r.get("ratio", 2.0)),
+                             float(r.get("xi", 0.0)), int(r.get("max_level", 30)))
+
+
+def _leaves(mesh) -> "C.Array":
+    arr = (map_block_desc * mesh.nleaves)()
+    for q, (p, lv, i, j, k) in enumerate(mesh.leaves):
+        arr[q].problem = int(p)
+        arr[q].level = int(lv)
+        arr[q].ijk[0] = int(i)
+        arr[q].ijk[1] = int(j)
+        arr[q].ijk[2] = int(k)
+    return arr
+
+
+class Pool:
+    """One block pool on the current CUDA device (wraps map_create_pool .. map_destroy_pool)."""
+
+    def __init__(self, mesh, precision: int = MAP_FP64, max_blocks: Optional[int] = None,
+                 stream: Optional[int] = None, ext_buffer: Optional[int] = None, ext_bytes: int = 0):
+        L = load()
+        self.mesh = mesh
+        self.precision = precision
+        n_par_est = mesh.nleaves // (3 if mesh.ndim == 2 else 7) + 4 * len(mesh.problems) + 64
+        self.max_blocks = int(max_blocks or (2 * (mesh.nleaves + n_par_est)))
+        probs = (map_problem_desc * len(mesh.problems))()
+        for q, pr in enumerate(mesh.problems):
+            for d in range(3):
+                probs[q].nbase[d] = int(pr.nbase[d])
+                probs[q].lo[d] = float(pr.lo[d])
+                probs[q].hi[d] = float(pr.hi[d])
+                probs[q].bc[d][0] = int(pr.bc[d][0])
+                probs[q].bc[d][1] = int(pr.bc[d][1])
+        self._probs = probs
+        desc = map_pool_desc(mesh.ndim, mesh.nb, 2, precision, self.max_blocks, len(mesh.problems),
+                             probs, C.c_void_p(ext_buffer or 0), ext_bytes)
+        h = C.c_void_p()
+        rc = L.map_create_pool(C.byref(desc), C.c_void_p(stream or 0), C.byref(h))
+        if rc != MAP_OK:
+            raise MapError(rc, "map_create_pool", L.map_last_error(None).decode())
+        self.h = h
+        self.set_tree(mesh)
+
+    # -- plumbing
+    def _ck(self, rc: int, what: str):
+        if rc != MAP_OK:
+            raise MapError(rc, what, load().map_last_error(self.h).decode())
+        return rc
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().map_destroy_pool(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def nleaves(self) -> int:
+        return self.mesh.nleaves
+
+    def interior_shape(self):
+        return (9,) + self.mesh.block_shape()
+
+    # -- ABI calls
+    def set_stream(self, stream: Optional[int]):
+        self._ck(load().map_set_stream(self.h, C.c_void_p(stream or 0)), "map_set_stream")
+
+    def set_tree(self, mesh):
+        self._leaves_arr = _leaves(mesh)
+        self._ck(load().map_set_tree(self.h, self._leaves_arr, mesh.nleaves), "map_set_tree")
+        self.mesh = mesh
+
+    def write_block(self, leaf: int, u: np.ndarray):
+        u = np.ascontiguousarray(u, dtype=np.float64)
+        self._ck(load().map_write_block(self.h, leaf, _ptr(u)), "map_write_block")
+
+    def read_block(self, leaf: int) -> np.ndarray:
+        out = np.empty(self.interior_shape(), dtype=np.float64)
+        self._ck(load().map_read_block(self.h, leaf, _ptr(out)), "map_read_block")
+        return out
+
+    def write_leaves(self, U: np.ndarray):
+        U = np.ascontiguousarray(U, dtype=np.float64)
+        assert U.shape == (self.nleaves,) + self.interior_shape()
+        self._ck(load().map_write_leaves(self.h, _ptr(U)), "map_write_leaves")
+
+    def write_leaves_ptr(self, host_ptr: int):
+        self._ck(load().map_write_leaves(self.h, C.c_void_p(host_ptr)), "map_write_leaves")
+
+    def read_leaves(self, out: Optional[np.ndarray] = None) -> np.ndarray:
+        if out is None:
+            out = np.empty((self.nleaves,) + self.interior_shape(), dtype=np.float64)
+        self._ck(load().map_read_leaves(self.h, _ptr(out)), "map_read_leaves")
+        return out
+
+    def read_leaves_ptr(self, host_ptr: int):
+        self._ck(load().map_read_leaves(self.h, C.c_void_p(host_ptr)), "map_read_leaves")
+
+    def fill_ghosts(self):
+        self._ck(load().map_fill_ghosts(self.h), "map_fill_ghosts")
+
+    def cfl_dt(self, params: Dict) -> np.ndarray:
+        dt = np.zeros(len(self.mesh.problems))
+        self._ck(load().map_cfl_dt(self.h, C.byref(make_params(params)), _ptr(dt)), "map_cfl_dt")
+        return dt
+
+    def step(self, params: Dict):
+        self._ck(load().map_step(self.h, C.byref(make_params(params))), "map_step")
+
+    def advance(self, params: Dict, nsteps: int = 1):
+        self._ck(load().map_advance(self.h, C.byref(make_params(params)), int(nsteps)), "map_advance")
+
+    def check(self) -> int:
+        return load().map_check(self.h)
+
+    def flag_refine(self, params: Dict, refine: Dict):
+        f = np.zeros(self.nleaves, dtype=np.int8)
+        est = np.zeros(self.nleaves, dtype=np.float64)
+        self._ck(load().map_flag_refine(self.h, C.byref(make_params(params)), C.byref(make_refine(refine)),
+                                        _ptr(f), _ptr(est)), "map_flag_refine")
+        return f, est
+
+    def regrid(self, new_mesh):
+        arr = _leaves(new_mesh)
+        self._ck(load().map_regrid(self.h, arr, new_mesh.nleaves), "map_regrid")
+        self._leaves_arr = arr
+        self.mesh = new_mesh
+
+    def conservation(self) -> np.ndarray:
+        out = np.zeros((len(self.mesh.problems), 9))
+        self._ck(load().map_conservation(self.h, _ptr(out)), "map_conservation")
+        return out
+
+    def speeds(self) -> np.ndarray:
+        out = np.zeros((len(self.mesh.problems), 5))
+        self._ck(load().map_get_speeds(self.h, _ptr(out)), "map_get_speeds")
+        return out
+
+    def kernel_launches(self) -> int:
+        return int(load().map_kernel_launches(self.h))

@@ -1,0 +1,323 @@
+// aux.cuh -- ghost fill, restriction, CFL reduction, refinement flags, conservation sums,
+// host-layout packing and regrid kernels.
+#pragma once
+#include "map_internal.hpp"
+#include "physics.cuh"
+#include "step.cuh"
+
+namespace mapgb {
+
+// Ghost fill of the leaves of one level (Sec. 4.3): every ghost cell gathers from the
+// block its region resolves to -- a copy from a same-level block, or the conservative
+// minmod prolongation of the covering coarser leaf (whose ghosts an earlier level pass
+// filled).  Region tables come from the host tree.
+template <typename T, int NDIM, int NB>
+__global__ void __launch_bounds__(256) fill_kernel(T* __restrict__ u, const int* __restrict__ blocks,
+                                                   int n, const GhostRegion* __restrict__ regions) {
+  using G = Geo<NDIM, NB>;
+  constexpr int NP = G::NP, P2 = G::P2, S = G::S;
+  __shared__ GhostRegion reg[27];
+  for (int bi = blockIdx.x; bi < n; bi += gridDim.x) {
+    const int blk = blocks[bi];
+    __syncthreads();
+    for (int r = threadIdx.x; r < 27; r += blockDim.x) reg[r] = regions[(size_t)blk * 27 + r];
+    __syncthreads();
+    T* ub = u + (size_t)blk * NV * S;
+    for (int c = threadIdx.x; c < S; c += blockDim.x) {
+      const int i = c % NP, j = (c / NP) % NP, k = NDIM == 3 ? c / P2 : 0;
+      const int rx = i < NG ? 0 : (i >= NG + NB ? 2 : 1);
+      const int ry = j < NG ? 0 : (j >= NG + NB ? 2 : 1);
+      const int rz = NDIM == 3 ? (k < NG ? 0 : (k >= NG + NB ? 2 : 1)) : 1;
+      if (rx == 1 && ry == 1 && rz == 1) continue;
+      const GhostRegion& g = reg[rx + 3 * ry + 9 * rz];
+      const T* sb = u + (size_t)g.src * NV * S;
+      if (g.kind == 0) {
+        const int si = g.m[0] * i + g.a[0], sj = g.m[1] * j + g.a[1];
+        const int sk = NDIM == 3 ? g.m[2] * k + g.a[2] : 0;
+        const int sc = (sk * NP + sj) * NP + si;
+#pragma unroll
+        for (int v = 0; v < NV; ++v) ub[(size_t)v * S + c] = sb[(size_t)v * S + sc];
+      } else {
+        const int gi = g.m[0] * i + g.a[0], gj = g.m[1] * j + g.a[1];
+        const int gk = NDIM == 3 ? g.m[2] * k + g.a[2] : 0;
+        const int ci = (gi >> 1) - g.corg[0] + NG, cj = (gj >> 1) - g.corg[1] + NG;
+        const int ck = NDIM == 3 ? (gk >> 1) - g.corg[2] + NG : 0;
+        const int cc = (ck * NP + cj) * NP + ci;
+        const T ox = (gi & 1) ? T(0.25) : T(-0.25);
+        const T oy = (gj & 1) ? T(0.25) : T(-0.25);
+        const T oz = (gk & 1) ? T(0.25) : T(-0.25);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+          const T* f = sb + (size_t)v * S;
+          T val = f[cc];
+          val += minmod<T>(f[cc + 1] - f[cc], f[cc] - f[cc - 1]) * ox;
+          val += minmod<T>(f[cc + NP] - f[cc], f[cc] - f[cc - NP]) * oy;
+          if (NDIM == 3) val += minmod<T>(f[cc + P2] - f[cc], f[cc] - f[cc - P2]) * oz;
+          ub[(size_t)v * S + c] = val;
+        }
+      }
+    }
+  }
+}
+
+// Parents of one level become the mean of their 2^ndim children (Sec. 4.3 step (1)).
+template <typename T, int NDIM, int NB>
+__global__ void __launch_bounds__(256) restrict_kernel(T* __restrict__ u, const int* __restrict__ parents,
+                                                       int n, const int* __restrict__ children) {
+  using G = Geo<NDIM, NB>;
+  constexpr int NP = G::NP, P2 = G::P2, S = G::S;
+  constexpr int NI = NDIM == 3 ? NB * NB * NB : NB * NB;
+  for (int bi = blockIdx.x; bi < n; bi += gridDim.x) {
+    const int par = parents[bi];
+    int ch[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) ch[q] = children[(size_t)par * 8 + q];
+    T* pb = u + (size_t)par * NV * S;
+    for (int c = threadIdx.x; c < NI; c += blockDim.x) {
+      const int i = c % NB, j = (c / NB) % NB, k = NDIM == 3 ? c / (NB * NB) : 0;
+      const int dst = ((NDIM == 3 ? k + NG : 0) * NP + j + NG) * NP + i + NG;
+#pragma unroll 1
+      for (int v = 0; v < NV; ++v) {
+        T sum = T(0);
+        for (int dz = 0; dz < (NDIM == 3 ? 2 : 1); ++dz)
+          for (int dy = 0; dy < 2; ++dy)
+            for (int dx = 0; dx < 2; ++dx) {
+              const int fi = 2 * i + dx, fj = 2 * j + dy, fk = 2 * k + dz;
+              const int cb = (fi / NB) | ((fj / NB) << 1) | ((NDIM == 3 ? fk / NB : 0) << 2);
+              const int lc = ((NDIM == 3 ? fk % NB + NG : 0) * NP + fj % NB + NG) * NP + fi % NB + NG;
+              sum += u[(size_t)ch[cb] * NV * S + (size_t)v * S + lc];
+            }
+        pb[(size_t)v * S + dst] = sum / T(1 << NDIM);
+      }
+    }
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void load_global(const T* b, size_t S, int c, T* w) {
+#pragma unroll
+  for (int v = 0; v < NV; ++v) w[v] = b[(size_t)v * S + c];
+}
+
+// alpha_g: max over leaf interior cells and directions of |v_d| + c_f,d (Sec. 3.7).
+template <typename T, int NDIM, int NB>
+__global__ void __launch_bounds__(256) cfl_kernel(const T* __restrict__ u, const int* __restrict__ blocks, int n,
+                                                  const BlockGeo* __restrict__ geo, ProbDyn* dyn, T gamma, T gm1) {
+  using G = Geo<NDIM, NB>;
+  constexpr int NP = G::NP, S = G::S;
+  constexpr int NI = NDIM == 3 ? NB * NB * NB : NB * NB;
+  __shared__ double red[32];
+  Phys<T> P;
+  P.gamma = gamma;
+  P.gm1 = gm1;
+  P.ch = T(0);
+  P.tau = T(0);
+  for (int bi = blockIdx.x; bi < n; bi += gridDim.x) {
+    const int blk = blocks[bi];
+    const T* ub = u + (size_t)blk * NV * S;
+    double am = 0.0;
+    for (int c = threadIdx.x; c < NI; c += blockDim.x) {
+      const int i = c % NB, j = (c / NB) % NB, k = NDIM == 3 ? c / (NB * NB) : 0;
+      const int cc = ((NDIM == 3 ? k + NG : 0) * NP + j + NG) * NP + i + NG;
+      T w[NV];
+      load_global<T>(ub, S, cc, w);
+      const T p = pressure<T>(w, P);
+      double a = (double)alpha_p<T, 0>(w, p, P);
+      a = fmax(a, (double)alpha_p<T, 1>(w, p, P));
+      if (NDIM == 3) a = fmax(a, (double)alpha_p<T, 2>(w, p, P));
+      if (a != a) am = a;            // NaN wins
+      else if (!(am != am)) am = fmax(am, a);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      double t = __shfl_xor_sync(0xffffffffu, am, o);
+      am = (t != t) ? t : fmax(am, t);
+    }
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = am;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double a = 0.0;
+      for (int q = 0; q < (int)(blockDim.x + 31) / 32; ++q) a = (red[q] != red[q]) ? red[q] : fmax(a, red[q]);
+      atomicMax(&dyn[geo[blk].problem].alpha_bits, (unsigned long long)__double_as_longlong(a));
+    }
+    __syncthreads();
+  }
+}
+
+// Refinement estimator (Sec. 4.5), computed in FP64 from the pool values, over the
+// interior and the first ghost ring; block maximum -> flag.
+template <typename T, int NDIM, int NB>
+__global__ void __launch_bounds__(256) flags_kernel(FlagLaunch L) {
+  using G = Geo<NDIM, NB>;
+  constexpr int NP = G::NP, P2 = G::P2, S = G::S;
+  constexpr int NR = NDIM == 3 ? (NB + 2) * (NB + 2) * (NB + 2) : (NB + 2) * (NB + 2);
+  __shared__ double red[32];
+  const T* u = (const T*)L.u;
+  const double gm1 = L.gamma - 1.0;
+  auto pres = [&](const T* ub, int c) -> double {
+    double w[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) w[v] = (double)ub[(size_t)v * S + c];
+    double m2 = w[MX] * w[MX] + w[MY] * w[MY] + w[MZ] * w[MZ];
+    double b2 = w[BX] * w[BX] + w[BY] * w[BY] + w[BZ] * w[BZ];
+    return gm1 * (w[EN] - 0.5 * m2 / w[RHO] - 0.5 * b2);
+  };
+  const int offs[3] = {1, NP, P2};
+  for (int bi = blockIdx.x; bi < L.nblocks; bi += gridDim.x) {
+    const int blk = L.blocks[bi];
+    const BlockGeo gg = L.geo[blk];
+    const T* ub = u + (size_t)blk * NV * S;
+    double mindx = gg.dx[0];
+    for (int d = 1; d < NDIM; ++d) mindx = fmin(mindx, gg.dx[d]);
+    const double lvf = pow(L.r.ratio, L.r.xi * (double)(gg.level + 1 - 1));
+    double emax = 0.0;
+    for (int q = threadIdx.x; q < NR; q += blockDim.x) {
+      const int i = 1 + q % (NB + 2), j = 1 + (q / (NB + 2)) % (NB + 2);
+      const int k = NDIM == 3 ? 1 + q / ((NB + 2) * (NB + 2)) : 0;
+      const int c = (k * NP + j) * NP + i;
+      auto est = [&](auto field, double eps) -> double {
+        double s1 = 0.0, s2 = 0.0;
+        const double f0 = field(c);
+        for (int d = 0; d < NDIM; ++d) {
+          const double fp = field(c + offs[d]), fm = field(c - offs[d]);
+          const double d1 = fp - fm;
+          const double d2 = fp - 2.0 * f0 + fm;
+          s1 += d1 * d1;
+          s2 += d2 * d2;
+        }
+        const double du = sqrt(3.0) / 2.0 * sqrt(s1);
+        const double d2u = sqrt(s2);
+        const double au = fabs(f0) + eps;
+        const double e = L.r.bias * du / au + (1.0 - L.r.bias) * d2u / (du + L.r.filter * au);
+        return e * lvf;
+      };
+      if (L.r.var_mask & 1) emax = fmax(emax, est([&](int cc) { return (double)ub[RHO * (size_t)S + cc]; }, L.r.eps_rho));
+      if (L.r.var_mask & 2) emax = fmax(emax, est([&](int cc) { return pres(ub, cc); }, L.r.eps_p));
+      if (L.r.var_mask & 4) {
+        auto cd = [&](int comp, int d) -> double {
+          if (d >= NDIM) return 0.0;
+          return ((double)ub[(size_t)comp * S + c + offs[d]] - (double)ub[(size_t)comp * S + c - offs[d]]) /
+                 (2.0 * gg.dx[d]);
+        };
+        const double jx = cd(BZ, 1) - cd(BY, 2);
+        const double jy = cd(BX, 2) - cd(BZ, 0);
+        const double jz = cd(BY, 0) - cd(BX, 1);
+        const double bx = ub[(size_t)BX * S + c], by = ub[(size_t)BY * S + c], bz = ub[(size_t)BZ * S + c];
+        const double e = sqrt(jx * jx + jy * jy + jz * jz) * mindx / (sqrt(bx * bx + by * by + bz * bz) + L.r.eps_b);
+        emax = fmax(emax, e);
+      }
+    }
+    for (int o = 16; o > 0; o >>= 1) emax = fmax(emax, __shfl_xor_sync(0xffffffffu, emax, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = emax;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double e = 0.0;
+      for (int q = 0; q < (int)(blockDim.x + 31) / 32; ++q) e = fmax(e, red[q]);
+      int8_t f = 0;
+      if (e > L.r.thr && gg.level < L.r.max_level) f = 1;
+      else if (e < L.r.coarsen_thr && gg.level > 0) f = -1;
+      L.flags[bi] = f;
+      if (L.est) L.est[bi] = e;
+    }
+    __syncthreads();
+  }
+}
+
+// FP64 conservation sums of the leaf interiors: sum U * cell volume per problem.
+template <typename T, int NDIM, int NB>
+__global__ void __launch_bounds__(256) sums_kernel(SumLaunch L) {
+  using G = Geo<NDIM, NB>;
+  constexpr int NP = G::NP, S = G::S;
+  constexpr int NI = NDIM == 3 ? NB * NB * NB : NB * NB;
+  __shared__ double red[NV][32];
+  const T* u = (const T*)L.u;
+  for (int bi = blockIdx.x; bi < L.nblocks; bi += gridDim.x) {
+    const int blk = L.blocks[bi];
+    const BlockGeo gg = L.geo[blk];
+    const T* ub = u + (size_t)blk * NV * S;
+    double s[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) s[v] = 0.0;
+    for (int c = threadIdx.x; c < NI; c += blockDim.x) {
+      const int i = c % NB, j = (c / NB) % NB, k = NDIM == 3 ? c / (NB * NB) : 0;
+      const int cc = ((NDIM == 3 ? k + NG : 0) * NP + j + NG) * NP + i + NG;
+#pragma unroll
+      for (int v = 0; v < NV; ++v) s[v] += (double)ub[(size_t)v * S + cc];
+    }
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      for (int o = 16; o > 0; o >>= 1) s[v] += __shfl_xor_sync(0xffffffffu, s[v], o);
+      if ((threadIdx.x & 31) == 0) red[v][threadIdx.x >> 5] = s[v];
+    }
+    __syncthreads();
+    if (threadIdx.x < NV) {
+      double t = 0.0;
+      for (int q = 0; q < (int)(blockDim.x + 31) / 32; ++q) t += red[threadIdx.x][q];
+      const double vol = gg.dx[0] * gg.dx[1] * (NDIM == 3 ? gg.dx[2] : 1.0);
+      atomicAdd(&L.sums[gg.problem * NV + threadIdx.x], t * vol);
+    }
+    __syncthreads();
+  }
+}
+
+// Host layout [n][9][nz][nb][nb] (FP64) <-> pool interiors.
+template <typename T, int NDIM, int NB>
+__global__ void __launch_bounds__(256) pack_kernel(PackLaunch L) {
+  using G = Geo<NDIM, NB>;
+  constexpr int NP = G::NP, S = G::S;
+  constexpr int NI = NDIM == 3 ? NB * NB * NB : NB * NB;
+  T* u = (T*)L.u;
+  for (int bi = blockIdx.x; bi < L.nblocks; bi += gridDim.x) {
+    const int blk = L.blocks[bi];
+    T* ub = u + (size_t)blk * NV * S;
+    double* hb = L.host_layout + (size_t)bi * NV * NI;
+    for (int q = threadIdx.x; q < NV * NI; q += blockDim.x) {
+      const int v = q / NI, c = q % NI;
+      const int i = c % NB, j = (c / NB) % NB, k = NDIM == 3 ? c / (NB * NB) : 0;
+      const int cc = ((NDIM == 3 ? k + NG : 0) * NP + j + NG) * NP + i + NG;
+      if (L.to_pool) ub[(size_t)v * S + cc] = (T)hb[q];
+      else hb[q] = (double)ub[(size_t)v * S + cc];
+    }
+  }
+}
+
+// Regrid: copy kept / coarsened leaves, prolong new children from their old parent leaf
+// (Sec. 4.3 formula applied to interior cells; the old parent's ghosts are filled).
+template <typename T, int NDIM, int NB>
+__global__ void __launch_bounds__(256) regrid_kernel(RegridLaunch L) {
+  using G = Geo<NDIM, NB>;
+  constexpr int NP = G::NP, P2 = G::P2, S = G::S;
+  constexpr int NI = NDIM == 3 ? NB * NB * NB : NB * NB;
+  const T* uo = (const T*)L.u_old;
+  T* un = (T*)L.u_new;
+  for (int ti = blockIdx.x; ti < L.ntasks; ti += gridDim.x) {
+    const RegridTask tk = L.tasks[ti];
+    const T* sb = uo + (size_t)tk.src * NV * S;
+    T* db = un + (size_t)tk.dst * NV * S;
+    const int bx = tk.cb & 1, by = (tk.cb >> 1) & 1, bz = (tk.cb >> 2) & 1;
+    for (int c = threadIdx.x; c < NI; c += blockDim.x) {
+      const int i = c % NB, j = (c / NB) % NB, k = NDIM == 3 ? c / (NB * NB) : 0;
+      const int dc = ((NDIM == 3 ? k + NG : 0) * NP + j + NG) * NP + i + NG;
+      if (tk.kind == 0) {
+#pragma unroll
+        for (int v = 0; v < NV; ++v) db[(size_t)v * S + dc] = sb[(size_t)v * S + dc];
+      } else {
+        const int gi = bx * NB + i, gj = by * NB + j, gk = bz * NB + k;
+        const int cc = ((NDIM == 3 ? (gk >> 1) + NG : 0) * NP + (gj >> 1) + NG) * NP + (gi >> 1) + NG;
+        const T ox = (gi & 1) ? T(0.25) : T(-0.25);
+        const T oy = (gj & 1) ? T(0.25) : T(-0.25);
+        const T oz = (gk & 1) ? T(0.25) : T(-0.25);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+          const T* f = sb + (size_t)v * S;
+          T val = f[cc];
+          val += minmod<T>(f[cc + 1] - f[cc], f[cc] - f[cc - 1]) * ox;
+          val += minmod<T>(f[cc + NP] - f[cc], f[cc] - f[cc - NP]) * oy;
+          if (NDIM == 3) val += minmod<T>(f[cc + P2] - f[cc], f[cc] - f[cc - P2]) * oz;
+          db[(size_t)v * S + dc] = val;
+        }
+      }
+    }
+  }
+}
+
+}  // namespace mapgb

@@ -1,0 +1,669 @@
+// capi.cpp -- the extern "C" ABI declared in include/map.h: pool memory, tree tables,
+// the step sequence and its CUDA-graph replay.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <string.h>
+
+#include <string>
+#include <vector>
+
+#include "map_internal.hpp"
+
+using namespace mapgb;
+
+struct DevTree {
+  BlockGeo* geo = nullptr;
+  GhostRegion* regions = nullptr;
+  int* children = nullptr;
+  int* leaf_ids = nullptr;     // caller leaf order -> pool id
+  int* all_leaves = nullptr;   // pool ids 0..n-1 (Morton order)
+  int* level_leaves = nullptr; // concatenated by level
+  int* level_parents = nullptr;
+  std::vector<int> leaf_off, parent_off;  // offsets per level (host)
+};
+
+struct map_pool {
+  int ndim = 0, nb = 0, precision = 0, max_blocks = 0, nprob = 0;
+  std::vector<map_problem_desc> probs;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  size_t block_elems = 0, elem = 0;
+  void* buf[3] = {nullptr, nullptr, nullptr};
+  bool ext = false;
+  int cur = 0;
+  HostTree tree;
+  bool have_tree = false;
+  DevTree dt;
+  ProbDyn* dyn = nullptr;
+  unsigned* err_word = nullptr;
+  double* sums = nullptr;
+  double* staging = nullptr;
+  size_t staging_elems = 0;
+  int8_t* flags = nullptr;
+  double* est = nullptr;
+  int flags_cap = 0;
+  RegridTask* tasks = nullptr;
+  int tasks_cap = 0;
+  bool have_dt = false;
+  bool alpha_ready = false;   // dyn.alpha_bits holds alpha_g of the current state
+  long long launches = 0;
+  std::string err;
+  // graph cache (one per starting buffer parity)
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  long long graph_kernels[2] = {0, 0};
+  map_params graph_params{};
+  bool graph_valid[2] = {false, false};
+};
+
+static std::string g_create_error;
+
+static int fail(map_pool* p, int code, const std::string& msg) {
+  if (p) p->err = msg;
+  else g_create_error = msg;
+  return code;
+}
+
+#define CK(call)                                                                              \
+  do {                                                                                        \
+    cudaError_t e_ = (call);                                                                  \
+    if (e_ != cudaSuccess) return fail(pool, MAP_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+static KernelConfig kcfg(const map_pool* p) { return KernelConfig{p->ndim, p->nb}; }
+static bool is64(const map_pool* p) { return p->precision == MAP_FP64; }
+
+// dispatch helpers ----------------------------------------------------------------------
+#define DISPATCH(pool, name, L) \
+  (is64(pool) ? launch_##name##_f64(kcfg(pool), L, pool->stream, &pool->launches) \
+              : launch_##name##_f32(kcfg(pool), L, pool->stream, &pool->launches))
+
+static void free_tree(map_pool* pool) {
+  cudaFree(pool->dt.geo);
+  cudaFree(pool->dt.regions);
+  cudaFree(pool->dt.children);
+  cudaFree(pool->dt.leaf_ids);
+  cudaFree(pool->dt.all_leaves);
+  cudaFree(pool->dt.level_leaves);
+  cudaFree(pool->dt.level_parents);
+  pool->dt = DevTree();
+}
+
+static void drop_graphs(map_pool* pool) {
+  for (int q = 0; q < 2; ++q) {
+    if (pool->graph[q]) cudaGraphExecDestroy(pool->graph[q]);
+    pool->graph[q] = nullptr;
+    pool->graph_valid[q] = false;
+  }
+}
+
+template <typename X>
+static cudaError_t upload(X** dst, const std::vector<X>& src, cudaStream_t s) {
+  size_t n = src.size() ? src.size() : 1;
+  cudaError_t e = cudaMalloc((void**)dst, n * sizeof(X));
+  if (e != cudaSuccess) return e;
+  if (!src.empty()) e = cudaMemcpyAsync(*dst, src.data(), src.size() * sizeof(X), cudaMemcpyHostToDevice, s);
+  return e;
+}
+
+extern "C" {
+
+int map_create_pool(const map_pool_desc* d, void* stream, map_pool** out) {
+  map_pool* pool = nullptr;
+  if (!d || !out) return fail(nullptr, MAP_EINVAL, "null argument");
+  *out = nullptr;
+  if (d->ndim != 2 && d->ndim != 3) return fail(nullptr, MAP_EINVAL, "ndim must be 2 or 3");
+  if (d->nb != 8 && d->nb != 16) return fail(nullptr, MAP_EUNSUPPORTED, "nb must be 8 or 16");
+  if (d->n_ghost != 2) return fail(nullptr, MAP_EINVAL, "n_ghost must be 2");
+  if (d->precision != MAP_FP64 && d->precision != MAP_FP32_FIX64) return fail(nullptr, MAP_EINVAL, "bad precision");
+  if (d->max_blocks < 1 || d->n_problems < 1 || !d->problems) return fail(nullptr, MAP_EINVAL, "bad capacity or problems");
+  pool = new map_pool();
+  pool->ndim = d->ndim;
+  pool->nb = d->nb;
+  pool->precision = d->precision;
+  pool->max_blocks = d->max_blocks;
+  pool->nprob = d->n_problems;
+  pool->probs.assign(d->problems, d->problems + d->n_problems);
+  const int NP = d->nb + 4;
+  const size_t S = (size_t)NP * NP * (d->ndim == 3 ? NP : 1);
+  pool->block_elems = (size_t)kNV * S;
+  pool->elem = d->precision == MAP_FP64 ? 8 : 4;
+  const size_t buf_bytes = pool->block_elems * pool->elem * (size_t)d->max_blocks;
+  auto cleanup = [&](int code, const std::string& m) {
+    g_create_error = m;
+    map_destroy_pool(pool);
+    return code;
+  };
+  if (stream) {
+    pool->stream = (cudaStream_t)stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&pool->stream, cudaStreamNonBlocking) != cudaSuccess)
+      return cleanup(MAP_ECUDA, "cudaStreamCreate failed");
+    pool->own_stream = true;
+  }
+  if (d->ext_buffer) {
+    if (d->ext_bytes < 3 * buf_bytes) return cleanup(MAP_ENOMEM, "external buffer smaller than 3 state buffers");
+    if (((uintptr_t)d->ext_buffer) % 256) return cleanup(MAP_EINVAL, "external buffer must be 256-byte aligned");
+    pool->ext = true;
+    for (int q = 0; q < 3; ++q) pool->buf[q] = (char*)d->ext_buffer + q * buf_bytes;
+  } else {
+    for (int q = 0; q < 3; ++q)
+      if (cudaMalloc(&pool->buf[q], buf_bytes) != cudaSuccess) return cleanup(MAP_ENOMEM, "cudaMalloc of the block pool failed");
+  }
+  // zero the state buffers so never-written ghost or parent cells are finite
+  for (int q = 0; q < 3; ++q)
+    if (cudaMemsetAsync(pool->buf[q], 0, buf_bytes, pool->stream) != cudaSuccess) return cleanup(MAP_ECUDA, "memset failed");
+  if (cudaMalloc(&pool->dyn, sizeof(ProbDyn) * pool->nprob) != cudaSuccess ||
+      cudaMalloc(&pool->err_word, sizeof(unsigned)) != cudaSuccess ||
+      cudaMalloc(&pool->sums, sizeof(double) * kNV * pool->nprob) != cudaSuccess)
+    return cleanup(MAP_ENOMEM, "cudaMalloc of the step constants failed");
+  cudaMemsetAsync(pool->dyn, 0, sizeof(ProbDyn) * pool->nprob, pool->stream);
+  cudaMemsetAsync(pool->err_word, 0, sizeof(unsigned), pool->stream);
+  if (cudaStreamSynchronize(pool->stream) != cudaSuccess) return cleanup(MAP_ECUDA, "stream synchronize failed");
+  *out = pool;
+  return MAP_OK;
+}
+
+int map_destroy_pool(map_pool* pool) {
+  if (!pool) return MAP_OK;
+  if (pool->stream) cudaStreamSynchronize(pool->stream);
+  drop_graphs(pool);
+  free_tree(pool);
+  if (!pool->ext)
+    for (int q = 0; q < 3; ++q) cudaFree(pool->buf[q]);
+  cudaFree(pool->dyn);
+  cudaFree(pool->err_word);
+  cudaFree(pool->sums);
+  cudaFree(pool->staging);
+  cudaFree(pool->flags);
+  cudaFree(pool->est);
+  cudaFree(pool->tasks);
+  if (pool->own_stream) cudaStreamDestroy(pool->stream);
+  delete pool;
+  return MAP_OK;
+}
+
+int map_set_stream(map_pool* pool, void* stream) {
+  if (!pool) return MAP_EINVAL;
+  cudaStreamSynchronize(pool->stream);
+  if (pool->own_stream) cudaStreamDestroy(pool->stream);
+  pool->own_stream = false;
+  if (stream) pool->stream = (cudaStream_t)stream;
+  else {
+    CK(cudaStreamCreateWithFlags(&pool->stream, cudaStreamNonBlocking));
+    pool->own_stream = true;
+  }
+  drop_graphs(pool);
+  return MAP_OK;
+}
+
+static int install_tree(map_pool* pool, HostTree& t) {
+  free_tree(pool);
+  drop_graphs(pool);
+  DevTree& D = pool->dt;
+  CK(upload(&D.geo, t.geo, pool->stream));
+  CK(upload(&D.regions, t.regions, pool->stream));
+  CK(upload(&D.children, t.children, pool->stream));
+  CK(upload(&D.leaf_ids, t.leaf_to_block, pool->stream));
+  CK(upload(&D.all_leaves, t.all_leaves, pool->stream));
+  std::vector<int> ll, pl;
+  D.leaf_off.assign(t.maxlev + 2, 0);
+  D.parent_off.assign(t.maxlev + 2, 0);
+  for (int L = 0; L <= t.maxlev; ++L) {
+    D.leaf_off[L] = (int)ll.size();
+    ll.insert(ll.end(), t.leaves_by_level[L].begin(), t.leaves_by_level[L].end());
+    D.parent_off[L] = (int)pl.size();
+    pl.insert(pl.end(), t.parents_by_level[L].begin(), t.parents_by_level[L].end());
+  }
+  D.leaf_off[t.maxlev + 1] = (int)ll.size();
+  D.parent_off[t.maxlev + 1] = (int)pl.size();
+  CK(upload(&D.level_leaves, ll, pool->stream));
+  CK(upload(&D.level_parents, pl, pool->stream));
+  // per-problem minimum spacing (dt uses the finest leaf, Sec. 4.5 / Sec. 3.7)
+  std::vector<ProbDyn> dyn(pool->nprob);
+  CK(cudaMemcpyAsync(dyn.data(), pool->dyn, sizeof(ProbDyn) * pool->nprob, cudaMemcpyDeviceToHost, pool->stream));
+  CK(cudaStreamSynchronize(pool->stream));
+  for (int p = 0; p < pool->nprob; ++p) {
+    dyn[p].mindx = t.mindx[p];
+    dyn[p].alpha_bits = 0ull;
+  }
+  CK(cudaMemcpyAsync(pool->dyn, dyn.data(), sizeof(ProbDyn) * pool->nprob, cudaMemcpyHostToDevice, pool->stream));
+  // staging for host-layout copies
+  const size_t ni = (size_t)pool->nb * pool->nb * (pool->ndim == 3 ? pool->nb : 1);
+  const size_t need = (size_t)t.nleaves * kNV * ni;
+  if (need > pool->staging_elems) {
+    cudaFree(pool->staging);
+    pool->staging = nullptr;
+    CK(cudaMalloc(&pool->staging, need * sizeof(double)));
+    pool->staging_elems = need;
+  }
+  if (t.nleaves > pool->flags_cap) {
+    cudaFree(pool->flags);
+    cudaFree(pool->est);
+    CK(cudaMalloc(&pool->flags, t.nleaves));
+    CK(cudaMalloc(&pool->est, t.nleaves * sizeof(double)));
+    pool->flags_cap = t.nleaves;
+  }
+  CK(cudaStreamSynchronize(pool->stream));
+  pool->tree = std::move(t);
+  pool->have_tree = true;
+  pool->have_dt = false;
+  pool->alpha_ready = false;
+  return MAP_OK;
+}
+
+int map_set_tree(map_pool* pool, const map_block_desc* leaves, int n) {
+  if (!pool || !leaves || n <= 0) return fail(pool, MAP_EINVAL, "null or empty leaf list");
+  HostTree t;
+  std::string why = build_tree(pool->ndim, pool->nb, pool->probs, leaves, n, t);
+  if (!why.empty()) return fail(pool, MAP_EINVAL, why);
+  if (t.nblocks > pool->max_blocks) return fail(pool, MAP_ENOMEM, "tree has more blocks than max_blocks");
+  return install_tree(pool, t);
+}
+
+static size_t interior_elems(const map_pool* p) {
+  return (size_t)p->nb * p->nb * (p->ndim == 3 ? p->nb : 1) * kNV;
+}
+
+static int pack(map_pool* pool, const int* dev_ids, int n, int to_pool) {
+  PackLaunch L;
+  L.u = pool->buf[pool->cur];
+  L.host_layout = pool->staging;
+  L.blocks = dev_ids;
+  L.nblocks = n;
+  L.to_pool = to_pool;
+  CK(DISPATCH(pool, pack, L));
+  return MAP_OK;
+}
+
+int map_write_block(map_pool* pool, int leaf, const double* u) {
+  if (!pool || !u) return fail(pool, MAP_EINVAL, "null argument");
+  if (!pool->have_tree) return fail(pool, MAP_ESTATE, "no tree");
+  if (leaf < 0 || leaf >= pool->tree.nleaves) return fail(pool, MAP_EINVAL, "leaf index out of range");
+  CK(cudaMemcpyAsync(pool->staging, u, interior_elems(pool) * sizeof(double), cudaMemcpyHostToDevice, pool->stream));
+  pool->have_dt = false;
+  pool->alpha_ready = false;
+  return pack(pool, pool->dt.leaf_ids + leaf, 1, 1);
+}
+
+int map_read_block(map_pool* pool, int leaf, double* u) {
+  if (!pool || !u) return fail(pool, MAP_EINVAL, "null argument");
+  if (!pool->have_tree) return fail(pool, MAP_ESTATE, "no tree");
+  if (leaf < 0 || leaf >= pool->tree.nleaves) return fail(pool, MAP_EINVAL, "leaf index out of range");
+  int rc = pack(pool, pool->dt.leaf_ids + leaf, 1, 0);
+  if (rc) return rc;
+  CK(cudaMemcpyAsync(u, pool->staging, interior_elems(pool) * sizeof(double), cudaMemcpyDeviceToHost, pool->stream));
+  CK(cudaStreamSynchronize(pool->stream));
+  return MAP_OK;
+}
+
+int map_write_leaves(map_pool* pool, const double* u) {
+  if (!pool || !u) return fail(pool, MAP_EINVAL, "null argument");
+  if (!pool->have_tree) return fail(pool, MAP_ESTATE, "no tree");
+  const int n = pool->tree.nleaves;
+  CK(cudaMemcpyAsync(pool->staging, u, (size_t)n * interior_elems(pool) * sizeof(double), cudaMemcpyHostToDevice,
+                     pool->stream));
+  pool->have_dt = false;
+  pool->alpha_ready = false;
+  return pack(pool, pool->dt.leaf_ids, n, 1);
+}
+
+int map_read_leaves(map_pool* pool, double* u) {
+  if (!pool || !u) return fail(pool, MAP_EINVAL, "null argument");
+  if (!pool->have_tree) return fail(pool, MAP_ESTATE, "no tree");
+  const int n = pool->tree.nleaves;
+  int rc = pack(pool, pool->dt.leaf_ids, n, 0);
+  if (rc) return rc;
+  CK(cudaMemcpyAsync(u, pool->staging, (size_t)n * interior_elems(pool) * sizeof(double), cudaMemcpyDeviceToHost,
+                     pool->stream));
+  CK(cudaStreamSynchronize(pool->stream));
+  return MAP_OK;
+}
+
+// ghost fill on state buffer q: restriction bottom-up, then level passes top-down
+static int fill_on(map_pool* pool, int q) {
+  const HostTree& t = pool->tree;
+  const DevTree& D = pool->dt;
+  for (int L = t.maxlev - 1; L >= 0; --L) {
+    RestrictLaunch R;
+    R.u = pool->buf[q];
+    R.parents = D.level_parents + D.parent_off[L];
+    R.nparents = D.parent_off[L + 1] - D.parent_off[L];
+    R.children = D.children;
+    CK(DISPATCH(pool, restrict, R));
+  }
+  for (int L = 0; L <= t.maxlev; ++L) {
+    FillLaunch F;
+    F.u = pool->buf[q];
+    F.blocks = D.level_leaves + D.leaf_off[L];
+    F.nblocks = D.leaf_off[L + 1] - D.leaf_off[L];
+    F.regions = D.regions;
+    CK(DISPATCH(pool, fill, F));
+  }
+  return MAP_OK;
+}
+
+int map_fill_ghosts(map_pool* pool) {
+  if (!pool) return MAP_EINVAL;
+  if (!pool->have_tree) return fail(pool, MAP_ESTATE, "no tree");
+  return fill_on(pool, pool->cur);
+}
+
+static FinalizeLaunch make_finalize(const map_pool* pool, const map_params* p) {
+  FinalizeLaunch F;
+  F.dyn = pool->dyn;
+  F.nprob = pool->nprob;
+  F.ndim = pool->ndim;
+  F.c_cfl = p->c_cfl;
+  F.eta = p->eta;
+  F.ch_fixed = p->ch;
+  F.cp_fixed = p->cp;
+  F.c_d = p->c_d;
+  F.dt_override = p->dt_override;
+  F.ch_mode = p->ch_mode;
+  F.cp_mode = p->cp_mode;
+  return F;
+}
+
+// alpha_g of the current state into dyn.alpha_bits (max over leaf cells, Sec. 3.7)
+static int alpha_device(map_pool* pool, const map_params* p) {
+  CK(launch_zero_alpha(pool->dyn, pool->nprob, pool->stream, &pool->launches));
+  CflLaunch C;
+  C.u = pool->buf[pool->cur];
+  C.blocks = pool->dt.all_leaves;
+  C.nblocks = pool->tree.nleaves;
+  C.geo = pool->dt.geo;
+  C.dyn = pool->dyn;
+  C.gamma = p->gamma;
+  CK(DISPATCH(pool, cfl, C));
+  return MAP_OK;
+}
+
+static int cfl_device(map_pool* pool, const map_params* p) {
+  int rc = alpha_device(pool, p);
+  if (rc) return rc;
+  CK(launch_finalize(make_finalize(pool, p), pool->stream, &pool->launches));
+  pool->alpha_ready = false;  // finalize consumed and reset the running maximum
+  return MAP_OK;
+}
+
+static bool params_equal(const map_params& a, const map_params& b) {
+  return a.gamma == b.gamma && a.c_cfl == b.c_cfl && a.ch_mode == b.ch_mode && a.ch == b.ch &&
+         a.cp_mode == b.cp_mode && a.c_d == b.c_d && a.cp == b.cp && a.eta == b.eta && a.eglm == b.eglm &&
+         a.scheme == b.scheme && a.limiter == b.limiter && a.dt_override == b.dt_override &&
+         a.fp64_fix_tau == b.fp64_fix_tau;
+}
+
+static int check_params(map_pool* pool, const map_params* p) {
+  if (!p) return fail(pool, MAP_EINVAL, "null params");
+  if (!(p->gamma > 1.0) || !(p->c_cfl > 0.0)) return fail(pool, MAP_EINVAL, "gamma must exceed 1 and c_cfl be positive");
+  if (p->scheme < 0 || p->scheme > 2 || p->limiter < 0 || p->limiter > 1) return fail(pool, MAP_EINVAL, "bad scheme or limiter");
+  if (p->ch_mode < 0 || p->ch_mode > 2 || p->cp_mode < 0 || p->cp_mode > 1) return fail(pool, MAP_EINVAL, "bad c_h / c_p mode");
+  if (p->cp_mode == MAP_CP_FROM_CD && !(p->c_d > 0.0 && p->c_d < 1.0)) return fail(pool, MAP_EINVAL, "c_d must lie in (0,1)");
+  if (p->eta < 0.0) return fail(pool, MAP_EINVAL, "eta must be >= 0");
+  if (!pool->have_tree) return fail(pool, MAP_ESTATE, "no tree");
+  size_t smem = is64(pool) ? step_smem_f64(kcfg(pool), p->scheme, p->eta > 0.0)
+                           : step_smem_f32(kcfg(pool), p->scheme, p->eta > 0.0);
+  int dev = 0, optin = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (smem == 0 || (optin > 0 && smem > (size_t)optin))
+    return fail(pool, MAP_EUNSUPPORTED, "this block size / precision / scheme / resistivity needs more shared memory than a block has");
+  return MAP_OK;
+}
+
+int map_cfl_dt(map_pool* pool, const map_params* p, double* dt_out) {
+  if (!pool) return MAP_EINVAL;
+  int rc = check_params(pool, p);
+  if (rc) return rc;
+  rc = cfl_device(pool, p);
+  if (rc) return rc;
+  std::vector<ProbDyn> dyn(pool->nprob);
+  CK(cudaMemcpyAsync(dyn.data(), pool->dyn, sizeof(ProbDyn) * pool->nprob, cudaMemcpyDeviceToHost, pool->stream));
+  CK(cudaStreamSynchronize(pool->stream));
+  pool->have_dt = true;
+  int status = MAP_OK;
+  for (int q = 0; q < pool->nprob; ++q) {
+    if (dt_out) dt_out[q] = dyn[q].dt;
+    if (!(isfinite(dyn[q].dt) && dyn[q].dt > 0.0)) status = MAP_ENONFINITE;
+  }
+  if (status) return fail(pool, status, "time step is not finite and positive (non-finite or zero signal speed)");
+  return MAP_OK;
+}
+
+// launches of one step on buffer pool->cur; flips cur.  fused: also reduce alpha of the
+// new state into dyn (next dt) and the FP64 sums.
+static int step_launches(map_pool* pool, const map_params* p, bool fused) {
+  const HostTree& t = pool->tree;
+  StepLaunch S{};
+  S.geo = pool->dt.geo;
+  S.dyn = pool->dyn;
+  S.gamma = p->gamma;
+  S.eta = p->eta;
+  S.tau = is64(pool) ? 0.0 : (p->fp64_fix_tau > 0.0 ? p->fp64_fix_tau : 0.0);
+  S.eglm = p->eglm;
+  S.scheme = p->scheme;
+  S.limiter = p->limiter;
+  S.err_word = pool->err_word;
+  S.sums = fused ? pool->sums : nullptr;
+  S.dyn_next = fused ? pool->dyn : nullptr;
+  const int in = pool->cur, out = 1 - pool->cur;
+  // the plain FP64 form launches once per level; the FP32 form once over all leaves
+  auto run = [&](const void* uin, void* uout, const void* ubase, int stage, bool with_fused) -> int {
+    S.u_in = uin;
+    S.u_out = uout;
+    S.u_base = ubase;
+    S.stage = stage;
+    S.sums = with_fused ? pool->sums : nullptr;
+    S.dyn_next = with_fused ? pool->dyn : nullptr;
+    if (is64(pool)) {
+      for (int L = 0; L <= t.maxlev; ++L) {
+        S.blocks = pool->dt.level_leaves + pool->dt.leaf_off[L];
+        S.nblocks = pool->dt.leaf_off[L + 1] - pool->dt.leaf_off[L];
+        S.grid = 0;
+        CK(DISPATCH(pool, step, S));
+      }
+    } else {
+      S.blocks = pool->dt.all_leaves;
+      S.nblocks = t.nleaves;
+      S.grid = 0;
+      CK(DISPATCH(pool, step, S));
+    }
+    return MAP_OK;
+  };
+  int rc;
+  if (fused) {
+    CK(cudaMemsetAsync(pool->sums, 0, sizeof(double) * kNV * pool->nprob, pool->stream));
+  }
+  if (p->scheme == MAP_WENO) {
+    rc = run(pool->buf[in], pool->buf[2], nullptr, 1, false);
+    if (rc) return rc;
+    rc = fill_on(pool, 2);
+    if (rc) return rc;
+    rc = run(pool->buf[2], pool->buf[out], pool->buf[in], 2, fused);
+    if (rc) return rc;
+  } else {
+    rc = run(pool->buf[in], pool->buf[out], nullptr, 0, fused);
+    if (rc) return rc;
+  }
+  pool->cur = out;
+  return MAP_OK;
+}
+
+int map_step(map_pool* pool, const map_params* p) {
+  if (!pool) return MAP_EINVAL;
+  int rc = check_params(pool, p);
+  if (rc) return rc;
+  if (!pool->have_dt && !(p->dt_override > 0.0)) return fail(pool, MAP_ESTATE, "no time step: call map_cfl_dt first");
+  if (p->dt_override > 0.0 && !pool->have_dt) {
+    rc = cfl_device(pool, p);
+    if (rc) return rc;
+  }
+  rc = step_launches(pool, p, false);
+  pool->have_dt = false;
+  pool->alpha_ready = false;
+  return rc;
+}
+
+// one full step on the current buffer: ghost fill, dt from the alpha_g that the previous
+// fused step (or the initial reduction) left in dyn, update with the alpha_g of the new
+// state and the conservation sums reduced in the same kernel
+static int advance_once(map_pool* pool, const map_params* p) {
+  int rc = fill_on(pool, pool->cur);
+  if (rc) return rc;
+  CK(launch_finalize(make_finalize(pool, p), pool->stream, &pool->launches));
+  return step_launches(pool, p, true);
+}
+
+int map_advance(map_pool* pool, const map_params* p, int nsteps) {
+  if (!pool) return MAP_EINVAL;
+  int rc = check_params(pool, p);
+  if (rc) return rc;
+  if (nsteps <= 0) return MAP_OK;
+  if (!params_equal(pool->graph_params, *p)) {
+    drop_graphs(pool);
+    pool->graph_params = *p;
+  }
+  if (!pool->alpha_ready) {
+    rc = alpha_device(pool, p);
+    if (rc) return rc;
+    pool->alpha_ready = true;
+  }
+  for (int s = 0; s < nsteps; ++s) {
+    const int q = pool->cur;
+    if (!pool->graph_valid[q]) {
+      // first step from this buffer: run eagerly (this also sets kernel attributes), then
+      // capture the same sequence starting from buffer q for later replays
+      rc = advance_once(pool, p);
+      if (rc) return rc;
+      const int after = pool->cur;
+      const long long before = pool->launches;
+      pool->cur = q;
+      cudaGraph_t g = nullptr;
+      if (cudaStreamBeginCapture(pool->stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+        rc = advance_once(pool, p);
+        cudaError_t ce = cudaStreamEndCapture(pool->stream, &g);
+        if (rc == MAP_OK && ce == cudaSuccess && g) {
+          size_t nnodes = 0;
+          cudaGraphGetNodes(g, nullptr, &nnodes);
+          cudaGraphExec_t ex = nullptr;
+          if (cudaGraphInstantiate(&ex, g, 0) == cudaSuccess) {
+            pool->graph[q] = ex;
+            pool->graph_valid[q] = true;
+            pool->graph_kernels[q] = pool->launches - before;
+            (void)nnodes;
+          }
+        }
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+      }
+      pool->cur = after;
+      pool->launches = before;
+      if (rc) return rc;
+      continue;
+    }
+    CK(cudaGraphLaunch(pool->graph[q], pool->stream));
+    pool->launches += pool->graph_kernels[q];
+    pool->cur = 1 - q;
+  }
+  pool->have_dt = false;
+  return MAP_OK;
+}
+
+int map_check(map_pool* pool) {
+  if (!pool) return MAP_EINVAL;
+  unsigned e = 0;
+  CK(cudaMemcpyAsync(&e, pool->err_word, sizeof(unsigned), cudaMemcpyDeviceToHost, pool->stream));
+  CK(cudaMemsetAsync(pool->err_word, 0, sizeof(unsigned), pool->stream));
+  CK(cudaStreamSynchronize(pool->stream));
+  if (e & 1u) return fail(pool, MAP_ENONFINITE, "a leaf cell became non-finite");
+  if (e & 2u) return fail(pool, MAP_ENEGPRES, "a leaf cell has rho <= 0 or p < 0");
+  return MAP_OK;
+}
+
+int map_flag_refine(map_pool* pool, const map_params* p, const map_refine_params* r, int8_t* flags_out,
+                    double* est_out) {
+  if (!pool || !p || !r || !flags_out) return fail(pool, MAP_EINVAL, "null argument");
+  if (!pool->have_tree) return fail(pool, MAP_ESTATE, "no tree");
+  FlagLaunch F;
+  F.u = pool->buf[pool->cur];
+  F.blocks = pool->dt.leaf_ids;
+  F.nblocks = pool->tree.nleaves;
+  F.geo = pool->dt.geo;
+  F.gamma = p->gamma;
+  F.r = *r;
+  F.flags = pool->flags;
+  F.est = pool->est;
+  CK(DISPATCH(pool, flags, F));
+  CK(cudaMemcpyAsync(flags_out, pool->flags, pool->tree.nleaves, cudaMemcpyDeviceToHost, pool->stream));
+  if (est_out)
+    CK(cudaMemcpyAsync(est_out, pool->est, pool->tree.nleaves * sizeof(double), cudaMemcpyDeviceToHost, pool->stream));
+  CK(cudaStreamSynchronize(pool->stream));
+  return MAP_OK;
+}
+
+int map_regrid(map_pool* pool, const map_block_desc* leaves, int n) {
+  if (!pool || !leaves || n <= 0) return fail(pool, MAP_EINVAL, "null or empty leaf list");
+  if (!pool->have_tree) return fail(pool, MAP_ESTATE, "no tree");
+  HostTree t;
+  std::string why = build_tree(pool->ndim, pool->nb, pool->probs, leaves, n, t);
+  if (!why.empty()) return fail(pool, MAP_EINVAL, why);
+  if (t.nblocks > pool->max_blocks) return fail(pool, MAP_ENOMEM, "tree has more blocks than max_blocks");
+  std::vector<RegridTask> tasks;
+  why = build_regrid(pool->tree, t, tasks);
+  if (!why.empty()) return fail(pool, MAP_EINVAL, why);
+  if ((int)tasks.size() > pool->tasks_cap) {
+    cudaFree(pool->tasks);
+    pool->tasks = nullptr;
+    CK(cudaMalloc(&pool->tasks, tasks.size() * sizeof(RegridTask)));
+    pool->tasks_cap = (int)tasks.size();
+  }
+  CK(cudaMemcpyAsync(pool->tasks, tasks.data(), tasks.size() * sizeof(RegridTask), cudaMemcpyHostToDevice, pool->stream));
+  RegridLaunch R;
+  R.u_old = pool->buf[pool->cur];
+  R.u_new = pool->buf[1 - pool->cur];
+  R.tasks = pool->tasks;
+  R.ntasks = (int)tasks.size();
+  CK(DISPATCH(pool, regrid, R));
+  CK(cudaStreamSynchronize(pool->stream));
+  pool->cur = 1 - pool->cur;
+  return install_tree(pool, t);   // also clears alpha_ready
+}
+
+int map_conservation(map_pool* pool, double* sums_out) {
+  if (!pool || !sums_out) return fail(pool, MAP_EINVAL, "null argument");
+  if (!pool->have_tree) return fail(pool, MAP_ESTATE, "no tree");
+  CK(cudaMemsetAsync(pool->sums, 0, sizeof(double) * kNV * pool->nprob, pool->stream));
+  SumLaunch L;
+  L.u = pool->buf[pool->cur];
+  L.blocks = pool->dt.all_leaves;
+  L.nblocks = pool->tree.nleaves;
+  L.geo = pool->dt.geo;
+  L.sums = pool->sums;
+  CK(DISPATCH(pool, sums, L));
+  CK(cudaMemcpyAsync(sums_out, pool->sums, sizeof(double) * kNV * pool->nprob, cudaMemcpyDeviceToHost, pool->stream));
+  CK(cudaStreamSynchronize(pool->stream));
+  return MAP_OK;
+}
+
+int map_get_speeds(map_pool* pool, double* out) {
+  if (!pool || !out) return fail(pool, MAP_EINVAL, "null argument");
+  std::vector<ProbDyn> dyn(pool->nprob);
+  CK(cudaMemcpyAsync(dyn.data(), pool->dyn, sizeof(ProbDyn) * pool->nprob, cudaMemcpyDeviceToHost, pool->stream));
+  CK(cudaStreamSynchronize(pool->stream));
+  for (int q = 0; q < pool->nprob; ++q) {
+    out[5 * q + 0] = dyn[q].dt;
+    out[5 * q + 1] = dyn[q].ch;
+    out[5 * q + 2] = dyn[q].cp;
+    out[5 * q + 3] = dyn[q].damp;
+    out[5 * q + 4] = dyn[q].alpha_g;
+  }
+  return MAP_OK;
+}
+
+long long map_kernel_launches(const map_pool* pool) { return pool ? pool->launches : 0; }
+
+const char* map_last_error(const map_pool* pool) {
+  return pool ? pool->err.c_str() : g_create_error.c_str();
+}
+
+}  // extern "C"

@@ -1,0 +1,179 @@
+// kernels_impl.cuh -- launch dispatch over (ndim, block size, scheme, limiter, stage).
+// Included once per precision by kernels_f64.cu and kernels_f32.cu.
+#pragma once
+#include "aux.cuh"
+#include "step.cuh"
+
+namespace mapgb {
+
+template <typename T, int NDIM, int NB, int SCHEME, int LIM, int STAGE>
+cudaError_t launch_step_one(const StepLaunch& L, cudaStream_t s) {
+  const bool res = L.eta > 0.0;
+  const size_t smem = step_smem_bytes<T, NDIM, NB, SCHEME>(res);
+  auto kern = step_kernel<T, NDIM, NB, SCHEME, LIM, STAGE>;
+  static bool attr_done[2] = {false, false};
+  if (!attr_done[res]) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr_done[res] = true;
+  }
+  StepArgsT<T> A;
+  A.u_in = (const T*)L.u_in;
+  A.u_out = (T*)L.u_out;
+  A.u_base = (const T*)L.u_base;
+  A.blocks = L.blocks;
+  A.nblocks = L.nblocks;
+  A.geo = L.geo;
+  A.dyn = L.dyn;
+  A.gamma = (T)L.gamma;
+  A.gm1 = (T)(L.gamma - 1.0);
+  A.tau = (T)L.tau;
+  A.eta = L.eta;
+  A.eglm = L.eglm;
+  A.resistive = res ? 1 : 0;
+  A.err_word = L.err_word;
+  A.sums = L.sums;
+  A.dyn_next = L.dyn_next;
+  const int grid = L.grid > 0 ? (L.grid < L.nblocks ? L.grid : L.nblocks) : L.nblocks;
+  if (grid <= 0) return cudaSuccess;
+  kern<<<grid, NB * NB, smem, s>>>(A);
+  return cudaGetLastError();
+}
+
+template <typename T, int NDIM, int NB>
+cudaError_t launch_step_geo(const StepLaunch& L, cudaStream_t s) {
+  const int lim = L.limiter ? 1 : 0;
+  if (L.scheme == SCH_MMC)
+    return lim ? launch_step_one<T, NDIM, NB, SCH_MMC, 1, 0>(L, s) : launch_step_one<T, NDIM, NB, SCH_MMC, 0, 0>(L, s);
+  if (L.scheme == SCH_LF)
+    return lim ? launch_step_one<T, NDIM, NB, SCH_LF, 1, 0>(L, s) : launch_step_one<T, NDIM, NB, SCH_LF, 0, 0>(L, s);
+  if (L.stage == 1) return launch_step_one<T, NDIM, NB, SCH_WENO, 0, 1>(L, s);
+  return launch_step_one<T, NDIM, NB, SCH_WENO, 0, 2>(L, s);
+}
+
+#define MAPGB_GEO_DISPATCH(KC, CALL)                              \
+  do {                                                            \
+    if ((KC).ndim == 2 && (KC).nb == 16) { CALL(2, 16); }         \
+    if ((KC).ndim == 3 && (KC).nb == 16) { CALL(3, 16); }         \
+    if ((KC).ndim == 3 && (KC).nb == 8) { CALL(3, 8); }           \
+    if ((KC).ndim == 2 && (KC).nb == 8) { CALL(2, 8); }           \
+    return cudaErrorInvalidValue;                                 \
+  } while (0)
+
+inline int grid_for(int n) { return n < 1 ? 0 : n; }
+
+template <typename T>
+cudaError_t launch_step_T(const KernelConfig& kc, const StepLaunch& L, cudaStream_t s, long long* cnt) {
+  if (L.nblocks <= 0) return cudaSuccess;
+  if (cnt) ++*cnt;
+#define CALL_STEP(ND, NBV) return launch_step_geo<T, ND, NBV>(L, s)
+  MAPGB_GEO_DISPATCH(kc, CALL_STEP);
+#undef CALL_STEP
+}
+
+template <typename T>
+size_t step_smem_T(const KernelConfig& kc, int scheme, int res) {
+#define SM(ND, NBV)                                                                        \
+  return scheme == SCH_MMC ? step_smem_bytes<T, ND, NBV, SCH_MMC>(res)                     \
+                           : (scheme == SCH_LF ? step_smem_bytes<T, ND, NBV, SCH_LF>(res)  \
+                                               : step_smem_bytes<T, ND, NBV, SCH_WENO>(res))
+  if (kc.ndim == 2 && kc.nb == 16) { SM(2, 16); }
+  if (kc.ndim == 3 && kc.nb == 16) { SM(3, 16); }
+  if (kc.ndim == 3 && kc.nb == 8) { SM(3, 8); }
+  if (kc.ndim == 2 && kc.nb == 8) { SM(2, 8); }
+#undef SM
+  return 0;
+}
+
+template <typename T>
+cudaError_t launch_fill_T(const KernelConfig& kc, const FillLaunch& L, cudaStream_t s, long long* cnt) {
+  if (L.nblocks <= 0) return cudaSuccess;
+  if (cnt) ++*cnt;
+#define CALL_FILL(ND, NBV)                                                                   \
+  fill_kernel<T, ND, NBV><<<grid_for(L.nblocks), 256, 0, s>>>((T*)L.u, L.blocks, L.nblocks, L.regions); \
+  return cudaGetLastError()
+  MAPGB_GEO_DISPATCH(kc, CALL_FILL);
+#undef CALL_FILL
+}
+
+template <typename T>
+cudaError_t launch_restrict_T(const KernelConfig& kc, const RestrictLaunch& L, cudaStream_t s, long long* cnt) {
+  if (L.nparents <= 0) return cudaSuccess;
+  if (cnt) ++*cnt;
+#define CALL_RES(ND, NBV)                                                                          \
+  restrict_kernel<T, ND, NBV><<<grid_for(L.nparents), 256, 0, s>>>((T*)L.u, L.parents, L.nparents, L.children); \
+  return cudaGetLastError()
+  MAPGB_GEO_DISPATCH(kc, CALL_RES);
+#undef CALL_RES
+}
+
+template <typename T>
+cudaError_t launch_cfl_T(const KernelConfig& kc, const CflLaunch& L, cudaStream_t s, long long* cnt) {
+  if (L.nblocks <= 0) return cudaSuccess;
+  if (cnt) ++*cnt;
+#define CALL_CFL(ND, NBV)                                                                     \
+  cfl_kernel<T, ND, NBV><<<grid_for(L.nblocks), 256, 0, s>>>((const T*)L.u, L.blocks, L.nblocks, L.geo, L.dyn, \
+                                                             (T)L.gamma, (T)(L.gamma - 1.0)); \
+  return cudaGetLastError()
+  MAPGB_GEO_DISPATCH(kc, CALL_CFL);
+#undef CALL_CFL
+}
+
+template <typename T>
+cudaError_t launch_flags_T(const KernelConfig& kc, const FlagLaunch& L, cudaStream_t s, long long* cnt) {
+  if (L.nblocks <= 0) return cudaSuccess;
+  if (cnt) ++*cnt;
+#define CALL_FLAGS(ND, NBV)                                              \
+  flags_kernel<T, ND, NBV><<<grid_for(L.nblocks), 256, 0, s>>>(L);       \
+  return cudaGetLastError()
+  MAPGB_GEO_DISPATCH(kc, CALL_FLAGS);
+#undef CALL_FLAGS
+}
+
+template <typename T>
+cudaError_t launch_sums_T(const KernelConfig& kc, const SumLaunch& L, cudaStream_t s, long long* cnt) {
+  if (L.nblocks <= 0) return cudaSuccess;
+  if (cnt) ++*cnt;
+#define CALL_SUMS(ND, NBV)                                             \
+  sums_kernel<T, ND, NBV><<<grid_for(L.nblocks), 256, 0, s>>>(L);      \
+  return cudaGetLastError()
+  MAPGB_GEO_DISPATCH(kc, CALL_SUMS);
+#undef CALL_SUMS
+}
+
+template <typename T>
+cudaError_t launch_pack_T(const KernelConfig& kc, const PackLaunch& L, cudaStream_t s, long long* cnt) {
+  if (L.nblocks <= 0) return cudaSuccess;
+  if (cnt) ++*cnt;
+#define CALL_PACK(ND, NBV)                                             \
+  pack_kernel<T, ND, NBV><<<grid_for(L.nblocks), 256, 0, s>>>(L);      \
+  return cudaGetLastError()
+  MAPGB_GEO_DISPATCH(kc, CALL_PACK);
+#undef CALL_PACK
+}
+
+template <typename T>
+cudaError_t launch_regrid_T(const KernelConfig& kc, const RegridLaunch& L, cudaStream_t s, long long* cnt) {
+  if (L.ntasks <= 0) return cudaSuccess;
+  if (cnt) ++*cnt;
+#define CALL_REGRID(ND, NBV)                                            \
+  regrid_kernel<T, ND, NBV><<<grid_for(L.ntasks), 256, 0, s>>>(L);      \
+  return cudaGetLastError()
+  MAPGB_GEO_DISPATCH(kc, CALL_REGRID);
+#undef CALL_REGRID
+}
+
+}  // namespace mapgb
+
+#define MAPGB_DEFINE_LAUNCHERS(T, SUFFIX)                                                          \
+  namespace mapgb {                                                                                \
+  cudaError_t launch_step_##SUFFIX(const KernelConfig& k, const StepLaunch& l, cudaStream_t s, long long* c) { return launch_step_T<T>(k, l, s, c); } \
+  cudaError_t launch_fill_##SUFFIX(const KernelConfig& k, const FillLaunch& l, cudaStream_t s, long long* c) { return launch_fill_T<T>(k, l, s, c); } \
+  cudaError_t launch_restrict_##SUFFIX(const KernelConfig& k, const RestrictLaunch& l, cudaStream_t s, long long* c) { return launch_restrict_T<T>(k, l, s, c); } \
+  cudaError_t launch_cfl_##SUFFIX(const KernelConfig& k, const CflLaunch& l, cudaStream_t s, long long* c) { return launch_cfl_T<T>(k, l, s, c); } \
+  cudaError_t launch_flags_##SUFFIX(const KernelConfig& k, const FlagLaunch& l, cudaStream_t s, long long* c) { return launch_flags_T<T>(k, l, s, c); } \
+  cudaError_t launch_sums_##SUFFIX(const KernelConfig& k, const SumLaunch& l, cudaStream_t s, long long* c) { return launch_sums_T<T>(k, l, s, c); } \
+  cudaError_t launch_pack_##SUFFIX(const KernelConfig& k, const PackLaunch& l, cudaStream_t s, long long* c) { return launch_pack_T<T>(k, l, s, c); } \
+  cudaError_t launch_regrid_##SUFFIX(const KernelConfig& k, const RegridLaunch& l, cudaStream_t s, long long* c) { return launch_regrid_T<T>(k, l, s, c); } \
+  size_t step_smem_##SUFFIX(const KernelConfig& k, int scheme, int res) { return step_smem_T<T>(k, scheme, res); } \
+  }

@@ -1,0 +1,191 @@
+// map_internal.hpp -- internal types shared by the host runtime and the kernels.
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/map.h"
+
+namespace mapgb {
+
+constexpr int kNV = 9;
+constexpr int kNG = 2;
+
+// Per pool block: geometry of one block (leaf or parent).
+struct BlockGeo {
+  double dx[3];
+  int problem;
+  int level;
+  int leaf;        // caller leaf index or -1 for a parent
+  int pad;
+};
+
+// Per problem, device-resident step constants (written by the CFL reduction).
+struct ProbDyn {
+  double dt, ch, cp, damp, alpha_g, mindx;
+  unsigned long long alpha_bits;   // running max of alpha (as ordered bits, alpha >= 0)
+  unsigned long long pad;
+};
+
+// One ghost region of a leaf (3^ndim regions, region id = rx + 3 ry + 9 rz with
+// r = 0 low ghosts, 1 interior range, 2 high ghosts).  Per dimension the source index is
+// m*i + a (i = padded index in the destination block).
+//   kind 0 COPY:    src block interior/any cell at padded index (m*i + a)
+//   kind 1 PROLONG: fine global cell g = m*i + a; coarse padded = (g >> 1) - corg + NG,
+//                   offset sign from g & 1 (minmod-linear, Sec. 4.3)
+struct GhostRegion {
+  int kind;
+  int src;
+  int m[3];
+  int a[3];
+  int corg[3];
+  int pad;
+};
+
+// Regrid task for one new leaf (Sec. 4.3 interpolation on the interior).
+//   kind 0 copy interior of old block src
+//   kind 1 prolong from old leaf src; child bits in cb (x | y<<1 | z<<2)
+struct RegridTask {
+  int kind;
+  int src;
+  int dst;
+  int cb;
+};
+
+// Host-side tree built from the caller's leaves.
+struct HostTree {
+  int ndim = 0, nb = 0;
+  int nblocks = 0, nleaves = 0, maxlev = 0;
+  std::vector<int> leaf_to_block;           // caller leaf index -> pool block id
+  std::vector<BlockGeo> geo;                // per pool block
+  std::vector<int> blk_problem, blk_level, blk_ijk;  // ijk: 3 per block
+  std::vector<int> children;                // 8 per block (-1 if leaf)
+  std::vector<GhostRegion> regions;         // 27 per block (valid for leaves)
+  std::vector<std::vector<int>> leaves_by_level;   // pool ids
+  std::vector<std::vector<int>> parents_by_level;  // pool ids
+  std::vector<int> all_leaves;              // pool ids, Morton order
+  std::vector<double> mindx;                // per problem
+  std::vector<int> leaves_per_problem;
+  // lookup (problem, level, i, j, k) -> pool id
+  int find(int p, int L, int i, int j, int k) const;
+  std::vector<std::pair<unsigned long long, int>> keys;  // sorted packed keys -> id
+};
+
+// Build the tree; returns an empty string on success, else the reason.
+std::string build_tree(int ndim, int nb, const std::vector<map_problem_desc>& probs,
+                       const map_block_desc* leaves, int n, HostTree& t);
+
+// Regrid tasks from an old tree to a new one; empty string on success.
+std::string build_regrid(const HostTree& old_t, const HostTree& new_t,
+                         std::vector<RegridTask>& tasks);
+
+// ---------------------------------------------------------------------------------------
+// Kernel launchers (kernels_f64.cu / kernels_f32.cu).
+
+struct StepLaunch {
+  const void* u_in;        // state with ghosts
+  void* u_out;             // output state (interior written)
+  const void* u_base;      // WENO stage 2: u^n (interior read)
+  const int* blocks;       // pool ids to update
+  int nblocks;
+  const BlockGeo* geo;
+  const ProbDyn* dyn;
+  double gamma, eta, tau;
+  int eglm, scheme, limiter, stage;   // stage: 0 single (MMC/LF), 1 WENO stage 1, 2 WENO stage 2
+  unsigned* err_word;
+  double* sums;            // optional FP64 conservation sums [nprob][9] of the output
+  ProbDyn* dyn_next;       // optional: max alpha of the output into dyn_next[p].alpha_bits
+  int grid;                // CTAs (0 = one per block)
+};
+
+struct FillLaunch {
+  void* u;
+  const int* blocks;
+  int nblocks;
+  const GhostRegion* regions;
+};
+
+struct RestrictLaunch {
+  void* u;
+  const int* parents;
+  int nparents;
+  const int* children;     // 8 per pool block
+};
+
+struct CflLaunch {
+  const void* u;
+  const int* blocks;
+  int nblocks;
+  const BlockGeo* geo;
+  ProbDyn* dyn;
+  double gamma;
+};
+
+struct FinalizeLaunch {
+  ProbDyn* dyn;
+  int nprob;
+  int ndim;
+  double c_cfl, eta, ch_fixed, cp_fixed, c_d, dt_override;
+  int ch_mode, cp_mode;
+};
+
+struct FlagLaunch {
+  const void* u;
+  const int* blocks;       // leaves in caller order
+  int nblocks;
+  const BlockGeo* geo;
+  double gamma;
+  map_refine_params r;
+  int8_t* flags;
+  double* est;
+};
+
+struct SumLaunch {
+  const void* u;
+  const int* blocks;
+  int nblocks;
+  const BlockGeo* geo;
+  double* sums;            // [nprob][9], accumulated
+};
+
+struct PackLaunch {
+  void* u;                 // pool
+  double* host_layout;     // staging [n][9][nz][nb][nb]
+  const int* blocks;       // pool ids in caller leaf order
+  int nblocks;
+  int to_pool;             // 1: staging -> pool, 0: pool -> staging
+};
+
+struct RegridLaunch {
+  const void* u_old;
+  void* u_new;
+  const RegridTask* tasks;
+  int ntasks;
+};
+
+struct KernelConfig {
+  int ndim, nb;
+};
+
+// Returns cudaSuccess or the launch error; each adds the number of kernels launched.
+#define MAPGB_DECLARE_LAUNCHERS(SUFFIX)                                                  \
+  cudaError_t launch_step_##SUFFIX(const KernelConfig&, const StepLaunch&, cudaStream_t, long long*); \
+  cudaError_t launch_fill_##SUFFIX(const KernelConfig&, const FillLaunch&, cudaStream_t, long long*); \
+  cudaError_t launch_restrict_##SUFFIX(const KernelConfig&, const RestrictLaunch&, cudaStream_t, long long*); \
+  cudaError_t launch_cfl_##SUFFIX(const KernelConfig&, const CflLaunch&, cudaStream_t, long long*); \
+  cudaError_t launch_flags_##SUFFIX(const KernelConfig&, const FlagLaunch&, cudaStream_t, long long*); \
+  cudaError_t launch_sums_##SUFFIX(const KernelConfig&, const SumLaunch&, cudaStream_t, long long*); \
+  cudaError_t launch_pack_##SUFFIX(const KernelConfig&, const PackLaunch&, cudaStream_t, long long*); \
+  cudaError_t launch_regrid_##SUFFIX(const KernelConfig&, const RegridLaunch&, cudaStream_t, long long*); \
+  size_t step_smem_##SUFFIX(const KernelConfig&, int scheme, int resistive);
+
+MAPGB_DECLARE_LAUNCHERS(f64)
+MAPGB_DECLARE_LAUNCHERS(f32)
+
+cudaError_t launch_finalize(const FinalizeLaunch&, cudaStream_t, long long*);
+cudaError_t launch_zero_alpha(ProbDyn* dyn, int nprob, cudaStream_t, long long*);
+
+}  // namespace mapgb

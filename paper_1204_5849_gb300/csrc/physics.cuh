@@ -1,0 +1,166 @@
+// physics.cuh -- point-wise EGLM-MHD physics on the device, templated on the real type.
+//
+// Equations: Jiang, Fang & Chen (arXiv:1204.5849) Sec. 2, eqs. MHD-1..MHD-5; the local
+// speed |v_d| + fast magnetosonic speed (Sec. 3.1/3.2 "local maximum eigenvalue");
+// Lax-Friedrichs flux (Equ:LFFlux); minmod (eq. minmod) and van Leer limiters; the
+// two-stencil WENO reconstruction (Sec. 3.3).
+//
+// The double instantiation is compiled without FMA contraction and keeps one expression
+// order per formula, so that it rounds like a plain C implementation of the same formulas.
+// The float instantiation stores and computes in FP32; the pressure recovery falls back
+// to FP64 where the internal energy is a small fraction of e (cancellation).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace mapgb {
+
+constexpr int NV = 9;
+enum { RHO = 0, MX = 1, MY = 2, MZ = 3, BX = 4, BY = 5, BZ = 6, EN = 7, PSI = 8 };
+constexpr int NG = 2;
+
+template <typename T>
+struct Phys {
+  T gamma;
+  T gm1;       // gamma - 1
+  T ch;        // GLM speed c_h
+  T tau;       // FP64-fix threshold on e_int / e (float only)
+};
+
+template <typename T>
+__device__ __forceinline__ T dmax(T a, T b) { return a > b ? a : b; }
+
+// p = (gamma-1) (e - m^2/(2 rho) - B^2/2)   (Sec. 2, total energy density)
+template <typename T>
+__device__ __forceinline__ T pressure(const T* w, const Phys<T>& P) {
+  T m2 = w[MX] * w[MX] + w[MY] * w[MY] + w[MZ] * w[MZ];
+  T b2 = w[BX] * w[BX] + w[BY] * w[BY] + w[BZ] * w[BZ];
+  return P.gm1 * (w[EN] - T(0.5) * m2 / w[RHO] - T(0.5) * b2);
+}
+
+template <>
+__device__ __forceinline__ float pressure<float>(const float* w, const Phys<float>& P) {
+  float m2 = w[MX] * w[MX] + w[MY] * w[MY] + w[MZ] * w[MZ];
+  float b2 = w[BX] * w[BX] + w[BY] * w[BY] + w[BZ] * w[BZ];
+  float kin = 0.5f * m2 / w[RHO];
+  float eint = w[EN] - kin - 0.5f * b2;
+  if (eint < P.tau * w[EN]) {
+    // low internal-energy fraction: recover p in FP64 from the same stored values
+    double m2d = (double)w[MX] * w[MX] + (double)w[MY] * w[MY] + (double)w[MZ] * w[MZ];
+    double b2d = (double)w[BX] * w[BX] + (double)w[BY] * w[BY] + (double)w[BZ] * w[BZ];
+    double ed = (double)w[EN] - 0.5 * m2d / (double)w[RHO] - 0.5 * b2d;
+    return (float)((double)P.gm1 * ed);
+  }
+  return P.gm1 * eint;
+}
+
+// Physical flux in direction D of the EGLM-MHD system (eqs. MHD-1..MHD-5, no sources),
+// given the pressure p of the state.
+template <typename T, int D>
+__device__ __forceinline__ void flux_p(const T* w, T p, const Phys<T>& P, T* f) {
+  T rho = w[RHO];
+  T v0 = w[MX] / rho, v1 = w[MY] / rho, v2 = w[MZ] / rho;
+  T b2 = w[BX] * w[BX] + w[BY] * w[BY] + w[BZ] * w[BZ];
+  T pt = p + T(0.5) * b2;
+  T vb = v0 * w[BX] + v1 * w[BY] + v2 * w[BZ];
+  T vd = D == 0 ? v0 : (D == 1 ? v1 : v2);
+  T bd = w[BX + D];
+  T md = w[MX + D];
+  f[RHO] = md;
+  f[MX] = md * v0 - bd * w[BX];
+  f[MY] = md * v1 - bd * w[BY];
+  f[MZ] = md * v2 - bd * w[BZ];
+  f[MX + D] += pt;
+  f[BX] = D == 0 ? w[PSI] : vd * w[BX] - bd * v0;
+  f[BY] = D == 1 ? w[PSI] : vd * w[BY] - bd * v1;
+  f[BZ] = D == 2 ? w[PSI] : vd * w[BZ] - bd * v2;
+  f[EN] = vd * (w[EN] + pt) - bd * vb;
+  f[PSI] = P.ch * P.ch * bd;
+}
+
+// Local speed in direction D: |v_d| + c_f,d with the pressure clamped at 0 here only.
+template <typename T, int D>
+__device__ __forceinline__ T alpha_p(const T* w, T p, const Phys<T>& P) {
+  T rho = w[RHO];
+  if (p < T(0)) p = T(0);
+  T a2 = P.gamma * p / rho;
+  T b2 = (w[BX] * w[BX] + w[BY] * w[BY] + w[BZ] * w[BZ]) / rho;
+  T bd2 = w[BX + D] * w[BX + D] / rho;
+  T s = a2 + b2;
+  T disc = s * s - T(4) * a2 * bd2;
+  if (disc < T(0)) disc = T(0);
+  T cf = sqrt(T(0.5) * (s + sqrt(disc)));
+  return fabs(w[MX + D] / rho) + cf;
+}
+
+template <typename T>
+__device__ __forceinline__ T alpha_dir(int d, const T* w, T p, const Phys<T>& P) {
+  return d == 0 ? alpha_p<T, 0>(w, p, P) : (d == 1 ? alpha_p<T, 1>(w, p, P) : alpha_p<T, 2>(w, p, P));
+}
+
+// Dissipation speed of component v in direction D: the (B_d, psi) pair uses c_h.
+template <int D>
+__device__ __forceinline__ bool glm_pair(int v) { return v == BX + D || v == PSI; }
+
+// Lax-Friedrichs flux f_m(a,b) = (f(a) + f(b) - alpha (b - a))/2 (Equ:LFFlux),
+// alpha = max of the two states' local speeds; c_h for the (B_d, psi) pair.
+template <typename T, int D>
+__device__ __forceinline__ void lf_flux(const T* a, const T* b, const Phys<T>& P, T* f) {
+  T fa[NV], fb[NV];
+  T pa = pressure<T>(a, P), pb = pressure<T>(b, P);
+  flux_p<T, D>(a, pa, P, fa);
+  flux_p<T, D>(b, pb, P, fb);
+  T aa = alpha_p<T, D>(a, pa, P), ab = alpha_p<T, D>(b, pb, P);
+  T al = aa > ab ? aa : ab;
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    T s = glm_pair<D>(v) ? P.ch : al;
+    f[v] = T(0.5) * ((fa[v] + fb[v]) - s * (b[v] - a[v]));
+  }
+}
+
+// minmod(a,b) = sgn(a) max(0, min(|a|, sgn(a) b))
+template <typename T>
+__device__ __forceinline__ T minmod(T a, T b) {
+  if (a > T(0)) { T m = a < b ? a : b; return m > T(0) ? m : T(0); }
+  if (a < T(0)) { T m = -a < -b ? -a : -b; return m > T(0) ? -m : T(0); }
+  return T(0);
+}
+
+// limiter(a, b): 0 minmod, 1 van Leer (2ab/(a+b) when ab > 0, else 0)
+template <typename T, int LIM>
+__device__ __forceinline__ T limiter(T a, T b) {
+  if (LIM == 0) return minmod<T>(a, b);
+  return (a * b > T(0)) ? (T(2) * a * b) / (a + b) : T(0);
+}
+
+// WENO two-stencil reconstruction around u0 (Sec. 3.3): the left state of the face on
+// the + side and the right state of the face on the - side (denominator of the latter
+// read as a_{i+1/2} + 2 a_{i-1/2}).
+template <typename T>
+__device__ __forceinline__ void weno_faces(T um, T u0, T up, T& minus_right, T& plus_left) {
+  const T eps = T(1e-12);
+  T dp = up - u0, dm = u0 - um;
+  T ap = T(1) / ((eps + dp * dp) * (eps + dp * dp));
+  T am = T(1) / ((eps + dm * dm) * (eps + dm * dm));
+  T wm = T(0.5) * (u0 + up), vm = T(0.5) * (T(3) * u0 - um);
+  T wp = T(0.5) * (T(3) * u0 - up), vp = T(0.5) * (u0 + um);
+  minus_right = (T(2) * ap * wm + am * vm) / (T(2) * ap + am);
+  plus_left = (ap * wp + T(2) * am * vp) / (ap + T(2) * am);
+}
+
+template <typename T>
+__device__ __forceinline__ T weno_minus_right(T um, T u0, T up) {
+  T a, b;
+  weno_faces<T>(um, u0, up, a, b);
+  return a;
+}
+
+template <typename T>
+__device__ __forceinline__ T weno_plus_left(T um, T u0, T up) {
+  T a, b;
+  weno_faces<T>(um, u0, up, a, b);
+  return b;
+}
+
+}  // namespace mapgb

@@ -1,0 +1,351 @@
+// tree.cpp -- host-side block tree: Morton ordering, validation, ghost-fill and regrid
+// tables (Sec. 4.1 hierarchical structure; Sec. 4.3 boundary conditions).
+//
+// The paper keeps a replicated linked list of blocks in Hilbert order with parent/child/
+// neighbour pointers (Table 1).  Here the tree lives on the host as flat arrays indexed by
+// pool block id: leaves first in Morton order (problem, then interleaved coordinates at the
+// finest level), then parents.  For each leaf the 3^ndim ghost regions are resolved once
+// into a source block and an affine index map, so the device fill is a pure gather.
+#include <algorithm>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "map_internal.hpp"
+
+namespace mapgb {
+
+namespace {
+
+unsigned long long pack_key(int p, int L, int i, int j, int k) {
+  return ((unsigned long long)p << 50) | ((unsigned long long)L << 45) |
+         ((unsigned long long)k << 30) | ((unsigned long long)j << 15) | (unsigned long long)i;
+}
+
+unsigned long long spread3(unsigned long long x) {
+  // bit q of x -> bit 3q
+  unsigned long long r = 0;
+  for (int q = 0; q < 21; ++q) r |= ((x >> q) & 1ull) << (3 * q);
+  return r;
+}
+
+unsigned long long morton(int ndim, int i, int j, int k) {
+  if (ndim == 2) {
+    unsigned long long r = 0;
+    for (int q = 0; q < 31; ++q) {
+      r |= ((unsigned long long)((i >> q) & 1) << (2 * q));
+      r |= ((unsigned long long)((j >> q) & 1) << (2 * q + 1));
+    }
+    return r;
+  }
+  return spread3(i) | (spread3(j) << 1) | (spread3(k) << 2);
+}
+
+struct Node {
+  int p, L, ijk[3];
+  bool leaf;
+  int caller;  // caller leaf index
+};
+
+std::string fmt(const char* what, int p, int L, const int* ijk) {
+  char buf[160];
+  snprintf(buf, sizeof buf, "%s: problem %d level %d block (%d,%d,%d)", what, p, L, ijk[0], ijk[1], ijk[2]);
+  return buf;
+}
+
+}  // namespace
+
+int HostTree::find(int p, int L, int i, int j, int k) const {
+  if (i < 0 || j < 0 || k < 0 || i >= (1 << 15) || j >= (1 << 15) || k >= (1 << 15)) return -1;
+  unsigned long long key = pack_key(p, L, i, j, k);
+  auto it = std::lower_bound(keys.begin(), keys.end(), std::make_pair(key, -1));
+  if (it != keys.end() && it->first == key) return it->second;
+  return -1;
+}
+
+std::string build_tree(int ndim, int nb, const std::vector<map_problem_desc>& probs,
+                       const map_block_desc* leaves, int n, HostTree& t) {
+  t = HostTree();
+  t.ndim = ndim;
+  t.nb = nb;
+  const int np = (int)probs.size();
+  if (n <= 0) return "empty leaf list";
+  if (np > 4000) return "too many problems";
+  for (int p = 0; p < np; ++p)
+    for (int d = 0; d < 3; ++d) {
+      if (d < ndim && (probs[p].nbase[d] < 1 || !(probs[p].hi[d] > probs[p].lo[d])))
+        return "bad problem box";
+      if (d < ndim && (probs[p].bc[d][0] < 0 || probs[p].bc[d][0] > 1 || probs[p].bc[d][1] < 0 ||
+                       probs[p].bc[d][1] > 1))
+        return "bad boundary kind";
+      if (d < ndim && ((probs[p].bc[d][0] == MAP_BC_PERIODIC) != (probs[p].bc[d][1] == MAP_BC_PERIODIC)))
+        return "periodic boundaries must pair";
+    }
+
+  std::vector<Node> nodes;
+  std::vector<std::pair<unsigned long long, int>> keys;
+  nodes.reserve((size_t)n * 2);
+  for (int l = 0; l < n; ++l) {
+    Node nd;
+    nd.p = leaves[l].problem;
+    nd.L = leaves[l].level;
+    for (int d = 0; d < 3; ++d) nd.ijk[d] = d < ndim ? leaves[l].ijk[d] : 0;
+    nd.leaf = true;
+    nd.caller = l;
+    if (nd.p < 0 || nd.p >= np || nd.L < 0 || nd.L > 12) return fmt("bad leaf", nd.p, nd.L, nd.ijk);
+    for (int d = 0; d < ndim; ++d) {
+      int nblk = probs[nd.p].nbase[d] << nd.L;
+      if (nd.ijk[d] < 0 || nd.ijk[d] >= nblk || nblk > (1 << 15)) return fmt("leaf out of range", nd.p, nd.L, nd.ijk);
+    }
+    if (nd.L > t.maxlev) t.maxlev = nd.L;
+    keys.push_back({pack_key(nd.p, nd.L, nd.ijk[0], nd.ijk[1], nd.ijk[2]), (int)nodes.size()});
+    nodes.push_back(nd);
+  }
+  std::sort(keys.begin(), keys.end());
+  for (size_t q = 1; q < keys.size(); ++q)
+    if (keys[q].first == keys[q - 1].first) return fmt("duplicate leaf", nodes[keys[q].second].p,
+                                                       nodes[keys[q].second].L, nodes[keys[q].second].ijk);
+  // ancestors
+  std::vector<std::pair<unsigned long long, int>> anc;
+  for (int l = 0; l < n; ++l) {
+    Node c = nodes[l];
+    while (c.L > 0) {
+      c.L -= 1;
+      for (int d = 0; d < 3; ++d) c.ijk[d] >>= 1;
+      anc.push_back({pack_key(c.p, c.L, c.ijk[0], c.ijk[1], c.ijk[2]), l});
+    }
+  }
+  std::sort(anc.begin(), anc.end());
+  for (size_t q = 0; q < anc.size(); ++q) {
+    if (q > 0 && anc[q].first == anc[q - 1].first) continue;
+    auto it = std::lower_bound(keys.begin(), keys.end(), std::make_pair(anc[q].first, -1));
+    if (it != keys.end() && it->first == anc[q].first) {
+      const Node& lf = nodes[it->second];
+      return fmt("leaf contains another leaf", lf.p, lf.L, lf.ijk);
+    }
+    Node c;
+    unsigned long long k = anc[q].first;
+    c.p = (int)(k >> 50);
+    c.L = (int)((k >> 45) & 31);
+    c.ijk[2] = (int)((k >> 30) & 32767);
+    c.ijk[1] = (int)((k >> 15) & 32767);
+    c.ijk[0] = (int)(k & 32767);
+    c.leaf = false;
+    c.caller = -1;
+    nodes.push_back(c);
+  }
+  // pool order: leaves by (problem, Morton at the finest level), then parents by level
+  std::vector<int> order(nodes.size());
+  for (size_t q = 0; q < nodes.size(); ++q) order[q] = (int)q;
+  const int ML = t.maxlev;
+  auto mkey = [&](const Node& a) {
+    int s = ML - a.L;
+    return morton(ndim, a.ijk[0] << s, a.ijk[1] << s, a.ijk[2] << s);
+  };
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+    const Node& a = nodes[x];
+    const Node& b = nodes[y];
+    if (a.leaf != b.leaf) return a.leaf;
+    if (a.p != b.p) return a.p < b.p;
+    if (!a.leaf && a.L != b.L) return a.L > b.L;
+    unsigned long long ma = mkey(a), mb = mkey(b);
+    if (ma != mb) return ma < mb;
+    return a.L < b.L;
+  });
+  const int NB = (int)nodes.size();
+  t.nblocks = NB;
+  t.nleaves = n;
+  t.leaf_to_block.assign(n, -1);
+  t.geo.resize(NB);
+  t.blk_problem.resize(NB);
+  t.blk_level.resize(NB);
+  t.blk_ijk.resize((size_t)NB * 3);
+  t.children.assign((size_t)NB * 8, -1);
+  t.keys.clear();
+  t.keys.reserve(NB);
+  for (int id = 0; id < NB; ++id) {
+    const Node& a = nodes[order[id]];
+    t.blk_problem[id] = a.p;
+    t.blk_level[id] = a.L;
+    for (int d = 0; d < 3; ++d) t.blk_ijk[3 * id + d] = a.ijk[d];
+    BlockGeo g;
+    for (int d = 0; d < 3; ++d) {
+      int ncell = d < ndim ? (probs[a.p].nbase[d] << a.L) * nb : 1;
+      g.dx[d] = (probs[a.p].hi[d] - probs[a.p].lo[d]) / (double)ncell;
+    }
+    g.problem = a.p;
+    g.level = a.L;
+    g.leaf = a.leaf ? a.caller : -1;
+    g.pad = 0;
+    t.geo[id] = g;
+    if (a.leaf) t.leaf_to_block[a.caller] = id;
+    t.keys.push_back({pack_key(a.p, a.L, a.ijk[0], a.ijk[1], a.ijk[2]), id});
+  }
+  std::sort(t.keys.begin(), t.keys.end());
+  // parent/child links and completeness
+  for (int id = 0; id < NB; ++id) {
+    int L = t.blk_level[id];
+    if (L == 0) continue;
+    const int* c = &t.blk_ijk[3 * id];
+    int par = t.find(t.blk_problem[id], L - 1, c[0] >> 1, c[1] >> 1, c[2] >> 1);
+    if (par < 0) return "internal error: missing parent";
+    int cb = (c[0] & 1) | ((c[1] & 1) << 1) | ((c[2] & 1) << 2);
+    t.children[(size_t)par * 8 + cb] = id;
+  }
+  for (int id = n; id < NB; ++id)
+    for (int cb = 0; cb < (1 << ndim); ++cb)
+      if (t.children[(size_t)id * 8 + cb] < 0)
+        return fmt("incomplete parent (a child is missing)", t.blk_problem[id], t.blk_level[id], &t.blk_ijk[3 * id]);
+  for (int p = 0; p < np; ++p) {
+    int nz = ndim == 3 ? probs[p].nbase[2] : 1;
+    for (int k = 0; k < nz; ++k)
+      for (int j = 0; j < probs[p].nbase[1]; ++j)
+        for (int i = 0; i < probs[p].nbase[0]; ++i)
+          if (t.find(p, 0, i, j, k) < 0) {
+            int ijk[3] = {i, j, k};
+            return fmt("domain not covered", p, 0, ijk);
+          }
+  }
+  // 2:1 balance over faces, edges and corners
+  for (int id = 0; id < n; ++id) {
+    int p = t.blk_problem[id], L = t.blk_level[id];
+    const int* c = &t.blk_ijk[3 * id];
+    for (int oz = (ndim == 3 ? -1 : 0); oz <= (ndim == 3 ? 1 : 0); ++oz)
+      for (int oy = -1; oy <= 1; ++oy)
+        for (int ox = -1; ox <= 1; ++ox) {
+          if (!ox && !oy && !oz) continue;
+          int off[3] = {ox, oy, oz}, q[3] = {0, 0, 0};
+          bool outside = false;
+          for (int d = 0; d < ndim; ++d) {
+            int nblk = probs[p].nbase[d] << L;
+            q[d] = c[d] + off[d];
+            if (q[d] < 0 || q[d] >= nblk) {
+              if (probs[p].bc[d][q[d] < 0 ? 0 : 1] == MAP_BC_PERIODIC) q[d] = (q[d] + nblk) % nblk;
+              else outside = true;
+            }
+          }
+          if (outside) continue;
+          int nbid = t.find(p, L, q[0], q[1], q[2]);
+          if (nbid >= 0) {
+            if (nbid < n) continue;
+            for (int cb = 0; cb < (1 << ndim); ++cb) {
+              bool touch = true;
+              for (int d = 0; d < ndim; ++d) {
+                int bit = (cb >> d) & 1;
+                if (off[d] == 1 && bit != 0) touch = false;
+                if (off[d] == -1 && bit != 1) touch = false;
+              }
+              if (touch && t.children[(size_t)nbid * 8 + cb] >= n)
+                return fmt("2:1 balance violated (finer by two levels)", p, L, c);
+            }
+          } else {
+            int cq = L > 0 ? t.find(p, L - 1, q[0] >> 1, q[1] >> 1, q[2] >> 1) : -1;
+            if (cq < 0 || cq >= n) return fmt("2:1 balance violated (coarser by two levels)", p, L, c);
+          }
+        }
+  }
+  // ghost regions of every leaf
+  t.regions.assign((size_t)NB * 27, GhostRegion{});
+  for (int id = 0; id < n; ++id) {
+    int p = t.blk_problem[id], L = t.blk_level[id];
+    const int* c = &t.blk_ijk[3 * id];
+    for (int rz = 0; rz < 3; ++rz)
+      for (int ry = 0; ry < 3; ++ry)
+        for (int rx = 0; rx < 3; ++rx) {
+          if (ndim == 2 && rz != 1) continue;
+          int r[3] = {rx, ry, rz};
+          int m[3] = {1, 1, 1}, A[3] = {0, 0, 0}, T[3] = {0, 0, 0}, rep[3] = {0, 0, 0};
+          for (int d = 0; d < ndim; ++d) {
+            int N = (probs[p].nbase[d] << L) * nb;
+            int nblk = probs[p].nbase[d] << L;
+            int O = c[d] * nb;
+            int irep = r[d] == 0 ? 0 : (r[d] == 1 ? kNG : kNG + nb);
+            if (r[d] == 1) {
+              m[d] = 1; A[d] = O - kNG; T[d] = c[d];
+            } else {
+              int nbk = c[d] + (r[d] == 0 ? -1 : 1);
+              if (nbk >= 0 && nbk < nblk) {
+                m[d] = 1; A[d] = O - kNG; T[d] = nbk;
+              } else if (probs[p].bc[d][r[d] == 0 ? 0 : 1] == MAP_BC_PERIODIC) {
+                m[d] = 1; A[d] = O - kNG + (r[d] == 0 ? N : -N); T[d] = (nbk + nblk) % nblk;
+              } else {
+                m[d] = 0; A[d] = r[d] == 0 ? 0 : N - 1; T[d] = c[d];
+              }
+            }
+            rep[d] = m[d] * irep + A[d];
+          }
+          GhostRegion g{};
+          int src = t.find(p, L, T[0], T[1], T[2]);
+          if (src >= 0) {
+            g.kind = 0;
+            g.src = src;
+            for (int d = 0; d < 3; ++d) {
+              g.m[d] = d < ndim ? m[d] : 1;
+              g.a[d] = d < ndim ? A[d] - T[d] * nb + kNG : 0;
+              g.corg[d] = 0;
+            }
+          } else {
+            int Tc[3] = {0, 0, 0};
+            for (int d = 0; d < ndim; ++d) Tc[d] = (rep[d] >> 1) / nb;
+            int cs = L > 0 ? t.find(p, L - 1, Tc[0], Tc[1], Tc[2]) : -1;
+            if (cs < 0 || cs >= n) return fmt("no coarse source for a ghost region", p, L, c);
+            g.kind = 1;
+            g.src = cs;
+            for (int d = 0; d < 3; ++d) {
+              g.m[d] = d < ndim ? m[d] : 1;
+              g.a[d] = d < ndim ? A[d] : 0;
+              g.corg[d] = d < ndim ? Tc[d] * nb : 0;
+            }
+          }
+          t.regions[(size_t)id * 27 + rx + 3 * ry + 9 * rz] = g;
+        }
+  }
+  // level lists, per-problem minimum spacing
+  t.leaves_by_level.assign(t.maxlev + 1, {});
+  t.parents_by_level.assign(t.maxlev + 1, {});
+  t.all_leaves.resize(n);
+  t.mindx.assign(np, 1e300);
+  t.leaves_per_problem.assign(np, 0);
+  for (int id = 0; id < NB; ++id) {
+    int L = t.blk_level[id];
+    if (id < n) {
+      t.leaves_by_level[L].push_back(id);
+      t.all_leaves[id] = id;
+      int p = t.blk_problem[id];
+      t.leaves_per_problem[p]++;
+      for (int d = 0; d < ndim; ++d) t.mindx[p] = std::min(t.mindx[p], t.geo[id].dx[d]);
+    } else {
+      t.parents_by_level[L].push_back(id);
+    }
+  }
+  for (int p = 0; p < np; ++p)
+    if (t.leaves_per_problem[p] == 0) return "a problem has no leaves";
+  return "";
+}
+
+std::string build_regrid(const HostTree& o, const HostTree& nw, std::vector<RegridTask>& tasks) {
+  tasks.clear();
+  for (int id = 0; id < nw.nleaves; ++id) {
+    int p = nw.blk_problem[id], L = nw.blk_level[id];
+    const int* c = &nw.blk_ijk[3 * id];
+    RegridTask tk{};
+    tk.dst = id;
+    int same = o.find(p, L, c[0], c[1], c[2]);
+    if (same >= 0) {
+      tk.kind = 0;
+      tk.src = same;
+      tk.cb = 0;
+    } else {
+      int par = L > 0 ? o.find(p, L - 1, c[0] >> 1, c[1] >> 1, c[2] >> 1) : -1;
+      if (par < 0 || par >= o.nleaves)
+        return fmt("regrid: a new leaf is neither old, nor a child of an old leaf", p, L, c);
+      tk.kind = 1;
+      tk.src = par;
+      tk.cb = (c[0] & 1) | ((c[1] & 1) << 1) | ((c[2] & 1) << 2);
+    }
+    tasks.push_back(tk);
+  }
+  return "";
+}
+
+}  // namespace mapgb
