@@ -168,8 +168,9 @@ int map_step(map_pool* pool, const map_params* p);
  * starting buffer into a CUDA graph and replayed.  map_get_speeds reads the last dt. */
 int map_advance(map_pool* pool, const map_params* p, int nsteps);
 
-/* Device error word accumulated by the steps since the last check (ρ <= 0, p < 0,
- * non-finite), read and cleared; synchronises.  MAP_OK, MAP_ENONFINITE or MAP_ENEGPRES. */
+/* Device error word accumulated by the steps since the last check (rho <= 0, p < 0,
+ * non-finite, a bounded wait for a plane copy that gave up), read and cleared;
+ * synchronises.  MAP_OK, MAP_ETIMEOUT, MAP_ENONFINITE or MAP_ENEGPRES. */
 int map_check(map_pool* pool);
 
 /* Refinement flags (Sec. 4.5): per leaf +1 refine, 0 keep, -1 may coarsen, from the

@@ -24,7 +24,7 @@ NVCC_COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", IN
 
 UNITS = {
     "kernels_f64.cu": ["-fmad=false"],
-    "kernels_f32.cu": [],
+    "kernels_f32.cu": ["-ftz=true", "-prec-div=false", "-prec-sqrt=false"],
     "common.cu": ["-fmad=false"],
 }
 CPP_UNITS = ["tree.cpp", "capi.cpp"]

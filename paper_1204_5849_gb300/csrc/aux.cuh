@@ -11,10 +11,48 @@ namespace mapgb {
 // block its region resolves to -- a copy from a same-level block, or the conservative
 // minmod prolongation of the covering coarser leaf (whose ghosts an earlier level pass
 // filled).  Region tables come from the host tree.
+template <int NDIM, int NB>
+struct Shell {
+  static constexpr int NP = NB + 4;
+  static constexpr int P2 = NP * NP;
+  static constexpr int PLANE_GHOSTS = P2 - NB * NB;                  // ghost cells of an interior plane
+  static constexpr int COUNT = NDIM == 3 ? 2 * NG * P2 + NB * PLANE_GHOSTS : PLANE_GHOSTS;
+  // g-th ghost cell of a block -> padded (i, j, k): the 2*NG full ghost planes first (3D),
+  // then per interior plane its NG ghost rows on each side and NG ghost columns on each side
+  static __device__ __forceinline__ void cell(int g, int& i, int& j, int& k) {
+    if (NDIM == 3) {
+      if (g < 2 * NG * P2) {
+        const int pl = g / P2, c = g % P2;
+        k = pl < NG ? pl : NB + pl;
+        j = c / NP;
+        i = c % NP;
+        return;
+      }
+      g -= 2 * NG * P2;
+      k = NG + g / PLANE_GHOSTS;
+      g %= PLANE_GHOSTS;
+    } else {
+      k = 0;
+    }
+    constexpr int ROWS = 2 * NG * NP;          // full ghost rows of the plane
+    if (g < ROWS) {
+      const int r = g / NP;
+      j = r < NG ? r : NB + r;
+      i = g % NP;
+    } else {
+      g -= ROWS;                                // NB interior rows x 2*NG ghost columns
+      j = NG + g / (2 * NG);
+      const int q = g % (2 * NG);
+      i = q < NG ? q : NB + q;
+    }
+  }
+};
+
 template <typename T, int NDIM, int NB>
 __global__ void __launch_bounds__(256) fill_kernel(T* __restrict__ u, const int* __restrict__ blocks,
                                                    int n, const GhostRegion* __restrict__ regions) {
   using G = Geo<NDIM, NB>;
+  using SH = Shell<NDIM, NB>;
   constexpr int NP = G::NP, P2 = G::P2, S = G::S;
   __shared__ GhostRegion reg[27];
   for (int bi = blockIdx.x; bi < n; bi += gridDim.x) {
@@ -23,25 +61,29 @@ __global__ void __launch_bounds__(256) fill_kernel(T* __restrict__ u, const int*
     for (int r = threadIdx.x; r < 27; r += blockDim.x) reg[r] = regions[(size_t)blk * 27 + r];
     __syncthreads();
     T* ub = u + (size_t)blk * NV * S;
-    for (int c = threadIdx.x; c < S; c += blockDim.x) {
-      const int i = c % NP, j = (c / NP) % NP, k = NDIM == 3 ? c / P2 : 0;
+    for (int g = threadIdx.x; g < SH::COUNT; g += blockDim.x) {
+      int i, j, k;
+      SH::cell(g, i, j, k);
+      const int c = (k * NP + j) * NP + i;
       const int rx = i < NG ? 0 : (i >= NG + NB ? 2 : 1);
       const int ry = j < NG ? 0 : (j >= NG + NB ? 2 : 1);
       const int rz = NDIM == 3 ? (k < NG ? 0 : (k >= NG + NB ? 2 : 1)) : 1;
-      if (rx == 1 && ry == 1 && rz == 1) continue;
-      const GhostRegion& g = reg[rx + 3 * ry + 9 * rz];
-      const T* sb = u + (size_t)g.src * NV * S;
-      if (g.kind == 0) {
-        const int si = g.m[0] * i + g.a[0], sj = g.m[1] * j + g.a[1];
-        const int sk = NDIM == 3 ? g.m[2] * k + g.a[2] : 0;
+      const GhostRegion& gr = reg[rx + 3 * ry + 9 * rz];
+      const T* sb = u + (size_t)gr.src * NV * S;
+      if (gr.kind == 0) {
+        const int si = gr.m[0] * i + gr.a[0], sj = gr.m[1] * j + gr.a[1];
+        const int sk = NDIM == 3 ? gr.m[2] * k + gr.a[2] : 0;
         const int sc = (sk * NP + sj) * NP + si;
+        T val[NV];
 #pragma unroll
-        for (int v = 0; v < NV; ++v) ub[(size_t)v * S + c] = sb[(size_t)v * S + sc];
+        for (int v = 0; v < NV; ++v) val[v] = sb[(size_t)v * S + sc];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) ub[(size_t)v * S + c] = val[v];
       } else {
-        const int gi = g.m[0] * i + g.a[0], gj = g.m[1] * j + g.a[1];
-        const int gk = NDIM == 3 ? g.m[2] * k + g.a[2] : 0;
-        const int ci = (gi >> 1) - g.corg[0] + NG, cj = (gj >> 1) - g.corg[1] + NG;
-        const int ck = NDIM == 3 ? (gk >> 1) - g.corg[2] + NG : 0;
+        const int gi = gr.m[0] * i + gr.a[0], gj = gr.m[1] * j + gr.a[1];
+        const int gk = NDIM == 3 ? gr.m[2] * k + gr.a[2] : 0;
+        const int ci = (gi >> 1) - gr.corg[0] + NG, cj = (gj >> 1) - gr.corg[1] + NG;
+        const int ck = NDIM == 3 ? (gk >> 1) - gr.corg[2] + NG : 0;
         const int cc = (ck * NP + cj) * NP + ci;
         const T ox = (gi & 1) ? T(0.25) : T(-0.25);
         const T oy = (gj & 1) ? T(0.25) : T(-0.25);

@@ -575,6 +575,7 @@ int map_check(map_pool* pool) {
   CK(cudaMemcpyAsync(&e, pool->err_word, sizeof(unsigned), cudaMemcpyDeviceToHost, pool->stream));
   CK(cudaMemsetAsync(pool->err_word, 0, sizeof(unsigned), pool->stream));
   CK(cudaStreamSynchronize(pool->stream));
+  if (e & 4u) return fail(pool, MAP_ETIMEOUT, "a bounded device wait for a plane copy gave up");
   if (e & 1u) return fail(pool, MAP_ENONFINITE, "a leaf cell became non-finite");
   if (e & 2u) return fail(pool, MAP_ENEGPRES, "a leaf cell has rho <= 0 or p < 0");
   return MAP_OK;

@@ -13,6 +13,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 namespace mapgb {
 
 constexpr int NV = 9;
@@ -42,7 +44,7 @@ template <>
 __device__ __forceinline__ float pressure<float>(const float* w, const Phys<float>& P) {
   float m2 = w[MX] * w[MX] + w[MY] * w[MY] + w[MZ] * w[MZ];
   float b2 = w[BX] * w[BX] + w[BY] * w[BY] + w[BZ] * w[BZ];
-  float kin = 0.5f * m2 / w[RHO];
+  float kin = 0.5f * m2 * (1.0f / w[RHO]);
   float eint = w[EN] - kin - 0.5f * b2;
   if (eint < P.tau * w[EN]) {
     // low internal-energy fraction: recover p in FP64 from the same stored values
@@ -59,7 +61,13 @@ __device__ __forceinline__ float pressure<float>(const float* w, const Phys<floa
 template <typename T, int D>
 __device__ __forceinline__ void flux_p(const T* w, T p, const Phys<T>& P, T* f) {
   T rho = w[RHO];
-  T v0 = w[MX] / rho, v1 = w[MY] / rho, v2 = w[MZ] / rho;
+  T v0, v1, v2;
+  if constexpr (std::is_same<T, float>::value) {
+    const T ir = T(1) / rho;   // one reciprocal per state in FP32
+    v0 = w[MX] * ir; v1 = w[MY] * ir; v2 = w[MZ] * ir;
+  } else {
+    v0 = w[MX] / rho; v1 = w[MY] / rho; v2 = w[MZ] / rho;
+  }
   T b2 = w[BX] * w[BX] + w[BY] * w[BY] + w[BZ] * w[BZ];
   T pt = p + T(0.5) * b2;
   T vb = v0 * w[BX] + v1 * w[BY] + v2 * w[BZ];
@@ -83,14 +91,26 @@ template <typename T, int D>
 __device__ __forceinline__ T alpha_p(const T* w, T p, const Phys<T>& P) {
   T rho = w[RHO];
   if (p < T(0)) p = T(0);
-  T a2 = P.gamma * p / rho;
-  T b2 = (w[BX] * w[BX] + w[BY] * w[BY] + w[BZ] * w[BZ]) / rho;
-  T bd2 = w[BX + D] * w[BX + D] / rho;
-  T s = a2 + b2;
-  T disc = s * s - T(4) * a2 * bd2;
-  if (disc < T(0)) disc = T(0);
-  T cf = sqrt(T(0.5) * (s + sqrt(disc)));
-  return fabs(w[MX + D] / rho) + cf;
+  if constexpr (std::is_same<T, float>::value) {
+    const T ir = T(1) / rho;
+    T a2 = P.gamma * p * ir;
+    T b2 = (w[BX] * w[BX] + w[BY] * w[BY] + w[BZ] * w[BZ]) * ir;
+    T bd2 = w[BX + D] * w[BX + D] * ir;
+    T s = a2 + b2;
+    T disc = s * s - T(4) * a2 * bd2;
+    if (disc < T(0)) disc = T(0);
+    T cf = sqrtf(T(0.5) * (s + sqrtf(disc)));
+    return fabsf(w[MX + D] * ir) + cf;
+  } else {
+    T a2 = P.gamma * p / rho;
+    T b2 = (w[BX] * w[BX] + w[BY] * w[BY] + w[BZ] * w[BZ]) / rho;
+    T bd2 = w[BX + D] * w[BX + D] / rho;
+    T s = a2 + b2;
+    T disc = s * s - T(4) * a2 * bd2;
+    if (disc < T(0)) disc = T(0);
+    T cf = sqrt(T(0.5) * (s + sqrt(disc)));
+    return fabs(w[MX + D] / rho) + cf;
+  }
 }
 
 template <typename T>

@@ -53,20 +53,23 @@ struct Geo {
   static constexpr int NZ = NDIM == 3 ? NP : 1;
   static constexpr int S = NZ * P2;
   static constexpr int NT = NB * NB;
-  static constexpr int UPL = NDIM == 3 ? 4 : 1;
-  static constexpr int WPL = NDIM == 3 ? 3 : 1;   // u~ and J planes
-  static constexpr int RING = (NB + 2) * (NB + 2);
+  static constexpr int UPL = NDIM == 3 ? 4 : 1;   // u planes z..z+2 and one in flight
+  static constexpr int WPL = NDIM == 3 ? 3 : 1;   // u~ and J planes z-1..z+1
+  static constexpr int RW = NB + 2;               // ring row width (padded 1..NB+2)
+  static constexpr int RING = RW * RW;
   static constexpr int NFACE = NB * (NB + 1);
 };
 
 template <typename T, int NDIM, int NB, int SCHEME>
 __host__ __device__ constexpr size_t step_smem_bytes(bool resistive) {
   using G = Geo<NDIM, NB>;
-  size_t n = (size_t)G::UPL * NV * G::P2;                          // u window
-  if (SCHEME != SCH_WENO) n += (size_t)G::WPL * NV * G::P2;        // u~ window
-  n += (size_t)NV * G::NFACE;                                       // face fluxes
-  if (resistive) n += (size_t)G::WPL * 3 * G::P2;                   // J window
-  return n * sizeof(T);
+  size_t n = (size_t)G::UPL * NV * G::P2;                          // u window (full planes)
+  if (SCHEME != SCH_WENO) n += (size_t)G::WPL * NV * G::RING;      // u~ window (ring)
+  size_t nf = (size_t)2 * NV * G::NFACE;                            // x and y face fluxes
+  if (nf < (size_t)(NV + 1) * 32 * 2) nf = (size_t)(NV + 1) * 32 * 2;  // reused for reductions
+  n += nf;
+  if (resistive) n += (size_t)G::WPL * 3 * G::RING;                 // J window (ring)
+  return 256 + n * sizeof(T);                                       // 256 B: mbarriers, block constants
 }
 
 // ---- small helpers on shared-memory planes -----------------------------------------
@@ -243,226 +246,475 @@ __device__ __forceinline__ void mmc_face(const T* w0, const T* w1, const T* w2, 
   }
 }
 
+// ---- bulk-copy (TMA) helpers -----------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint64_t* bar, unsigned parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+
+// Bounded wait on an mbarrier phase: gives up after ~2^31 clock cycles (about a second).
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity) {
+  const long long t0 = clock64();
+  while (!mbar_try(bar, parity)) {
+    if (clock64() - t0 > (1ll << 31)) return false;
+  }
+  return true;
+}
+
+// EGLM sources at cell c of a centre plane given with its variable stride PS and row stride
+// RS; the z-neighbours of the same column come as states zm (z-1) and zp (z+1).
+template <typename T, int NDIM>
+__device__ __forceinline__ void eglm_src_col(const T* pc, int PS, int RS, int c, const T* zm, const T* zp,
+                                             const T* dx2, T* s) {
+  T divb = T(0);
+  divb += (pc[BX * PS + c + 1] - pc[BX * PS + c - 1]) / dx2[0];
+  divb += (pc[BY * PS + c + RS] - pc[BY * PS + c - RS]) / dx2[1];
+  if (NDIM == 3) divb += (zp[BZ] - zm[BZ]) / dx2[2];
+  T bg = T(0);
+  bg += pc[BX * PS + c] * ((pc[PSI * PS + c + 1] - pc[PSI * PS + c - 1]) / dx2[0]);
+  bg += pc[BY * PS + c] * ((pc[PSI * PS + c + RS] - pc[PSI * PS + c - RS]) / dx2[1]);
+  if (NDIM == 3) bg += pc[BZ * PS + c] * ((zp[PSI] - zm[PSI]) / dx2[2]);
+  s[MX] += -divb * pc[BX * PS + c];
+  s[MY] += -divb * pc[BY * PS + c];
+  s[MZ] += -divb * pc[BZ * PS + c];
+  s[EN] += -bg;
+}
+
+// Resistive sources at the own column (Sec. 3.5).  J: centre plane jc (ring layout, index
+// cj) and the column's J at z-1 / z+1 (jzm, jzp); B: centre plane uc (full layout, index
+// cu) and the column's states at z-1 / z+1 (bzm, bzp).
+template <typename T, int NDIM, int NP, int RW>
+__device__ __forceinline__ void resist_src_col(const T* jc, int cj, const T* jzm, const T* jzp, const T* uc, int cu,
+                                               const T* bzm, const T* bzp, const T* dx2, T eta, T* s) {
+  constexpr int PJ = RW * RW, PU = NP * NP;
+  auto cdJ = [&](int comp, int d) -> T {
+    if (d >= NDIM) return T(0);
+    if (d == 0) return (jc[comp * PJ + cj + 1] - jc[comp * PJ + cj - 1]) / dx2[0];
+    if (d == 1) return (jc[comp * PJ + cj + RW] - jc[comp * PJ + cj - RW]) / dx2[1];
+    return (jzp[comp] - jzm[comp]) / dx2[2];
+  };
+  T rx = eta * cdJ(1, 2) - eta * cdJ(2, 1);
+  T ry = eta * cdJ(2, 0) - eta * cdJ(0, 2);
+  T rz = eta * cdJ(0, 1) - eta * cdJ(1, 0);
+  T re = T(0);
+#pragma unroll
+  for (int d = 0; d < NDIM; ++d) {
+    T q[2];
+#pragma unroll
+    for (int sg = 0; sg < 2; ++sg) {
+      T Bx, By, Bz, Jx, Jy, Jz;
+      if (d < 2) {
+        const int oj = d == 0 ? (sg ? 1 : -1) : (sg ? RW : -RW);
+        const int ou = d == 0 ? (sg ? 1 : -1) : (sg ? NP : -NP);
+        Bx = uc[BX * PU + cu + ou]; By = uc[BY * PU + cu + ou]; Bz = uc[BZ * PU + cu + ou];
+        Jx = jc[0 * PJ + cj + oj]; Jy = jc[1 * PJ + cj + oj]; Jz = jc[2 * PJ + cj + oj];
+      } else {
+        const T* bb = sg ? bzp : bzm;
+        const T* jj = sg ? jzp : jzm;
+        Bx = bb[BX]; By = bb[BY]; Bz = bb[BZ];
+        Jx = jj[0]; Jy = jj[1]; Jz = jj[2];
+      }
+      T t;
+      if (d == 0) t = Jz * By - Jy * Bz;
+      else if (d == 1) t = Jx * Bz - Jz * Bx;
+      else t = Jy * Bx - Jx * By;
+      q[sg] = eta * t;
+    }
+    re += (q[1] - q[0]) / dx2[d];
+  }
+  s[BX] += rx;
+  s[BY] += ry;
+  s[BZ] += rz;
+  s[EN] += re;
+}
+
 // ---- the kernel --------------------------------------------------------------------------
+//
+// 3D z-march with a window of three resident u planes (z..z+2) plus one plane in flight:
+// plane z+3 is fetched by bulk copies (cp.async.bulk, completion on an mbarrier) while
+// plane z is computed.  Every z-direction stencil (z faces, z derivatives of the sources)
+// runs along a thread's own column, so the column's state at z-1 is carried in registers
+// and no fourth resident plane is needed.  u~ and J live in ring layout (padded 1..NB+2).
+// Per plane, the predictor of plane z+1 and the x and y faces of plane z form one
+// warp-aligned work list (they touch different slots), so a plane costs three barriers.
+
+template <int N>
+struct Pad32 { static constexpr int value = (N + 31) / 32 * 32; };
+
+// a + b as an unevaluated pair (hi, lo) (TwoSum, Knuth)
+template <typename T>
+__device__ __forceinline__ void two_sum_acc(T& hi, T& lo, T h2, T l2) {
+  const T s = hi + h2;
+  const T bp = s - hi;
+  const T err = (hi - (s - bp)) + (h2 - bp);
+  lo = lo + l2 + err;
+  hi = s;
+}
 
 template <typename T, int NDIM, int NB, int SCHEME, int LIM, int STAGE>
-__global__ void __launch_bounds__(NB * NB, (sizeof(T) == 4 && NDIM == 3 && NB == 16) ? 2 : 1)
+__global__ void __launch_bounds__(NB * NB, sizeof(T) == 4 ? (NB == 16 ? 2 : 8) : 1)
 step_kernel(StepArgsT<T> A) {
   using G = Geo<NDIM, NB>;
   constexpr int NP = G::NP, P2 = G::P2, NZ = G::NZ, S = G::S, NT = G::NT;
-  constexpr int UPL = G::UPL, WPL = G::WPL;
+  constexpr int UPL = G::UPL, WPL = G::WPL, RW = G::RW, RING = G::RING, NFACE = G::NFACE;
   constexpr bool HAS_T = SCHEME != SCH_WENO;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* su = reinterpret_cast<T*>(smem_raw);
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw);           // UPL mbarriers
+  volatile int* status = reinterpret_cast<volatile int*>(smem_raw + 48);
+  T* kc = reinterpret_cast<T*>(smem_raw + 64);                       // block constants
+  T* su = reinterpret_cast<T*>(smem_raw + 256);
   T* sut = su + (size_t)UPL * NV * P2;
-  T* sf = sut + (HAS_T ? (size_t)WPL * NV * P2 : 0);
-  T* sj = sf + (size_t)NV * G::NFACE;
+  T* sf = sut + (HAS_T ? (size_t)WPL * NV * RING : 0);
+  size_t nf = (size_t)2 * NV * NFACE;
+  if (nf < (size_t)(NV + 1) * 32 * 2) nf = (size_t)(NV + 1) * 32 * 2;
+  T* sj = sf + nf;
 
   const int tid = threadIdx.x;
   const int tx = tid % NB, ty = tid / NB;
-  const int cown = (ty + NG) * NP + (tx + NG);
+  const int cown = (ty + NG) * NP + (tx + NG);          // own column, full plane layout
+  const int rown = (ty + 1) * RW + (tx + 1);            // own column, ring layout
 
-  double alpha_max = 0.0;
-  double csum[NV];
+  if (tid == 0) {
+    for (int q = 0; q < UPL; ++q) mbar_init(&bars[q], 1);
+    *status = 0;
+    fence_mbar_init();
+  }
+  __syncthreads();
+  unsigned phase = 0;                                   // parity bit per u slot
+  unsigned inflight = 0;                                // thread 0: slots with copies in flight
+
+  // fused diagnostics: the running alpha maximum is exact in T; the sums of a thread's
+  // column are Kahan-compensated in T and promoted to FP64 once per block
+  T alpha_max = T(0);
+  T csum[NV], ccmp[NV];
 #pragma unroll
-  for (int v = 0; v < NV; ++v) csum[v] = 0.0;
+  for (int v = 0; v < NV; ++v) { csum[v] = T(0); ccmp[v] = T(0); }
   unsigned errbits = 0;
 
   for (int bi = blockIdx.x; bi < A.nblocks; bi += gridDim.x) {
     const int blk = A.blocks[bi];
     const BlockGeo gg = A.geo[blk];
-    const ProbDyn dy = A.dyn[gg.problem];
-    Phys<T> P;
-    P.gamma = A.gamma;
-    P.gm1 = A.gm1;
-    P.ch = (T)dy.ch;
-    P.tau = A.tau;
-    const double dtd = dy.dt;
-    const T dt = (T)dtd;
-    T lam[3], lamh[3], dx2[3], dxT[3];
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      lam[d] = (T)(dtd / gg.dx[d]);
-      lamh[d] = (T)((0.5 * dtd) / gg.dx[d]);
-      dx2[d] = (T)(2.0 * gg.dx[d]);
-      dxT[d] = (T)gg.dx[d];
+    if (tid == 0) {
+      // per-block constants, computed once in FP64 and rounded to T
+      const ProbDyn dy = A.dyn[gg.problem];
+      for (int d = 0; d < 3; ++d) {
+        kc[d] = (T)(dy.dt / gg.dx[d]);
+        kc[3 + d] = (T)((0.5 * dy.dt) / gg.dx[d]);
+        kc[6 + d] = (T)(2.0 * gg.dx[d]);
+        kc[9 + d] = (T)gg.dx[d];
+      }
+      kc[12] = (T)dy.dt;
+      kc[13] = (T)(0.5 * dy.dt);
+      kc[14] = (T)dy.damp;
+      kc[15] = (T)dy.ch;
     }
-    const T damp = (T)dy.damp;
-    const T eta = (T)A.eta;
     const T* ub = A.u_in + (size_t)blk * NV * S;
     T* ob = A.u_out + (size_t)blk * NV * S;
     const T* bb = (STAGE == 2) ? A.u_base + (size_t)blk * NV * S : nullptr;
     const bool RES = A.resistive != 0;
+    const T eta = (T)A.eta;
 
     auto uslot = [&](int z) -> T* { return su + (size_t)(NDIM == 3 ? (z & 3) : 0) * NV * P2; };
-    auto tslot = [&](int z) -> T* { return sut + (size_t)(NDIM == 3 ? (z % 3) : 0) * NV * P2; };
-    auto jslot = [&](int z) -> T* { return sj + (size_t)(NDIM == 3 ? (z % 3) : 0) * 3 * P2; };
+    auto tslot = [&](int z) -> T* { return sut + (size_t)(NDIM == 3 ? (z % 3) : 0) * NV * RING; };
+    auto jslot = [&](int z) -> T* { return sj + (size_t)(NDIM == 3 ? (z % 3) : 0) * 3 * RING; };
 
-    auto load_plane = [&](int z) {
-      T* dst = uslot(z);
-      const T* src = ub + (size_t)z * P2;
+    // issue the bulk copies of u plane z into its slot (thread 0 only)
+    auto issue_plane = [&](int z) {
+      const int q = NDIM == 3 ? (z & 3) : 0;
+      fence_async_smem();
+      inflight |= 1u << q;
+      mbar_expect_tx(&bars[q], (unsigned)(NV * P2 * sizeof(T)));
 #pragma unroll 1
-      for (int v = 0; v < NV; ++v) {
-        const T* s = src + (size_t)v * NZ * P2;
-        T* d = dst + v * P2;
-        for (int c = tid; c < P2; c += NT) d[c] = s[c];
+      for (int v = 0; v < NV; ++v)
+        bulk_g2s(uslot(z) + v * P2, ub + ((size_t)v * NZ + z) * P2, (unsigned)(P2 * sizeof(T)), &bars[q]);
+    };
+    // wait for u plane z (thread 0 waits with a bound, the CTA follows via the barrier);
+    // returns false on timeout
+    auto wait_plane = [&](int z) -> bool {
+      const int q = NDIM == 3 ? (z & 3) : 0;
+      if (tid == 0) {
+        if (mbar_wait_bounded(&bars[q], (phase >> q) & 1u)) inflight &= ~(1u << q);
+        else *status = 1;
       }
+      __syncthreads();
+      const bool good = *status == 0;
+      if (good) phase ^= 1u << q;
+      return good;
     };
 
-    // u~ (MMC/LF) and J (resistive) on the ring of plane z (needs u planes z-1..z+1)
-    auto predict_plane = [&](int z) {
+    // the block constants are valid after the first barrier of the block
+    Phys<T> P;
+    T lam[3], lamh[3], dx2[3], dxT[3], dt, hdt, damp;
+    auto read_constants = [&]() {
+      P.gamma = A.gamma;
+      P.gm1 = A.gm1;
+      P.tau = A.tau;
+      P.ch = kc[15];
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        lam[d] = kc[d];
+        lamh[d] = kc[3 + d];
+        dx2[d] = kc[6 + d];
+        dxT[d] = kc[9 + d];
+      }
+      dt = kc[12];
+      hdt = kc[13];
+      damp = kc[14];
+    };
+
+    // u~ (MMC/LF) and J (resistive) at ring cell r of plane z (needs u planes z-1..z+1)
+    auto predict_cell = [&](int z, int r) {
       const T* ul[3] = {uslot(z - 1), uslot(z), uslot(z + 1)};
-      T* tp = tslot(z);
-      for (int r = tid; r < G::RING; r += NT) {
-        const int x = 1 + r % (NB + 2), y = 1 + r / (NB + 2);
-        const int c = y * NP + x;
-        if (HAS_T) {
-          T w[NV], acc[NV];
-          ldw<T, P2>(ul[1], c, w);
+      const int x = 1 + r % RW, y = 1 + r / RW;
+      const int c = y * NP + x;
+      if (HAS_T) {
+        T w[NV], acc[NV];
+        ldw<T, P2>(ul[1], c, w);
 #pragma unroll
-          for (int v = 0; v < NV; ++v) acc[v] = w[v];
-          if (SCHEME == SCH_MMC) {
-            T wm[NV], wp[NV], hp[NV], hm[NV];
-            // x
-            ldw<T, P2>(ul[1], c - 1, wm);
-            ldw<T, P2>(ul[1], c + 1, wp);
-            mmc_h<T, 0>(w, wp, P, hp);
-            mmc_h<T, 0>(wm, w, P, hm);
+        for (int v = 0; v < NV; ++v) acc[v] = w[v];
+        T* tp = tslot(z);
+        if (SCHEME == SCH_MMC) {
+          T wm[NV], wp[NV], hp[NV], hm[NV];
+          ldw<T, P2>(ul[1], c - 1, wm);
+          ldw<T, P2>(ul[1], c + 1, wp);
+          mmc_h<T, 0>(w, wp, P, hp);
+          mmc_h<T, 0>(wm, w, P, hm);
 #pragma unroll
-            for (int v = 0; v < NV; ++v) acc[v] -= lam[0] * (hp[v] - hm[v]);
-            // y
-            ldw<T, P2>(ul[1], c - NP, wm);
-            ldw<T, P2>(ul[1], c + NP, wp);
-            mmc_h<T, 1>(w, wp, P, hp);
-            mmc_h<T, 1>(wm, w, P, hm);
+          for (int v = 0; v < NV; ++v) acc[v] -= lam[0] * (hp[v] - hm[v]);
+          ldw<T, P2>(ul[1], c - NP, wm);
+          ldw<T, P2>(ul[1], c + NP, wp);
+          mmc_h<T, 1>(w, wp, P, hp);
+          mmc_h<T, 1>(wm, w, P, hm);
 #pragma unroll
-            for (int v = 0; v < NV; ++v) acc[v] -= lam[1] * (hp[v] - hm[v]);
-            if (NDIM == 3) {
-              ldw<T, P2>(ul[0], c, wm);
-              ldw<T, P2>(ul[2], c, wp);
-              mmc_h<T, 2>(w, wp, P, hp);
-              mmc_h<T, 2>(wm, w, P, hm);
+          for (int v = 0; v < NV; ++v) acc[v] -= lam[1] * (hp[v] - hm[v]);
+          if (NDIM == 3) {
+            ldw<T, P2>(ul[0], c, wm);
+            ldw<T, P2>(ul[2], c, wp);
+            mmc_h<T, 2>(w, wp, P, hp);
+            mmc_h<T, 2>(wm, w, P, hm);
 #pragma unroll
-              for (int v = 0; v < NV; ++v) acc[v] -= lam[2] * (hp[v] - hm[v]);
-            }
-#pragma unroll
-            for (int v = 0; v < NV; ++v) tp[v * P2 + c] = acc[v];
-          } else {
-            // LF: MUSCL-Hancock half step
-            T a[NV], b[NV], fa[NV], fb[NV];
-            auto half = [&](auto Dc, const T* plm, int cm, const T* plp, int cp) {
-              constexpr int D = decltype(Dc)::value;
-#pragma unroll
-              for (int v = 0; v < NV; ++v) {
-                T ph = limiter<T, LIM>(w[v] - plm[v * P2 + cm], plp[v * P2 + cp] - w[v]);
-                a[v] = w[v] + T(0.5) * ph;
-                b[v] = w[v] - T(0.5) * ph;
-              }
-              flux_p<T, D>(a, pressure<T>(a, P), P, fa);
-              flux_p<T, D>(b, pressure<T>(b, P), P, fb);
-#pragma unroll
-              for (int v = 0; v < NV; ++v) acc[v] -= lamh[D] * (fa[v] - fb[v]);
-            };
-            half(std::integral_constant<int, 0>(), ul[1], c - 1, ul[1], c + 1);
-            half(std::integral_constant<int, 1>(), ul[1], c - NP, ul[1], c + NP);
-            if (NDIM == 3) half(std::integral_constant<int, 2>(), ul[0], c, ul[2], c);
-            T s[NV];
-#pragma unroll
-            for (int v = 0; v < NV; ++v) s[v] = T(0);
-            if (A.eglm) eglm_src<T, NDIM, NP>(ul, c, dx2, s);
-            const T hdt = (T)(0.5 * dtd);
-#pragma unroll
-            for (int v = 0; v < NV; ++v) tp[v * P2 + c] = acc[v] + hdt * s[v];
+            for (int v = 0; v < NV; ++v) acc[v] -= lam[2] * (hp[v] - hm[v]);
           }
+#pragma unroll
+          for (int v = 0; v < NV; ++v) tp[v * RING + r] = acc[v];
+        } else {
+          T a[NV], b[NV], fa[NV], fb[NV];
+          auto half = [&](auto Dc, const T* plm, int cm, const T* plp, int cp) {
+            constexpr int D = decltype(Dc)::value;
+#pragma unroll
+            for (int v = 0; v < NV; ++v) {
+              T ph = limiter<T, LIM>(w[v] - plm[v * P2 + cm], plp[v * P2 + cp] - w[v]);
+              a[v] = w[v] + T(0.5) * ph;
+              b[v] = w[v] - T(0.5) * ph;
+            }
+            flux_p<T, D>(a, pressure<T>(a, P), P, fa);
+            flux_p<T, D>(b, pressure<T>(b, P), P, fb);
+#pragma unroll
+            for (int v = 0; v < NV; ++v) acc[v] -= lamh[D] * (fa[v] - fb[v]);
+          };
+          half(std::integral_constant<int, 0>(), ul[1], c - 1, ul[1], c + 1);
+          half(std::integral_constant<int, 1>(), ul[1], c - NP, ul[1], c + NP);
+          if (NDIM == 3) half(std::integral_constant<int, 2>(), ul[0], c, ul[2], c);
+          T s[NV];
+#pragma unroll
+          for (int v = 0; v < NV; ++v) s[v] = T(0);
+          if (A.eglm) eglm_src<T, NDIM, NP>(ul, c, dx2, s);
+#pragma unroll
+          for (int v = 0; v < NV; ++v) tp[v * RING + r] = acc[v] + hdt * s[v];
         }
-        if (RES) {
-          T J[3];
-          current<T, NDIM, NP>(ul, c, dx2, J);
-          T* jp = jslot(z);
-          jp[0 * P2 + c] = J[0];
-          jp[1 * P2 + c] = J[1];
-          jp[2 * P2 + c] = J[2];
-        }
+      }
+      if (RES) {
+        T J[3];
+        current<T, NDIM, NP>(ul, c, dx2, J);
+        T* jp = jslot(z);
+        jp[0 * RING + r] = J[0];
+        jp[1 * RING + r] = J[1];
+        jp[2 * RING + r] = J[2];
       }
     };
 
-    // face flux between cell cl (planes/offsets given) and its + neighbour in direction D
-    auto face_flux = [&](auto Dc, const T* const* up, const T* const* tp, int c0, int st, T* F) {
-      // up[k], tp[k]: plane pointers of cells i-1, i, i+1, i+2 (k = 0..3) along D;
-      // cell index in its plane = c0 + (k-1)*st (st = 0 for D = 2)
+    // x (D=0) or y (D=1) face flux between in-plane cells cl and cl+st (full layout), with
+    // the u~ ring cells rl and rl+rs
+    auto face_xy = [&](auto Dc, const T* up, const T* tp, int cl, int st, int rl, int rs, T* F) {
       constexpr int D = decltype(Dc)::value;
-      const int cm = c0 - st, c1 = c0, c2 = c0 + st, c3 = c0 + 2 * st;
       if (SCHEME == SCH_MMC) {
         T w0[NV], w1[NV], w2[NV], w3[NV], t0[NV], t1[NV];
-        ldw<T, P2>(up[0], cm, w0);
-        ldw<T, P2>(up[1], c1, w1);
-        ldw<T, P2>(up[2], c2, w2);
-        ldw<T, P2>(up[3], c3, w3);
-        ldw<T, P2>(tp[1], c1, t0);
-        ldw<T, P2>(tp[2], c2, t1);
+        ldw<T, P2>(up, cl - st, w0);
+        ldw<T, P2>(up, cl, w1);
+        ldw<T, P2>(up, cl + st, w2);
+        ldw<T, P2>(up, cl + 2 * st, w3);
+        ldw<T, RING>(tp, rl, t0);
+        ldw<T, RING>(tp, rl + rs, t1);
         mmc_face<T, D, LIM>(w0, w1, w2, w3, t0, t1, P, F);
-      } else if (SCHEME == SCH_LF) {
-        T a[NV], b[NV];
-#pragma unroll
-        for (int v = 0; v < NV; ++v) {
-          const T um = up[0][v * P2 + cm], u1 = up[1][v * P2 + c1];
-          const T u2 = up[2][v * P2 + c2], u3 = up[3][v * P2 + c3];
-          T phl = limiter<T, LIM>(u1 - um, u2 - u1);
-          T phr = limiter<T, LIM>(u2 - u1, u3 - u2);
-          a[v] = tp[1][v * P2 + c1] + T(0.5) * phl;
-          b[v] = tp[2][v * P2 + c2] - T(0.5) * phr;
-        }
-        lf_flux<T, D>(a, b, P, F);
       } else {
         T a[NV], b[NV];
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
-          const T um = up[0][v * P2 + cm], u1 = up[1][v * P2 + c1];
-          const T u2 = up[2][v * P2 + c2], u3 = up[3][v * P2 + c3];
-          a[v] = weno_minus_right<T>(um, u1, u2);
-          b[v] = weno_plus_left<T>(u1, u2, u3);
+          const T um = up[v * P2 + cl - st], u1 = up[v * P2 + cl];
+          const T u2 = up[v * P2 + cl + st], u3 = up[v * P2 + cl + 2 * st];
+          if (SCHEME == SCH_LF) {
+            T phl = limiter<T, LIM>(u1 - um, u2 - u1);
+            T phr = limiter<T, LIM>(u2 - u1, u3 - u2);
+            a[v] = tp[v * RING + rl] + T(0.5) * phl;
+            b[v] = tp[v * RING + rl + rs] - T(0.5) * phr;
+          } else {
+            a[v] = weno_minus_right<T>(um, u1, u2);
+            b[v] = weno_plus_left<T>(u1, u2, u3);
+          }
         }
         lf_flux<T, D>(a, b, P, F);
       }
     };
 
-    // z-face flux of the own column between planes z and z+1
-    auto zface = [&](int z, T* F) {
-      const T* up[4] = {uslot(z - 1), uslot(z), uslot(z + 1), uslot(z + 2)};
-      const T* tp[4] = {nullptr, HAS_T ? tslot(z) : nullptr, HAS_T ? tslot(z + 1) : nullptr, nullptr};
-      face_flux(std::integral_constant<int, 2>(), up, tp, cown, 0, F);
+    // x face f (fx = f % (NB+1), row = f / (NB+1)) or y face f (col = f % NB, fy = f / NB)
+    // of plane z into the face buffer (x faces first, then y faces)
+    T* sfx = sf;
+    T* sfy = sf + (size_t)NV * NFACE;
+    auto do_xface = [&](int z, int f) {
+      const int row = f / (NB + 1), fx = f % (NB + 1);
+      T F[NV];
+      face_xy(std::integral_constant<int, 0>(), uslot(z), HAS_T ? tslot(z) : nullptr, (row + NG) * NP + fx + 1, 1,
+              (row + 1) * RW + fx, 1, F);
+#pragma unroll
+      for (int v = 0; v < NV; ++v) sfx[v * NFACE + f] = F[v];
+    };
+    auto do_yface = [&](int z, int f) {
+      const int fy = f / NB, col = f % NB;
+      T F[NV];
+      face_xy(std::integral_constant<int, 1>(), uslot(z), HAS_T ? tslot(z) : nullptr, (fy + 1) * NP + col + NG, NP,
+              fy * RW + col + 1, RW, F);
+#pragma unroll
+      for (int v = 0; v < NV; ++v) sfy[v * NFACE + f] = F[v];
     };
 
-    T Fzlo[NV];
+    // z face of the own column between planes z and z+1; um1 = the column's state at z-1
+    auto face_z = [&](int z, const T* um1, T* F) {
+      const T* p0 = uslot(z);
+      const T* p1 = uslot(z + 1);
+      const T* p2 = uslot(z + 2);
+      if (SCHEME == SCH_MMC) {
+        T w1[NV], w2[NV], w3[NV], t0[NV], t1[NV];
+        ldw<T, P2>(p0, cown, w1);
+        ldw<T, P2>(p1, cown, w2);
+        ldw<T, P2>(p2, cown, w3);
+        ldw<T, RING>(tslot(z), rown, t0);
+        ldw<T, RING>(tslot(z + 1), rown, t1);
+        mmc_face<T, 2, LIM>(um1, w1, w2, w3, t0, t1, P, F);
+      } else {
+        T a[NV], b[NV];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+          const T um = um1[v], u1 = p0[v * P2 + cown], u2 = p1[v * P2 + cown], u3 = p2[v * P2 + cown];
+          if (SCHEME == SCH_LF) {
+            T phl = limiter<T, LIM>(u1 - um, u2 - u1);
+            T phr = limiter<T, LIM>(u2 - u1, u3 - u2);
+            a[v] = tslot(z)[v * RING + rown] + T(0.5) * phl;
+            b[v] = tslot(z + 1)[v * RING + rown] - T(0.5) * phr;
+          } else {
+            a[v] = weno_minus_right<T>(um, u1, u2);
+            b[v] = weno_plus_left<T>(u1, u2, u3);
+          }
+        }
+        lf_flux<T, 2>(a, b, P, F);
+      }
+    };
+
+    // work list of one barrier interval: [predictor ring cells of plane zp (if any)] then
+    // [x faces of plane zf] then [y faces of plane zf], each padded to whole warps
+    constexpr int PW = Pad32<RING>::value, FW = Pad32<NFACE>::value;
+    auto work = [&](int zp, bool do_pred, int zf, bool do_faces) {
+      const int npred = do_pred ? PW : 0;
+      const int total = npred + (do_faces ? 2 * FW : 0);
+      for (int it = tid; it < total; it += NT) {
+        if (it < npred) {
+          if (it < RING) predict_cell(zp, it);
+        } else if (it < npred + FW) {
+          const int f = it - npred;
+          if (f < NFACE) do_xface(zf, f);
+        } else {
+          const int f = it - npred - FW;
+          if (f < NFACE) do_yface(zf, f);
+        }
+      }
+    };
+
+    T Fzlo[NV], uprev[NV];
     int zbeg = 0, zend = 1;
+    bool ok = true;
+    const bool PRED = HAS_T || RES;
     if (NDIM == 3) {
-      for (int z = 0; z < 4; ++z) load_plane(z);
+      if (tid == 0) {
+        issue_plane(0);
+        issue_plane(1);
+        issue_plane(2);
+        issue_plane(3);
+      }
+      ok = ok && wait_plane(0);
+      ok = ok && wait_plane(1);
+      ok = ok && wait_plane(2);
+      if (ok) {
+        read_constants();
+        if (PRED) work(1, true, 0, false);
+      }
+      ok = ok && wait_plane(3);
+      if (ok && PRED) work(2, true, 0, false);
       __syncthreads();
-      if (HAS_T || RES) {
-        predict_plane(1);
-        predict_plane(2);
+      if (ok) {
+        ldw<T, P2>(uslot(0), cown, uprev);
+        face_z(1, uprev, Fzlo);
+        ldw<T, P2>(uslot(1), cown, uprev);
       }
       __syncthreads();
-      zface(1, Fzlo);
-      __syncthreads();
+      if (ok && tid == 0) issue_plane(4);
       zbeg = NG;
       zend = NB + NG;
     } else {
-      load_plane(0);
-      __syncthreads();
-      if (HAS_T || RES) predict_plane(0);
+      if (tid == 0) issue_plane(0);
+      ok = wait_plane(0);
+      if (ok) {
+        read_constants();
+        if (PRED) work(0, true, 0, false);
+      }
       __syncthreads();
     }
+    if (!ok) break;
 
     for (int z = zbeg; z < zend; ++z) {
       if (NDIM == 3) {
-        // window: u planes z-1..z+2, u~ and J planes z-1..z+1
-        load_plane(z + 2);
-        __syncthreads();
-        if (HAS_T || RES) predict_plane(z + 1);
-        __syncthreads();
+        // planes z, z+1 resident; z+2 in flight since the previous iteration
+        if (!wait_plane(z + 2)) { ok = false; break; }
+        if (tid == 0 && z + 3 <= NP - 1) issue_plane(z + 3);   // into the slot of z-1
+        work(z + 1, PRED, z, true);                            // predictor z+1, faces of z
+      } else {
+        work(0, false, 0, true);
       }
+      __syncthreads();
       const T* P0 = uslot(z);
+      const T* T0 = HAS_T ? tslot(z) : nullptr;
       T acc[NV];
       if (SCHEME == SCH_WENO) {
 #pragma unroll
@@ -470,55 +722,24 @@ step_kernel(StepArgsT<T> A) {
       } else {
         ldw<T, P2>(P0, cown, acc);
       }
-      // x faces of the plane
-      {
-        const T* up[4] = {P0, P0, P0, P0};
-        const T* tq = HAS_T ? tslot(z) : nullptr;
-        const T* tp[4] = {tq, tq, tq, tq};
-        for (int f = tid; f < G::NFACE; f += NT) {
-          const int row = f / (NB + 1), fx = f % (NB + 1);
-          const int cl = (row + NG) * NP + fx + 1;
-          T F[NV];
-          face_flux(std::integral_constant<int, 0>(), up, tp, cl, 1, F);
 #pragma unroll
-          for (int v = 0; v < NV; ++v) sf[v * G::NFACE + f] = F[v];
-        }
-        __syncthreads();
-#pragma unroll
-        for (int v = 0; v < NV; ++v) {
-          T fr = sf[v * G::NFACE + ty * (NB + 1) + tx + 1];
-          T fl = sf[v * G::NFACE + ty * (NB + 1) + tx];
-          if (SCHEME == SCH_WENO) acc[v] -= (fr - fl) / dxT[0];
-          else acc[v] -= lam[0] * (fr - fl);
-        }
-        __syncthreads();
+      for (int v = 0; v < NV; ++v) {
+        const T fr = sfx[v * NFACE + ty * (NB + 1) + tx + 1];
+        const T fl = sfx[v * NFACE + ty * (NB + 1) + tx];
+        if (SCHEME == SCH_WENO) acc[v] -= (fr - fl) / dxT[0];
+        else acc[v] -= lam[0] * (fr - fl);
       }
-      // y faces
-      {
-        const T* up[4] = {P0, P0, P0, P0};
-        const T* tq = HAS_T ? tslot(z) : nullptr;
-        const T* tp[4] = {tq, tq, tq, tq};
-        for (int f = tid; f < G::NFACE; f += NT) {
-          const int fy = f / NB, col = f % NB;
-          const int cl = (fy + 1) * NP + col + NG;
-          T F[NV];
-          face_flux(std::integral_constant<int, 1>(), up, tp, cl, NP, F);
 #pragma unroll
-          for (int v = 0; v < NV; ++v) sf[v * G::NFACE + f] = F[v];
-        }
-        __syncthreads();
-#pragma unroll
-        for (int v = 0; v < NV; ++v) {
-          T fr = sf[v * G::NFACE + (ty + 1) * NB + tx];
-          T fl = sf[v * G::NFACE + ty * NB + tx];
-          if (SCHEME == SCH_WENO) acc[v] -= (fr - fl) / dxT[1];
-          else acc[v] -= lam[1] * (fr - fl);
-        }
+      for (int v = 0; v < NV; ++v) {
+        const T fr = sfy[v * NFACE + (ty + 1) * NB + tx];
+        const T fl = sfy[v * NFACE + ty * NB + tx];
+        if (SCHEME == SCH_WENO) acc[v] -= (fr - fl) / dxT[1];
+        else acc[v] -= lam[1] * (fr - fl);
       }
       // z faces
       if (NDIM == 3) {
         T Fzhi[NV];
-        zface(z, Fzhi);
+        face_z(z, uprev, Fzhi);
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
           if (SCHEME == SCH_WENO) acc[v] -= (Fzhi[v] - Fzlo[v]) / dxT[2];
@@ -530,19 +751,32 @@ step_kernel(StepArgsT<T> A) {
       T s[NV];
 #pragma unroll
       for (int v = 0; v < NV; ++v) s[v] = T(0);
+      T unext[NV];
+      if (NDIM == 3) ldw<T, P2>(uslot(z + 1), cown, unext);
       if (A.eglm) {
         if (SCHEME == SCH_LF) {
-          const T* tl[3] = {tslot(z - 1), tslot(z), tslot(z + 1)};
-          eglm_src<T, NDIM, NP>(tl, cown, dx2, s);
+          T tm[NV], tq[NV];
+          if (NDIM == 3) {
+            ldw<T, RING>(tslot(z - 1), rown, tm);
+            ldw<T, RING>(tslot(z + 1), rown, tq);
+          }
+          eglm_src_col<T, NDIM>(T0, RING, RW, rown, tm, tq, dx2, s);
         } else {
-          const T* ul[3] = {uslot(z - 1), uslot(z), uslot(z + 1)};
-          eglm_src<T, NDIM, NP>(ul, cown, dx2, s);
+          eglm_src_col<T, NDIM>(P0, P2, NP, cown, uprev, unext, dx2, s);
         }
       }
       if (RES) {
-        const T* jl[3] = {jslot(z - 1), jslot(z), jslot(z + 1)};
-        const T* ul[3] = {uslot(z - 1), uslot(z), uslot(z + 1)};
-        resist_src<T, NDIM, NP>(jl, ul, cown, dx2, eta, s);
+        T jm[3] = {T(0), T(0), T(0)}, jq[3] = {T(0), T(0), T(0)};
+        if (NDIM == 3) {
+          const T* j0 = jslot(z - 1);
+          const T* j2 = jslot(z + 1);
+#pragma unroll
+          for (int q = 0; q < 3; ++q) {
+            jm[q] = j0[q * RING + rown];
+            jq[q] = j2[q * RING + rown];
+          }
+        }
+        resist_src_col<T, NDIM, NP, RW>(jslot(z), rown, jm, jq, P0, cown, uprev, unext, dx2, eta, s);
       }
       // update and write
       T out[NV];
@@ -569,68 +803,95 @@ step_kernel(StepArgsT<T> A) {
       if (STAGE != 1) {
         bool fin = true;
 #pragma unroll
-        for (int v = 0; v < NV; ++v) fin = fin && isfinite((double)out[v]);
+        for (int v = 0; v < NV; ++v) fin = fin && isfinite(out[v]);
         if (!fin) errbits |= 1u;
         else {
           T pr = pressure<T>(out, P);
           if (!(out[RHO] > T(0)) || pr < T(0)) errbits |= 2u;
           if (A.dyn_next) {
-            double am = 0.0;
-            am = fmax(am, (double)alpha_p<T, 0>(out, pr, P));
-            am = fmax(am, (double)alpha_p<T, 1>(out, pr, P));
-            if (NDIM == 3) am = fmax(am, (double)alpha_p<T, 2>(out, pr, P));
-            alpha_max = fmax(alpha_max, am);
+            T am = alpha_p<T, 0>(out, pr, P);
+            am = dmax<T>(am, alpha_p<T, 1>(out, pr, P));
+            if (NDIM == 3) am = dmax<T>(am, alpha_p<T, 2>(out, pr, P));
+            alpha_max = dmax<T>(alpha_max, am);
           }
         }
+        if (!fin) alpha_max = (T)NAN;
         if (A.sums) {
-          double vol = gg.dx[0] * gg.dx[1] * (NDIM == 3 ? gg.dx[2] : 1.0);
 #pragma unroll
-          for (int v = 0; v < NV; ++v) csum[v] += (double)out[v] * vol;
+          for (int v = 0; v < NV; ++v) {
+            // Kahan: csum - ccmp carries the column sum
+            const T y = out[v] - ccmp[v];
+            const T t = csum[v] + y;
+            ccmp[v] = (t - csum[v]) - y;
+            csum[v] = t;
+          }
         }
       }
+      if (NDIM == 3) ldw<T, P2>(P0, cown, uprev);
       __syncthreads();
     }
-    // per-block reductions of the fused diagnostics (block problem is uniform per block)
+    if (!ok) break;
+    // per-block reductions of the fused diagnostics (one problem per block), in T within
+    // each warp (TwoSum pairs for the sums), then FP64 across warps
     if (A.dyn_next || A.sums) {
-      __shared__ double red[NV + 1][32];
+      double* red = reinterpret_cast<double*>(sf);     // (NV+1) x 32 doubles
       const int lane = tid & 31, wid = tid >> 5;
-      double am = alpha_max;
-      for (int o = 16; o > 0; o >>= 1) am = fmax(am, __shfl_xor_sync(0xffffffffu, am, o));
-      double cs[NV];
+      T am = alpha_max;
+      for (int o = 16; o > 0; o >>= 1) {
+        const T t = __shfl_xor_sync(0xffffffffu, am, o);
+        am = (t != t || am != am) ? (T)NAN : dmax<T>(am, t);
+      }
+      T hi[NV], lo[NV];
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
-        cs[v] = csum[v];
-        for (int o = 16; o > 0; o >>= 1) cs[v] += __shfl_xor_sync(0xffffffffu, cs[v], o);
+        hi[v] = csum[v];
+        lo[v] = -ccmp[v];
+        for (int o = 16; o > 0; o >>= 1) {
+          const T h2 = __shfl_xor_sync(0xffffffffu, hi[v], o);
+          const T l2 = __shfl_xor_sync(0xffffffffu, lo[v], o);
+          two_sum_acc<T>(hi[v], lo[v], h2, l2);
+        }
       }
       if (lane == 0) {
-        red[NV][wid] = am;
+        red[NV * 32 + wid] = (double)am;
 #pragma unroll
-        for (int v = 0; v < NV; ++v) red[v][wid] = cs[v];
+        for (int v = 0; v < NV; ++v) red[v * 32 + wid] = (double)hi[v] + (double)lo[v];
       }
       __syncthreads();
       if (tid == 0) {
         const int nw = (NT + 31) / 32;
         double a2 = 0.0;
-        for (int q = 0; q < nw; ++q) a2 = fmax(a2, red[NV][q]);
+        for (int q = 0; q < nw; ++q) {
+          const double t = red[NV * 32 + q];
+          a2 = (t != t || a2 != a2) ? __longlong_as_double(0x7ff8000000000000ll) : fmax(a2, t);
+        }
         if (A.dyn_next) {
           // alpha >= 0: its IEEE bit pattern orders like the value (NaN above everything)
           atomicMax(&A.dyn_next[gg.problem].alpha_bits, (unsigned long long)__double_as_longlong(a2));
         }
         if (A.sums) {
+          const double vol = gg.dx[0] * gg.dx[1] * (NDIM == 3 ? gg.dx[2] : 1.0);
           for (int v = 0; v < NV; ++v) {
             double t = 0.0;
-            for (int q = 0; q < nw; ++q) t += red[v][q];
-            atomicAdd(&A.sums[gg.problem * NV + v], t);
+            for (int q = 0; q < nw; ++q) t += red[v * 32 + q];
+            atomicAdd(&A.sums[gg.problem * NV + v], t * vol);
           }
         }
       }
       __syncthreads();
-      alpha_max = 0.0;
+      alpha_max = T(0);
 #pragma unroll
-      for (int v = 0; v < NV; ++v) csum[v] = 0.0;
+      for (int v = 0; v < NV; ++v) { csum[v] = T(0); ccmp[v] = T(0); }
     }
   }
-  // error word
+  if (*status != 0) {
+    errbits |= 4u;
+    // a copy never completed: wait (bounded again) for the copies still in flight so none
+    // lands after the block has left
+    if (tid == 0)
+      for (int q = 0; q < UPL; ++q)
+        if ((inflight >> q) & 1u) mbar_wait_bounded(&bars[q], (phase >> q) & 1u);
+  }
   unsigned e = errbits;
   for (int o = 16; o > 0; o >>= 1) e |= __shfl_xor_sync(0xffffffffu, e, o);
   if ((tid & 31) == 0 && e) atomicOr(A.err_word, e);
