@@ -201,6 +201,34 @@ long long map_kernel_launches(const map_pool* pool);
 /* Last error text of the pool (or of the last failed create when pool is NULL). */
 const char* map_last_error(const map_pool* pool);
 
+/* Allocation-free CFL reduction (no counterpart in the paper; an interface addition).
+ *
+ * For callers that cannot allocate device memory: code that runs inside a CUDA-graph
+ * capture and must not add allocation nodes, embedders whose device memory belongs to
+ * another allocator (a framework's caching allocator, a fixed arena) and who forbid
+ * cudaMalloc/cudaFree, and real-time loops that cannot afford the device synchronisation
+ * cudaMalloc/cudaFree may cause.  Unlike map_cfl_dt it needs no pool: the caller passes
+ * the state and receives the result, and nothing is allocated by this call.
+ *
+ * u_dev: device pointer to nblocks blocks of one problem with uniform spacing dx[ndim],
+ *   in the pool layout [block][9][nz+4][nb+4][nb+4] (nz = nb in 3D, the z extent is 1 in
+ *   2D), FP64 (precision MAP_FP64) or FP32 (MAP_FP32_FIX64); ghost cells are not read.
+ * out (host): dt, c_h, c_p, psi damping factor, alpha_g -- the same quantities, from the
+ *   same formulas, as map_cfl_dt and map_get_speeds for one problem.
+ * The per-block partial maxima live in one file-scope static device array sized for
+ *   MAP_NOALLOC_MAX_BLOCKS blocks (512 KB); every GPU that loads the library holds it until
+ *   the process exits.  nblocks above that maximum is rejected with MAP_EINVAL (text in
+ *   map_last_error(NULL)).
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress)
+ *   with that device current; make that first call before any stream capture.
+ * All calls share the array: calls whose kernels overlap on the GPU (different streams,
+ *   no ordering between them) race and give wrong results.  Runs on `stream` (a
+ *   cudaStream_t, NULL = legacy default stream) and synchronises it.
+ * Errors: MAP_EINVAL, MAP_ECUDA, MAP_ENONFINITE (dt not finite and positive). */
+#define MAP_NOALLOC_MAX_BLOCKS 65536
+int map_cfl_dt_noalloc(const void* u_dev, int precision, int ndim, int nb, int nblocks,
+                       const double* dx, const map_params* p, void* stream, double* out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -26,6 +26,7 @@ UNITS = {
     "kernels_f64.cu": ["-fmad=false"],
     "kernels_f32.cu": ["-ftz=true", "-prec-div=false", "-prec-sqrt=false"],
     "common.cu": ["-fmad=false"],
+    "noalloc.cu": ["-fmad=false"],
 }
 CPP_UNITS = ["tree.cpp", "capi.cpp"]
 

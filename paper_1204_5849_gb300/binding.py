@@ -86,7 +86,24 @@ _SIGS = {
     "map_get_speeds": (C.c_int, [C.c_void_p, C.c_void_p]),
     "map_kernel_launches": (C.c_longlong, [C.c_void_p]),
     "map_last_error": (C.c_char_p, [C.c_void_p]),
+    "map_cfl_dt_noalloc": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p,
+                                     C.POINTER(map_params), C.c_void_p, C.c_void_p]),
 }
+
+NOALLOC_MAX_BLOCKS = 65536
+
+
+def cfl_dt_noalloc(u_dev_ptr: int, precision: int, ndim: int, nb: int, nblocks: int, dx,
+                   params: Dict, stream: Optional[int] = None) -> np.ndarray:
+    """map_cfl_dt_noalloc: (dt, c_h, c_p, damping, alpha_g) of a device-resident state."""
+    L = load()
+    dxa = np.ascontiguousarray(dx, dtype=np.float64)
+    out = np.zeros(5, dtype=np.float64)
+    rc = L.map_cfl_dt_noalloc(C.c_void_p(u_dev_ptr), precision, ndim, nb, nblocks, _ptr(dxa),
+                              C.byref(make_params(params)), C.c_void_p(stream or 0), _ptr(out))
+    if rc != MAP_OK:
+        raise MapError(rc, "map_cfl_dt_noalloc", L.map_last_error(None).decode())
+    return out
 
 
 def load(path: str = LIB_PATH):

@@ -185,6 +185,50 @@ __global__ void __launch_bounds__(256) cfl_kernel(const T* __restrict__ u, const
   }
 }
 
+// Per-block maxima of alpha (the allocation-free CFL variant): partial[b] = max over the
+// interior cells of block b and the directions of |v_d| + c_f,d.
+template <typename T, int NDIM, int NB>
+__global__ void __launch_bounds__(256) cfl_partial_kernel(const T* __restrict__ u, int nblocks, T gamma, T gm1,
+                                                          double* __restrict__ partial) {
+  using G = Geo<NDIM, NB>;
+  constexpr int NP = G::NP, S = G::S;
+  constexpr int NI = NDIM == 3 ? NB * NB * NB : NB * NB;
+  __shared__ double red[32];
+  Phys<T> P;
+  P.gamma = gamma;
+  P.gm1 = gm1;
+  P.ch = T(0);
+  P.tau = T(0);
+  for (int blk = blockIdx.x; blk < nblocks; blk += gridDim.x) {
+    const T* ub = u + (size_t)blk * NV * S;
+    double am = 0.0;
+    for (int c = threadIdx.x; c < NI; c += blockDim.x) {
+      const int i = c % NB, j = (c / NB) % NB, k = NDIM == 3 ? c / (NB * NB) : 0;
+      const int cc = ((NDIM == 3 ? k + NG : 0) * NP + j + NG) * NP + i + NG;
+      T w[NV];
+      load_global<T>(ub, S, cc, w);
+      const T p = pressure<T>(w, P);
+      double a = (double)alpha_p<T, 0>(w, p, P);
+      a = fmax(a, (double)alpha_p<T, 1>(w, p, P));
+      if (NDIM == 3) a = fmax(a, (double)alpha_p<T, 2>(w, p, P));
+      if (a != a) am = a;
+      else if (!(am != am)) am = fmax(am, a);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      const double t = __shfl_xor_sync(0xffffffffu, am, o);
+      am = (t != t) ? t : ((am != am) ? am : fmax(am, t));
+    }
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = am;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double a = 0.0;
+      for (int q = 0; q < (int)(blockDim.x + 31) / 32; ++q) a = (red[q] != red[q] || a != a) ? (a != a ? a : red[q]) : fmax(a, red[q]);
+      partial[blk] = a;     // every slot < nblocks is written before it is read
+    }
+    __syncthreads();
+  }
+}
+
 // Refinement estimator (Sec. 4.5), computed in FP64 from the pool values, over the
 // interior and the first ghost ring; block maximum -> flag.
 template <typename T, int NDIM, int NB>

@@ -57,6 +57,11 @@ struct map_pool {
 
 static std::string g_create_error;
 
+namespace mapgb {
+// error text for calls without a pool (returned by map_last_error(NULL))
+void set_global_error(const char* msg) { g_create_error = msg; }
+}  // namespace mapgb
+
 static int fail(map_pool* p, int code, const std::string& msg) {
   if (p) p->err = msg;
   else g_create_error = msg;

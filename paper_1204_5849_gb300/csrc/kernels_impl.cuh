@@ -163,6 +163,18 @@ cudaError_t launch_regrid_T(const KernelConfig& kc, const RegridLaunch& L, cudaS
 #undef CALL_REGRID
 }
 
+template <typename T>
+cudaError_t launch_cfl_partial_T(const KernelConfig& kc, const void* u, int nblocks, double gamma, double* partial,
+                                 cudaStream_t s) {
+  if (nblocks <= 0) return cudaSuccess;
+#define CALL_PART(ND, NBV)                                                                          \
+  cfl_partial_kernel<T, ND, NBV><<<nblocks, 256, 0, s>>>((const T*)u, nblocks, (T)gamma, (T)(gamma - 1.0), \
+                                                        partial);                                   \
+  return cudaGetLastError()
+  MAPGB_GEO_DISPATCH(kc, CALL_PART);
+#undef CALL_PART
+}
+
 }  // namespace mapgb
 
 #define MAPGB_DEFINE_LAUNCHERS(T, SUFFIX)                                                          \
@@ -176,4 +188,5 @@ cudaError_t launch_regrid_T(const KernelConfig& kc, const RegridLaunch& L, cudaS
   cudaError_t launch_pack_##SUFFIX(const KernelConfig& k, const PackLaunch& l, cudaStream_t s, long long* c) { return launch_pack_T<T>(k, l, s, c); } \
   cudaError_t launch_regrid_##SUFFIX(const KernelConfig& k, const RegridLaunch& l, cudaStream_t s, long long* c) { return launch_regrid_T<T>(k, l, s, c); } \
   size_t step_smem_##SUFFIX(const KernelConfig& k, int scheme, int res) { return step_smem_T<T>(k, scheme, res); } \
+  cudaError_t launch_cfl_partial_##SUFFIX(const KernelConfig& k, const void* u, int n, double g, double* part, cudaStream_t s) { return launch_cfl_partial_T<T>(k, u, n, g, part, s); } \
   }

@@ -180,7 +180,9 @@ struct KernelConfig {
   cudaError_t launch_sums_##SUFFIX(const KernelConfig&, const SumLaunch&, cudaStream_t, long long*); \
   cudaError_t launch_pack_##SUFFIX(const KernelConfig&, const PackLaunch&, cudaStream_t, long long*); \
   cudaError_t launch_regrid_##SUFFIX(const KernelConfig&, const RegridLaunch&, cudaStream_t, long long*); \
-  size_t step_smem_##SUFFIX(const KernelConfig&, int scheme, int resistive);
+  size_t step_smem_##SUFFIX(const KernelConfig&, int scheme, int resistive); \
+  cudaError_t launch_cfl_partial_##SUFFIX(const KernelConfig&, const void* u, int nblocks, double gamma, \
+                                          double* partial, cudaStream_t);
 
 MAPGB_DECLARE_LAUNCHERS(f64)
 MAPGB_DECLARE_LAUNCHERS(f32)
