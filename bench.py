@@ -161,6 +161,84 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def run_workload(args):
+    """Secondary configurations: cell-updates/s of the batched FP32 + FP64-fix form (with
+    regrid every few steps on the AMR ones), the plain FP64 form on the same input, and,
+    where the oracle finishes quickly, the FP32 form's per-variable L1 against it."""
+    import torch
+    import workloads as w
+    from workloads.problems import CONFIGS, initial_state
+    from paper_1204_5849_gb300 import MAP_FP32_FIX64, MAP_FP64, Pool
+    cfg = CONFIGS[args.workload](small=args.small)
+    mesh0 = cfg["mesh"]
+    U0 = initial_state(cfg)
+    params = dict(cfg["params"], fp64_fix_tau=1e-2)
+    every = cfg.get("regrid_every", 0)
+    refine = cfg.get("refine")
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    sptr = stream.cuda_stream
+    cap = 4 * mesh0.nleaves + 4096
+    out = {"workload": cfg["name"], "leaves": mesh0.nleaves, "cells": mesh0.ncells}
+    settle = (refine["max_level"] + 2) if (every and refine) else 0
+    for prec, key in ((MAP_FP32_FIX64, "fp32_batched"), (MAP_FP64, "fp64_plain")):
+        pool = Pool(mesh0, prec, max_blocks=cap, stream=sptr)
+        pool.write_leaves(U0)
+        # AMR: let the refinement criterion settle the initial mesh (adapt + one step, a few
+        # times) before timing
+        for _ in range(settle):
+            pool.adapt(params, refine)
+            pool.fill_ghosts(); pool.cfl_dt(params); pool.step(params)
+        out.setdefault("leaves_settled", {})[key] = pool.nleaves
+        nsteps = args.steps if prec == MAP_FP32_FIX64 else max(2, min(args.steps, 8))
+        for _ in range(args.warmup):
+            if prec == MAP_FP32_FIX64:
+                pool.advance(params, 1)
+            else:
+                pool.fill_ghosts(); pool.cfl_dt(params); pool.step(params)
+        torch.cuda.synchronize()
+        cell_updates = 0
+        adapt_ms = 0.0
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0 = time.perf_counter()
+        e0.record(stream)
+        for s in range(nsteps):
+            if every and refine and s > 0 and s % every == 0:
+                a0 = time.perf_counter()
+                pool.adapt(params, refine)
+                adapt_ms += 1e3 * (time.perf_counter() - a0)
+            if prec == MAP_FP32_FIX64:
+                pool.advance(params, 1)
+            else:
+                pool.fill_ghosts(); pool.cfl_dt(params); pool.step(params)
+            cell_updates += pool.nleaves * mesh0.cells_per_block
+        e1.record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        ms = e0.elapsed_time(e1)
+        out[key] = {"value": cell_updates / (ms * 1e-3), "unit": METRIC, "ms_per_step": ms / nsteps,
+                    "steps": nsteps, "wall_s": wall, "leaves_end": pool.nleaves,
+                    "adapt_ms_total": adapt_ms, "check": pool.check()}
+        pool.close()
+    if args.workload in ("ot2d", "ensemble") and not args.no_cpu:
+        from oracle import Oracle
+        nacc = 10
+        pool = Pool(mesh0, MAP_FP32_FIX64, max_blocks=cap, stream=sptr)
+        pool.write_leaves(U0)
+        pool.advance(params, nacc)
+        G = pool.read_leaves()
+        pool.close()
+        orc = Oracle(mesh0, U0)
+        orc.advance(params, nacc)
+        R = orc.get_state()
+        big = max(float(np.abs(R[:, v]).mean()) for v in range(9))
+        names = ("rho", "mx", "my", "mz", "bx", "by", "bz", "e", "psi")
+        out["l1_rel_fp32_vs_oracle"] = {"steps": nacc, **{
+            nm: float(np.abs(G[:, v] - R[:, v]).mean() / max(float(np.abs(R[:, v]).mean()), 1e-3 * big))
+            for v, nm in enumerate(names)}}
+    print(json.dumps(out))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -171,10 +249,17 @@ def main():
     ap.add_argument("--size", type=int, default=256, help="cells per edge (profiling of smaller cases)")
     ap.add_argument("--quick", action="store_true", help="value and kernel timing only (profiling)")
     ap.add_argument("--prec", type=int, default=32, choices=(32, 64), help="pool precision of --quick runs")
+    ap.add_argument("--workload", default="alfven3d",
+                    choices=("alfven3d", "ot2d", "rotor_amr", "harris_amr", "ensemble"),
+                    help="secondary configurations print their own line")
+    ap.add_argument("--small", action="store_true", help="small variant of a secondary workload")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.workload != "alfven3d":
+        run_workload(args)
         return
 
     import torch

@@ -186,6 +186,26 @@ int map_flag_refine(map_pool* pool, const map_params* p, const map_refine_params
  * new array.  Errors: MAP_EINVAL. */
 int map_regrid(map_pool* pool, const map_block_desc* new_leaves, int n);
 
+/* Regrid decision on the host (Sec. 4.5 "refine if the error exceeds the threshold"):
+ * from per-leaf flags (+1 refine, 0 keep, -1 may coarsen, in leaf order) build the new leaf
+ * list: refine leaves flagged +1 below max_level; refine further leaves until every new
+ * leaf's face, edge and corner neighbours are at most one level coarser (2:1); coarsen a
+ * parent whose 2^ndim children are all leaves flagged -1 and none refined, when the
+ * coarsened parent keeps 2:1.  Order: old leaf order, a kept leaf in place, a refined leaf
+ * as its children (child bits x | y<<1 | z<<2 ascending), a coarsened parent at the place
+ * of its first child.  out[cap] receives the list, *n_out its length (also when cap is too
+ * small: MAP_ENOMEM).  No device work. */
+int map_plan_regrid(map_pool* pool, const int8_t* flags, int max_level, map_block_desc* out,
+                    int cap, int* n_out);
+
+/* One adaptation cycle: ghost fill, refinement flags, map_plan_regrid with r->max_level,
+ * and map_regrid when the leaf set changes.  *n_out = number of leaves afterwards (read
+ * them with map_get_leaves).  Synchronises. */
+int map_adapt(map_pool* pool, const map_params* p, const map_refine_params* r, int* n_out);
+
+/* The current leaf list (leaf order of the last map_set_tree / map_regrid / map_adapt). */
+int map_get_leaves(map_pool* pool, map_block_desc* out, int cap, int* n_out);
+
 /* FP64 conservation sums: sums_out[n_problems][9] = sum over leaf cells of U * cell
  * volume.  Synchronises. */
 int map_conservation(map_pool* pool, double* sums_out);

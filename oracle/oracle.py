@@ -260,3 +260,115 @@ def block_step(ndim: int, nb: int, params: Dict, dx, dt: float, ch: float, damp:
     if rc != 0:
         raise ValueError("oracle block step supports MMC and LF only")
     return out
+
+
+# regrid decision ----------------------------------------------------------------------------
+
+def plan_regrid(mesh, flags, max_level: int) -> np.ndarray:
+    """New leaf list from per-leaf flags (+1 refine, 0 keep, -1 may coarsen), by brute force
+    over sets of block keys (Sec. 4.5 refinement rule with 2:1 balance over faces, edges and
+    corners).  Refine flagged leaves below max_level and, repeatedly, any leaf more than one
+    level coarser than a neighbour of a new leaf; coarsen a parent whose children are all
+    leaves flagged -1 and not refined, unless a block next to it ends two levels finer.
+    Order: old leaf order; a refined leaf becomes its children (bits x | y<<1 | z<<2
+    ascending); a coarsened parent takes the place of its first child."""
+    nd = mesh.ndim
+    leaves = [tuple(int(v) for v in row) for row in mesh.leaves]
+    leafset = set(leaves)
+    flag_of = {lf: int(f) for lf, f in zip(leaves, flags)}
+    internal = set()
+    for (p, L, i, j, k) in leaves:
+        while L > 0:
+            L -= 1
+            i, j, k = i >> 1, j >> 1, k >> 1
+            internal.add((p, L, i, j, k))
+
+    def offsets():
+        rz = (-1, 0, 1) if nd == 3 else (0,)
+        return [(ox, oy, oz) for oz in rz for oy in (-1, 0, 1) for ox in (-1, 0, 1) if (ox, oy, oz) != (0, 0, 0)]
+
+    def neighbour(p, L, c, off):
+        q = list(c)
+        for d in range(nd):
+            n = mesh.problems[p].nbase[d] << L
+            q[d] = c[d] + off[d]
+            if q[d] < 0 or q[d] >= n:
+                side = 0 if q[d] < 0 else 1
+                if mesh.problems[p].bc[d][side] != 0:
+                    return None
+                q[d] %= n
+        return tuple(q)
+
+    def cover(p, L, q):
+        """leaf covering block (L, q), or None when the region is refined below L"""
+        for l in range(L, -1, -1):
+            s = L - l
+            key = (p, l, q[0] >> s, q[1] >> s, q[2] >> s)
+            if key in leafset:
+                return key
+            if key in internal:
+                return None
+        return None
+
+    refine = {lf for lf in leaves if flag_of[lf] > 0 and lf[1] < max_level}
+    work = list(refine)
+    while work:
+        p, L, i, j, k = work.pop()
+        for off in offsets():
+            q = neighbour(p, L, (i, j, k), off)
+            if q is None:
+                continue
+            cv = cover(p, L, q)
+            if cv is not None and cv not in refine and cv[1] < L:
+                refine.add(cv)
+                work.append(cv)
+
+    def children(par):
+        p, L, i, j, k = par
+        out = []
+        for cb in range(1 << nd):
+            out.append((p, L + 1, 2 * i + (cb & 1), 2 * j + ((cb >> 1) & 1),
+                        2 * k + ((cb >> 2) & 1) if nd == 3 else 0))
+        return out
+
+    cand = set()
+    for par in internal:
+        ch = children(par)
+        if all(c in leafset and flag_of[c] < 0 and c not in refine for c in ch):
+            cand.add(par)
+    changed = True
+    while changed:
+        changed = False
+        for par in sorted(cand):
+            p, Lp, i, j, k = par
+            bad = False
+            for off in offsets():
+                q = neighbour(p, Lp, (i, j, k), off)
+                if q is None:
+                    continue
+                key = (p, Lp) + q
+                if key not in internal or key in cand:
+                    continue
+                for c in children(key):
+                    # children of the neighbour that touch par
+                    touch = all(not ((off[d] == 1 and ((c[2 + d] & 1) != 0)) or
+                                     (off[d] == -1 and ((c[2 + d] & 1) != 1))) for d in range(nd))
+                    if touch and (c in internal or c in refine):
+                        bad = True
+            if bad:
+                cand.discard(par)
+                changed = True
+
+    out, done = [], set()
+    for lf in leaves:
+        p, L, i, j, k = lf
+        par = (p, L - 1, i >> 1, j >> 1, k >> 1) if L > 0 else None
+        if par is not None and par in cand:
+            if par not in done:
+                done.add(par)
+                out.append(par)
+        elif lf in refine:
+            out.extend(children(lf))
+        else:
+            out.append(lf)
+    return np.asarray(out, dtype=np.int32).reshape(-1, 5)

@@ -86,6 +86,11 @@ _SIGS = {
     "map_get_speeds": (C.c_int, [C.c_void_p, C.c_void_p]),
     "map_kernel_launches": (C.c_longlong, [C.c_void_p]),
     "map_last_error": (C.c_char_p, [C.c_void_p]),
+    "map_plan_regrid": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.POINTER(map_block_desc), C.c_int,
+                                  C.POINTER(C.c_int)]),
+    "map_adapt": (C.c_int, [C.c_void_p, C.POINTER(map_params), C.POINTER(map_refine_params),
+                            C.POINTER(C.c_int)]),
+    "map_get_leaves": (C.c_int, [C.c_void_p, C.POINTER(map_block_desc), C.c_int, C.POINTER(C.c_int)]),
     "map_cfl_dt_noalloc": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p,
                                      C.POINTER(map_params), C.c_void_p, C.c_void_p]),
 }
@@ -158,6 +163,13 @@ def _leaves(mesh) -> "C.Array":
         arr[q].ijk[1] = int(j)
         arr[q].ijk[2] = int(k)
     return arr
+
+
+def _leaves_to_array(arr, n: int) -> np.ndarray:
+    out = np.zeros((n, 5), dtype=np.int32)
+    for q in range(n):
+        out[q] = (arr[q].problem, arr[q].level, arr[q].ijk[0], arr[q].ijk[1], arr[q].ijk[2])
+    return out
 
 
 class Pool:
@@ -276,6 +288,36 @@ class Pool:
         self._ck(load().map_regrid(self.h, arr, new_mesh.nleaves), "map_regrid")
         self._leaves_arr = arr
         self.mesh = new_mesh
+
+    def plan_regrid(self, flags: np.ndarray, max_level: int) -> np.ndarray:
+        """The new leaf list (n, 5) decided from per-leaf flags (map_plan_regrid)."""
+        f = np.ascontiguousarray(flags, dtype=np.int8)
+        cap = int(self.nleaves * (8 if self.mesh.ndim == 3 else 4))
+        arr = (map_block_desc * cap)()
+        n = C.c_int(0)
+        self._ck(load().map_plan_regrid(self.h, _ptr(f), int(max_level), arr, cap, C.byref(n)), "map_plan_regrid")
+        return _leaves_to_array(arr, n.value)
+
+    def get_leaves(self) -> np.ndarray:
+        cap = self.nleaves
+        arr = (map_block_desc * cap)()
+        n = C.c_int(0)
+        self._ck(load().map_get_leaves(self.h, arr, cap, C.byref(n)), "map_get_leaves")
+        return _leaves_to_array(arr, n.value)
+
+    def adapt(self, params: Dict, refine: Dict):
+        """flags -> plan -> regrid (map_adapt); the pool's mesh follows the new leaves."""
+        n = C.c_int(0)
+        self._ck(load().map_adapt(self.h, C.byref(make_params(params)), C.byref(make_refine(refine)),
+                                  C.byref(n)), "map_adapt")
+        cap = n.value
+        arr = (map_block_desc * cap)()
+        m = C.c_int(0)
+        self._ck(load().map_get_leaves(self.h, arr, cap, C.byref(m)), "map_get_leaves")
+        from dataclasses import replace
+        self.mesh = replace(self.mesh, leaves=_leaves_to_array(arr, m.value))
+        self._leaves_arr = arr
+        return self.mesh
 
     def conservation(self) -> np.ndarray:
         out = np.zeros((len(self.mesh.problems), 9))

@@ -635,6 +635,57 @@ int map_regrid(map_pool* pool, const map_block_desc* leaves, int n) {
   return install_tree(pool, t);   // also clears alpha_ready
 }
 
+int map_plan_regrid(map_pool* pool, const int8_t* flags, int max_level, map_block_desc* out, int cap,
+                    int* n_out) {
+  if (!pool || !flags || !n_out) return fail(pool, MAP_EINVAL, "null argument");
+  if (!pool->have_tree) return fail(pool, MAP_ESTATE, "no tree");
+  std::vector<map_block_desc> plan;
+  std::string why = plan_regrid(pool->tree, pool->probs, flags, max_level, plan);
+  if (!why.empty()) return fail(pool, MAP_EINVAL, why);
+  *n_out = (int)plan.size();
+  if ((int)plan.size() > cap || !out) return fail(pool, MAP_ENOMEM, "output array too small for the new leaf list");
+  memcpy(out, plan.data(), plan.size() * sizeof(map_block_desc));
+  return MAP_OK;
+}
+
+int map_get_leaves(map_pool* pool, map_block_desc* out, int cap, int* n_out) {
+  if (!pool || !n_out) return fail(pool, MAP_EINVAL, "null argument");
+  if (!pool->have_tree) return fail(pool, MAP_ESTATE, "no tree");
+  const HostTree& t = pool->tree;
+  *n_out = t.nleaves;
+  if (t.nleaves > cap || !out) return fail(pool, MAP_ENOMEM, "output array too small");
+  for (int l = 0; l < t.nleaves; ++l) {
+    const int id = t.leaf_to_block[l];
+    out[l].problem = t.blk_problem[id];
+    out[l].level = t.blk_level[id];
+    for (int d = 0; d < 3; ++d) out[l].ijk[d] = t.blk_ijk[3 * id + d];
+  }
+  return MAP_OK;
+}
+
+int map_adapt(map_pool* pool, const map_params* p, const map_refine_params* r, int* n_out) {
+  if (!pool || !p || !r || !n_out) return fail(pool, MAP_EINVAL, "null argument");
+  if (!pool->have_tree) return fail(pool, MAP_ESTATE, "no tree");
+  int rc = fill_on(pool, pool->cur);
+  if (rc) return rc;
+  std::vector<int8_t> flags(pool->tree.nleaves);
+  rc = map_flag_refine(pool, p, r, flags.data(), nullptr);
+  if (rc) return rc;
+  std::vector<map_block_desc> plan;
+  std::string why = plan_regrid(pool->tree, pool->probs, flags.data(), r->max_level, plan);
+  if (!why.empty()) return fail(pool, MAP_EINVAL, why);
+  bool same = (int)plan.size() == pool->tree.nleaves;
+  for (int l = 0; same && l < pool->tree.nleaves; ++l) {
+    const int id = pool->tree.leaf_to_block[l];
+    same = plan[l].level == pool->tree.blk_level[id] && plan[l].problem == pool->tree.blk_problem[id] &&
+           plan[l].ijk[0] == pool->tree.blk_ijk[3 * id] && plan[l].ijk[1] == pool->tree.blk_ijk[3 * id + 1] &&
+           plan[l].ijk[2] == pool->tree.blk_ijk[3 * id + 2];
+  }
+  *n_out = (int)plan.size();
+  if (same) return MAP_OK;                       // nothing to do: tree, tables and graphs stay
+  return map_regrid(pool, plan.data(), (int)plan.size());
+}
+
 int map_conservation(map_pool* pool, double* sums_out) {
   if (!pool || !sums_out) return fail(pool, MAP_EINVAL, "null argument");
   if (!pool->have_tree) return fail(pool, MAP_ESTATE, "no tree");

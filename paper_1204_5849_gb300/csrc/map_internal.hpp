@@ -78,6 +78,11 @@ struct HostTree {
 std::string build_tree(int ndim, int nb, const std::vector<map_problem_desc>& probs,
                        const map_block_desc* leaves, int n, HostTree& t);
 
+// Regrid decision from per-leaf flags (+1 refine, 0 keep, -1 may coarsen); the new leaf
+// list in the documented order.  Empty string on success.
+std::string plan_regrid(const HostTree& t, const std::vector<map_problem_desc>& probs, const int8_t* flags,
+                        int max_level, std::vector<map_block_desc>& out);
+
 // Regrid tasks from an old tree to a new one; empty string on success.
 std::string build_regrid(const HostTree& old_t, const HostTree& new_t,
                          std::vector<RegridTask>& tasks);

@@ -663,56 +663,54 @@ step_kernel(StepArgsT<T> A) {
     };
 
     T Fzlo[NV], uprev[NV];
-    int zbeg = 0, zend = 1;
     bool ok = true;
     const bool PRED = HAS_T || RES;
-    if (NDIM == 3) {
-      if (tid == 0) {
-        issue_plane(0);
+    if (tid == 0) {
+      issue_plane(0);
+      if (NDIM == 3) {
         issue_plane(1);
         issue_plane(2);
         issue_plane(3);
       }
-      ok = ok && wait_plane(0);
-      ok = ok && wait_plane(1);
-      ok = ok && wait_plane(2);
-      if (ok) {
-        read_constants();
-        if (PRED) work(1, true, 0, false);
-      }
-      ok = ok && wait_plane(3);
-      if (ok && PRED) work(2, true, 0, false);
-      __syncthreads();
-      if (ok) {
-        ldw<T, P2>(uslot(0), cown, uprev);
-        face_z(1, uprev, Fzlo);
-        ldw<T, P2>(uslot(1), cown, uprev);
-      }
-      __syncthreads();
-      if (ok && tid == 0) issue_plane(4);
-      zbeg = NG;
-      zend = NB + NG;
-    } else {
-      if (tid == 0) issue_plane(0);
-      ok = wait_plane(0);
-      if (ok) {
-        read_constants();
-        if (PRED) work(0, true, 0, false);
-      }
-      __syncthreads();
     }
-    if (!ok) break;
-
-    for (int z = zbeg; z < zend; ++z) {
+    // 3D: iteration z predicts plane z+1 and updates plane z (z >= NG); one call site per
+    // work-item kind keeps the kernel's code small.  2D: a single plane.
+    const int zlast = NDIM == 3 ? NB + NG - 1 : 0;
+    for (int z = 0; z <= zlast; ++z) {
       if (NDIM == 3) {
-        // planes z, z+1 resident; z+2 in flight since the previous iteration
-        if (!wait_plane(z + 2)) { ok = false; break; }
-        if (tid == 0 && z + 3 <= NP - 1) issue_plane(z + 3);   // into the slot of z-1
-        work(z + 1, PRED, z, true);                            // predictor z+1, faces of z
+        if (z == 0) {
+          ok = wait_plane(0);
+          if (ok) ok = wait_plane(1);
+          if (ok) ok = wait_plane(2);
+        } else {
+          ok = wait_plane(z + 2);                               // in flight since z-1
+        }
+        if (!ok) break;
+        if (z == 0) read_constants();
+        if (tid == 0 && z >= 1 && z + 3 <= NP - 1) issue_plane(z + 3);   // slot of z-1
+        work(z + 1, PRED, z, z >= NG);                           // predictor z+1, faces of z
       } else {
+        ok = wait_plane(0);
+        if (!ok) break;
+        read_constants();
+        if (PRED) {
+          work(0, true, 0, false);
+          __syncthreads();
+        }
         work(0, false, 0, true);
       }
       __syncthreads();
+      T Fzhi[NV];
+      if (NDIM == 3) {
+        if (z >= 1) face_z(z, uprev, Fzhi);                     // face between planes z, z+1
+        if (z < NG) {
+#pragma unroll
+          for (int v = 0; v < NV; ++v) Fzlo[v] = Fzhi[v];
+          ldw<T, P2>(uslot(z), cown, uprev);
+          __syncthreads();
+          continue;
+        }
+      }
       const T* P0 = uslot(z);
       const T* T0 = HAS_T ? tslot(z) : nullptr;
       T acc[NV];
@@ -738,8 +736,6 @@ step_kernel(StepArgsT<T> A) {
       }
       // z faces
       if (NDIM == 3) {
-        T Fzhi[NV];
-        face_z(z, uprev, Fzhi);
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
           if (SCHEME == SCH_WENO) acc[v] -= (Fzhi[v] - Fzlo[v]) / dxT[2];

@@ -349,3 +349,173 @@ std::string build_regrid(const HostTree& o, const HostTree& nw, std::vector<Regr
 }
 
 }  // namespace mapgb
+
+namespace mapgb {
+
+namespace {
+
+// leaf index (pool id < nleaves) covering block (p, L, c) of the current tree: the block
+// itself, or the leaf at a coarser level that contains it; -1 if the block region is
+// refined below L (then no single leaf covers it) or outside the domain.
+int covering_leaf(const HostTree& t, int p, int L, const int* c) {
+  int ijk[3] = {c[0], c[1], c[2]};
+  for (int l = L; l >= 0; --l) {
+    const int id = t.find(p, l, ijk[0], ijk[1], ijk[2]);
+    if (id >= 0) return id < t.nleaves ? id : -1;
+    for (int d = 0; d < 3; ++d) ijk[d] >>= 1;
+  }
+  return -1;
+}
+
+// neighbour block coordinates of (p, L, c) in direction off, periodic wrap; false if the
+// neighbour lies outside a non-periodic boundary
+bool neighbour(const std::vector<map_problem_desc>& probs, int ndim, int p, int L, const int* c, const int* off,
+               int* q) {
+  for (int d = 0; d < 3; ++d) q[d] = c[d];
+  for (int d = 0; d < ndim; ++d) {
+    const int n = probs[p].nbase[d] << L;
+    q[d] = c[d] + off[d];
+    if (q[d] < 0 || q[d] >= n) {
+      if (probs[p].bc[d][q[d] < 0 ? 0 : 1] != MAP_BC_PERIODIC) return false;
+      q[d] = (q[d] + n) % n;
+    }
+  }
+  return true;
+}
+
+template <typename F>
+void for_each_offset(int ndim, F&& f) {
+  for (int oz = (ndim == 3 ? -1 : 0); oz <= (ndim == 3 ? 1 : 0); ++oz)
+    for (int oy = -1; oy <= 1; ++oy)
+      for (int ox = -1; ox <= 1; ++ox) {
+        if (!ox && !oy && !oz) continue;
+        const int off[3] = {ox, oy, oz};
+        f(off);
+      }
+}
+
+}  // namespace
+
+// Regrid decision (Sec. 4.5): refine leaves flagged +1 (below max_level), refine further
+// leaves until every new leaf's neighbours (faces, edges, corners) are at most one level
+// coarser, and coarsen a parent whose children are all leaves flagged -1, none refined,
+// when the coarsened parent keeps the 2:1 rule.  New leaves are listed in the order of the
+// old leaves: a kept leaf in place, a refined leaf as its 2^ndim children (child bits
+// x | y<<1 | z<<2 ascending), a coarsened parent at the place of its first child.
+std::string plan_regrid(const HostTree& t, const std::vector<map_problem_desc>& probs, const int8_t* flags,
+                        int max_level, std::vector<map_block_desc>& out) {
+  const int n = t.nleaves, nd = t.ndim;
+  out.clear();
+  std::vector<char> refine(n, 0);
+  std::vector<int> work;
+  for (int l = 0; l < n; ++l) {
+    const int id = t.leaf_to_block[l];
+    if (flags[l] > 0 && t.blk_level[id] < max_level) {
+      refine[id] = 1;
+      work.push_back(id);
+    }
+  }
+  // balance: children of a refined leaf at level L+1 need neighbours at level >= L
+  while (!work.empty()) {
+    const int id = work.back();
+    work.pop_back();
+    const int p = t.blk_problem[id], L = t.blk_level[id];
+    const int* c = &t.blk_ijk[3 * id];
+    for_each_offset(nd, [&](const int* off) {
+      int q[3];
+      if (!neighbour(probs, nd, p, L, c, off, q)) return;
+      const int cov = covering_leaf(t, p, L, q);
+      if (cov < 0 || refine[cov]) return;
+      if (t.blk_level[cov] < L) {
+        if (t.blk_level[cov] >= max_level) return;  // cannot happen in a balanced tree
+        refine[cov] = 1;
+        work.push_back(cov);
+      }
+    });
+  }
+  // coarsening candidates: parents whose children are all leaves flagged -1, none refined
+  std::vector<char> coarsen(t.nblocks, 0);
+  std::vector<int> flag_of(n, 0);
+  for (int l = 0; l < n; ++l) flag_of[t.leaf_to_block[l]] = flags[l];
+  for (int par = n; par < t.nblocks; ++par) {
+    bool ok = true;
+    for (int cb = 0; cb < (1 << nd) && ok; ++cb) {
+      const int ch = t.children[(size_t)par * 8 + cb];
+      if (ch < 0 || ch >= n || flag_of[ch] >= 0 || refine[ch]) ok = false;
+    }
+    if (ok) coarsen[par] = 1;
+  }
+  // a coarsened parent at level L-1 may not touch a block that stays refined below L or a
+  // leaf at level L that is being refined; drop such candidates until none is left
+  bool changed = true;
+  while (changed) {
+    changed = false;
+    for (int par = n; par < t.nblocks; ++par) {
+      if (!coarsen[par]) continue;
+      const int p = t.blk_problem[par], L = t.blk_level[par] + 1;   // children level
+      const int* c = &t.blk_ijk[3 * par];
+      bool bad = false;
+      for_each_offset(nd, [&](const int* off) {
+        if (bad) return;
+        int q[3];
+        if (!neighbour(probs, nd, p, L - 1, c, off, q)) return;
+        const int nb = t.find(p, L - 1, q[0], q[1], q[2]);
+        if (nb < 0 || nb < n) return;                 // coarser or a leaf at L-1: fine
+        // neighbour parent at L-1: its children touching us must end at level <= L
+        if (coarsen[nb]) return;
+        for (int cb = 0; cb < (1 << nd); ++cb) {
+          bool touch = true;
+          for (int d = 0; d < nd; ++d) {
+            const int bit = (cb >> d) & 1;
+            if (off[d] == 1 && bit != 0) touch = false;
+            if (off[d] == -1 && bit != 1) touch = false;
+          }
+          if (!touch) continue;
+          const int ch = t.children[(size_t)nb * 8 + cb];
+          if (ch >= n || refine[ch]) bad = true;
+        }
+      });
+      if (bad) {
+        coarsen[par] = 0;
+        changed = true;
+      }
+    }
+  }
+  std::vector<char> emitted(t.nblocks, 0);
+  for (int l = 0; l < n; ++l) {
+    const int id = t.leaf_to_block[l];
+    const int p = t.blk_problem[id], L = t.blk_level[id];
+    const int* c = &t.blk_ijk[3 * id];
+    int par = -1;
+    if (L > 0) par = t.find(p, L - 1, c[0] >> 1, c[1] >> 1, c[2] >> 1);
+    if (par >= 0 && coarsen[par]) {
+      if (!emitted[par]) {
+        emitted[par] = 1;
+        map_block_desc b;
+        b.problem = p;
+        b.level = L - 1;
+        for (int d = 0; d < 3; ++d) b.ijk[d] = t.blk_ijk[3 * par + d];
+        out.push_back(b);
+      }
+    } else if (refine[id]) {
+      for (int cb = 0; cb < (1 << nd); ++cb) {
+        map_block_desc b;
+        b.problem = p;
+        b.level = L + 1;
+        b.ijk[0] = 2 * c[0] + (cb & 1);
+        b.ijk[1] = 2 * c[1] + ((cb >> 1) & 1);
+        b.ijk[2] = nd == 3 ? 2 * c[2] + ((cb >> 2) & 1) : 0;
+        out.push_back(b);
+      }
+    } else {
+      map_block_desc b;
+      b.problem = p;
+      b.level = L;
+      for (int d = 0; d < 3; ++d) b.ijk[d] = c[d];
+      out.push_back(b);
+    }
+  }
+  return "";
+}
+
+}  // namespace mapgb
