@@ -184,3 +184,105 @@ __device__ __forceinline__ T weno_plus_left(T um, T u0, T up) {
 }
 
 }  // namespace mapgb
+
+// ---- paired FP32 evaluation (sm_100+ f32x2 arithmetic) ---------------------------------
+// The two states of a face (or the two half-states u +- phi/2 of the MUSCL-Hancock step)
+// are evaluated together, one state per lane of a float2, so each paired instruction does
+// the work of two.  Division-free except one reciprocal of rho per state.
+namespace mapgb {
+namespace pair {
+
+__device__ __forceinline__ float2 add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 sub(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
+__device__ __forceinline__ float2 mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 splat(float a) { return make_float2(a, a); }
+
+// van Leer / minmod on two lanes at once
+template <int LIM>
+__device__ __forceinline__ float2 limiter2(float2 a, float2 b) {
+  if (LIM == 0) return make_float2(minmod<float>(a.x, b.x), minmod<float>(a.y, b.y));
+  const float2 pr = mul(a, b);
+  const float2 s = add(a, b);
+  const float2 q = mul(splat(2.0f), pr);
+  return make_float2(pr.x > 0.0f ? q.x / s.x : 0.0f, pr.y > 0.0f ? q.y / s.y : 0.0f);
+}
+
+// pressure of two states (same FP64 fallback rule as pressure<float>)
+__device__ __forceinline__ float2 pressure2(const float2* w, const Phys<float>& P, float2 ir) {
+  float2 m2 = mul(w[MX], w[MX]);
+  m2 = fma(w[MY], w[MY], m2);
+  m2 = fma(w[MZ], w[MZ], m2);
+  float2 b2 = mul(w[BX], w[BX]);
+  b2 = fma(w[BY], w[BY], b2);
+  b2 = fma(w[BZ], w[BZ], b2);
+  const float2 kin = mul(mul(splat(0.5f), m2), ir);
+  const float2 eint = sub(sub(w[EN], kin), mul(splat(0.5f), b2));
+  float2 p = mul(splat(P.gm1), eint);
+  if (eint.x < P.tau * w[EN].x || eint.y < P.tau * w[EN].y) {
+    float wx[NV], wy[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) { wx[v] = w[v].x; wy[v] = w[v].y; }
+    if (eint.x < P.tau * w[EN].x) p.x = pressure<float>(wx, P);
+    if (eint.y < P.tau * w[EN].y) p.y = pressure<float>(wy, P);
+  }
+  return p;
+}
+
+// physical flux in direction D of two states; if alpha != nullptr also their local speeds
+template <int D>
+__device__ __forceinline__ void flux2(const float2* w, const Phys<float>& P, float2* f, float2* alpha) {
+  const float2 ir = make_float2(1.0f / w[RHO].x, 1.0f / w[RHO].y);
+  const float2 p = pressure2(w, P, ir);
+  const float2 v0 = mul(w[MX], ir), v1 = mul(w[MY], ir), v2 = mul(w[MZ], ir);
+  float2 b2 = mul(w[BX], w[BX]);
+  b2 = fma(w[BY], w[BY], b2);
+  b2 = fma(w[BZ], w[BZ], b2);
+  const float2 pt = fma(splat(0.5f), b2, p);
+  float2 vb = mul(v0, w[BX]);
+  vb = fma(v1, w[BY], vb);
+  vb = fma(v2, w[BZ], vb);
+  const float2 vd = D == 0 ? v0 : (D == 1 ? v1 : v2);
+  const float2 bd = w[BX + D];
+  const float2 md = w[MX + D];
+  const float2 nbd = make_float2(-bd.x, -bd.y);
+  f[RHO] = md;
+  f[MX] = fma(nbd, w[BX], mul(md, v0));
+  f[MY] = fma(nbd, w[BY], mul(md, v1));
+  f[MZ] = fma(nbd, w[BZ], mul(md, v2));
+  f[MX + D] = add(f[MX + D], pt);
+  f[BX] = D == 0 ? w[PSI] : fma(nbd, v0, mul(vd, w[BX]));
+  f[BY] = D == 1 ? w[PSI] : fma(nbd, v1, mul(vd, w[BY]));
+  f[BZ] = D == 2 ? w[PSI] : fma(nbd, v2, mul(vd, w[BZ]));
+  f[EN] = fma(nbd, vb, mul(vd, add(w[EN], pt)));
+  f[PSI] = mul(splat(P.ch * P.ch), bd);
+  if (alpha) {
+    const float2 pc = make_float2(p.x > 0.0f ? p.x : 0.0f, p.y > 0.0f ? p.y : 0.0f);
+    const float2 a2 = mul(mul(splat(P.gamma), pc), ir);
+    const float2 bb = mul(b2, ir);
+    const float2 bd2 = mul(mul(bd, bd), ir);
+    const float2 s = add(a2, bb);
+    float2 disc = fma(mul(splat(-4.0f), a2), bd2, mul(s, s));
+    disc.x = disc.x > 0.0f ? disc.x : 0.0f;
+    disc.y = disc.y > 0.0f ? disc.y : 0.0f;
+    const float2 inner = mul(splat(0.5f), add(s, make_float2(sqrtf(disc.x), sqrtf(disc.y))));
+    const float2 vn = mul(md, ir);
+    *alpha = make_float2(fabsf(vn.x) + sqrtf(inner.x), fabsf(vn.y) + sqrtf(inner.y));
+  }
+}
+
+// Lax-Friedrichs flux of the face whose left state is lane x and right state lane y
+template <int D>
+__device__ __forceinline__ void lf_flux2(const float2* ab, const Phys<float>& P, float* f) {
+  float2 F[NV], al;
+  flux2<D>(ab, P, F, &al);
+  const float a = al.x > al.y ? al.x : al.y;
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    const float s = glm_pair<D>(v) ? P.ch : a;
+    f[v] = 0.5f * ((F[v].x + F[v].y) - s * (ab[v].y - ab[v].x));
+  }
+}
+
+}  // namespace pair
+}  // namespace mapgb

@@ -398,10 +398,29 @@ step_kernel(StepArgsT<T> A) {
   const int cown = (ty + NG) * NP + (tx + NG);          // own column, full plane layout
   const int rown = (ty + 1) * RW + (tx + 1);            // own column, ring layout
 
+  // Warp schedule of the per-plane work list: warp-sized units of predictor cells (NPU),
+  // x faces and y faces (NXU each), given greedily to the least-loaded warp with a
+  // predictor unit weighted 7 and a face unit 4 (their relative cost), the same on every
+  // block.  sched[w][15] holds the number of units of warp w.
+  constexpr int NW = NT / 32;
+  constexpr int NPU = (HAS_T || true) ? Pad32<RING>::value / 32 : 0;
+  constexpr int NXU = Pad32<NFACE>::value / 32;
+  constexpr int NU = NPU + 2 * NXU;
+  __shared__ int sched[NW][16];
   if (tid == 0) {
     for (int q = 0; q < UPL; ++q) mbar_init(&bars[q], 1);
     *status = 0;
     fence_mbar_init();
+    int load[NW], cnt[NW];
+    for (int q = 0; q < NW; ++q) { load[q] = 0; cnt[q] = 0; }
+    for (int u = 0; u < NU; ++u) {
+      int best = 0;
+      for (int q = 1; q < NW; ++q)
+        if (load[q] < load[best]) best = q;
+      if (cnt[best] < 15) sched[best][cnt[best]++] = u;
+      load[best] += u < NPU ? 7 : 4;
+    }
+    for (int q = 0; q < NW; ++q) sched[q][15] = cnt[q];
   }
   __syncthreads();
   unsigned phase = 0;                                   // parity bit per u slot
@@ -522,19 +541,32 @@ step_kernel(StepArgsT<T> A) {
 #pragma unroll
           for (int v = 0; v < NV; ++v) tp[v * RING + r] = acc[v];
         } else {
-          T a[NV], b[NV], fa[NV], fb[NV];
           auto half = [&](auto Dc, const T* plm, int cm, const T* plp, int cp) {
             constexpr int D = decltype(Dc)::value;
+            if constexpr (std::is_same<T, float>::value) {
+              // the two half-states u +- phi/2 in the lanes of a float2
+              float2 ab[NV], fab[NV];
 #pragma unroll
-            for (int v = 0; v < NV; ++v) {
-              T ph = limiter<T, LIM>(w[v] - plm[v * P2 + cm], plp[v * P2 + cp] - w[v]);
-              a[v] = w[v] + T(0.5) * ph;
-              b[v] = w[v] - T(0.5) * ph;
+              for (int v = 0; v < NV; ++v) {
+                const T ph = limiter<T, LIM>(w[v] - plm[v * P2 + cm], plp[v * P2 + cp] - w[v]);
+                ab[v] = pair::fma(pair::splat(ph), make_float2(0.5f, -0.5f), pair::splat(w[v]));
+              }
+              pair::flux2<D>(ab, P, fab, nullptr);
+#pragma unroll
+              for (int v = 0; v < NV; ++v) acc[v] -= lamh[D] * (fab[v].x - fab[v].y);
+            } else {
+              T a[NV], b[NV], fa[NV], fb[NV];
+#pragma unroll
+              for (int v = 0; v < NV; ++v) {
+                T ph = limiter<T, LIM>(w[v] - plm[v * P2 + cm], plp[v * P2 + cp] - w[v]);
+                a[v] = w[v] + T(0.5) * ph;
+                b[v] = w[v] - T(0.5) * ph;
+              }
+              flux_p<T, D>(a, pressure<T>(a, P), P, fa);
+              flux_p<T, D>(b, pressure<T>(b, P), P, fb);
+#pragma unroll
+              for (int v = 0; v < NV; ++v) acc[v] -= lamh[D] * (fa[v] - fb[v]);
             }
-            flux_p<T, D>(a, pressure<T>(a, P), P, fa);
-            flux_p<T, D>(b, pressure<T>(b, P), P, fb);
-#pragma unroll
-            for (int v = 0; v < NV; ++v) acc[v] -= lamh[D] * (fa[v] - fb[v]);
           };
           half(std::integral_constant<int, 0>(), ul[1], c - 1, ul[1], c + 1);
           half(std::integral_constant<int, 1>(), ul[1], c - NP, ul[1], c + NP);
@@ -570,6 +602,18 @@ step_kernel(StepArgsT<T> A) {
         ldw<T, RING>(tp, rl, t0);
         ldw<T, RING>(tp, rl + rs, t1);
         mmc_face<T, D, LIM>(w0, w1, w2, w3, t0, t1, P, F);
+      } else if (std::is_same<T, float>::value && SCHEME == SCH_LF) {
+        float2 ab[NV];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+          const float2 ulo = make_float2(up[v * P2 + cl - st], up[v * P2 + cl]);      // (u_i-1, u_i)
+          const float2 umid = make_float2(up[v * P2 + cl], up[v * P2 + cl + st]);    // (u_i, u_i+1)
+          const float2 uhi = make_float2(up[v * P2 + cl + st], up[v * P2 + cl + 2 * st]);
+          const float2 ph = pair::limiter2<LIM>(pair::sub(umid, ulo), pair::sub(uhi, umid));
+          const float2 tt = make_float2(tp[v * RING + rl], tp[v * RING + rl + rs]);
+          ab[v] = pair::fma(ph, make_float2(0.5f, -0.5f), tt);
+        }
+        pair::lf_flux2<D>(ab, *reinterpret_cast<const Phys<float>*>(&P), reinterpret_cast<float*>(F));
       } else {
         T a[NV], b[NV];
 #pragma unroll
@@ -624,6 +668,20 @@ step_kernel(StepArgsT<T> A) {
         ldw<T, RING>(tslot(z), rown, t0);
         ldw<T, RING>(tslot(z + 1), rown, t1);
         mmc_face<T, 2, LIM>(um1, w1, w2, w3, t0, t1, P, F);
+      } else if (std::is_same<T, float>::value && SCHEME == SCH_LF) {
+        float2 ab[NV];
+        const T* t0p = tslot(z);
+        const T* t1p = tslot(z + 1);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+          const float2 ulo = make_float2(um1[v], p0[v * P2 + cown]);
+          const float2 umid = make_float2(p0[v * P2 + cown], p1[v * P2 + cown]);
+          const float2 uhi = make_float2(p1[v * P2 + cown], p2[v * P2 + cown]);
+          const float2 ph = pair::limiter2<LIM>(pair::sub(umid, ulo), pair::sub(uhi, umid));
+          const float2 tt = make_float2(t0p[v * RING + rown], t1p[v * RING + rown]);
+          ab[v] = pair::fma(ph, make_float2(0.5f, -0.5f), tt);
+        }
+        pair::lf_flux2<2>(ab, *reinterpret_cast<const Phys<float>*>(&P), reinterpret_cast<float*>(F));
       } else {
         T a[NV], b[NV];
 #pragma unroll
@@ -645,19 +703,22 @@ step_kernel(StepArgsT<T> A) {
 
     // work list of one barrier interval: [predictor ring cells of plane zp (if any)] then
     // [x faces of plane zf] then [y faces of plane zf], each padded to whole warps
-    constexpr int PW = Pad32<RING>::value, FW = Pad32<NFACE>::value;
+    // each warp walks its own list of warp-sized units (see the schedule above); units of a
+    // kind that this interval does not run are skipped
     auto work = [&](int zp, bool do_pred, int zf, bool do_faces) {
-      const int npred = do_pred ? PW : 0;
-      const int total = npred + (do_faces ? 2 * FW : 0);
-      for (int it = tid; it < total; it += NT) {
-        if (it < npred) {
-          if (it < RING) predict_cell(zp, it);
-        } else if (it < npred + FW) {
-          const int f = it - npred;
-          if (f < NFACE) do_xface(zf, f);
+      const int wq = tid >> 5, lane = tid & 31;
+      const int cnt = sched[wq][15];
+      for (int k = 0; k < cnt; ++k) {
+        const int u = sched[wq][k];
+        if (u < NPU) {
+          const int r = u * 32 + lane;
+          if (do_pred && r < RING) predict_cell(zp, r);
+        } else if (u < NPU + NXU) {
+          const int f = (u - NPU) * 32 + lane;
+          if (do_faces && f < NFACE) do_xface(zf, f);
         } else {
-          const int f = it - npred - FW;
-          if (f < NFACE) do_yface(zf, f);
+          const int f = (u - NPU - NXU) * 32 + lane;
+          if (do_faces && f < NFACE) do_yface(zf, f);
         }
       }
     };
