@@ -50,7 +50,7 @@ struct Shell {
 
 template <typename T, int NDIM, int NB>
 __global__ void __launch_bounds__(256) fill_kernel(T* __restrict__ u, const int* __restrict__ blocks,
-                                                   int n, const GhostRegion* __restrict__ regions) {
+                                                   int n, const GhostRegion* __restrict__ regions, int skip_pushed) {
   using G = Geo<NDIM, NB>;
   using SH = Shell<NDIM, NB>;
   constexpr int NP = G::NP, P2 = G::P2, S = G::S;
@@ -69,6 +69,7 @@ __global__ void __launch_bounds__(256) fill_kernel(T* __restrict__ u, const int*
       const int ry = j < NG ? 0 : (j >= NG + NB ? 2 : 1);
       const int rz = NDIM == 3 ? (k < NG ? 0 : (k >= NG + NB ? 2 : 1)) : 1;
       const GhostRegion& gr = reg[rx + 3 * ry + 9 * rz];
+      if (skip_pushed && gr.pushed) continue;      // written by the source's step kernel
       const T* sb = u + (size_t)gr.src * NV * S;
       if (gr.kind == 0) {
         const int si = gr.m[0] * i + gr.a[0], sj = gr.m[1] * j + gr.a[1];

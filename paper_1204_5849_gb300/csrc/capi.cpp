@@ -19,6 +19,7 @@ struct DevTree {
   int* all_leaves = nullptr;   // pool ids 0..n-1 (Morton order)
   int* level_leaves = nullptr; // concatenated by level
   int* level_parents = nullptr;
+  PushEntry* pushes = nullptr;
   std::vector<int> leaf_off, parent_off;  // offsets per level (host)
 };
 
@@ -46,13 +47,14 @@ struct map_pool {
   int tasks_cap = 0;
   bool have_dt = false;
   bool alpha_ready = false;   // dyn.alpha_bits holds alpha_g of the current state
+  bool pushed[3] = {false, false, false};  // buffer q: same-level ghosts written by the last step
   long long launches = 0;
   std::string err;
-  // graph cache (one per starting buffer parity)
-  cudaGraphExec_t graph[2] = {nullptr, nullptr};
-  long long graph_kernels[2] = {0, 0};
+  // graph cache, one per starting buffer parity q and fill kind (2q + 1: residual fill)
+  cudaGraphExec_t graph[4] = {nullptr, nullptr, nullptr, nullptr};
+  long long graph_kernels[4] = {0, 0, 0, 0};
   map_params graph_params{};
-  bool graph_valid[2] = {false, false};
+  bool graph_valid[4] = {false, false, false, false};
 };
 
 static std::string g_create_error;
@@ -90,11 +92,12 @@ static void free_tree(map_pool* pool) {
   cudaFree(pool->dt.all_leaves);
   cudaFree(pool->dt.level_leaves);
   cudaFree(pool->dt.level_parents);
+  cudaFree(pool->dt.pushes);
   pool->dt = DevTree();
 }
 
 static void drop_graphs(map_pool* pool) {
-  for (int q = 0; q < 2; ++q) {
+  for (int q = 0; q < 4; ++q) {
     if (pool->graph[q]) cudaGraphExecDestroy(pool->graph[q]);
     pool->graph[q] = nullptr;
     pool->graph_valid[q] = false;
@@ -210,6 +213,7 @@ static int install_tree(map_pool* pool, HostTree& t) {
   CK(upload(&D.children, t.children, pool->stream));
   CK(upload(&D.leaf_ids, t.leaf_to_block, pool->stream));
   CK(upload(&D.all_leaves, t.all_leaves, pool->stream));
+  CK(upload(&D.pushes, t.pushes, pool->stream));
   std::vector<int> ll, pl;
   D.leaf_off.assign(t.maxlev + 2, 0);
   D.parent_off.assign(t.maxlev + 2, 0);
@@ -253,6 +257,7 @@ static int install_tree(map_pool* pool, HostTree& t) {
   pool->have_tree = true;
   pool->have_dt = false;
   pool->alpha_ready = false;
+  for (int q = 0; q < 3; ++q) pool->pushed[q] = false;
   return MAP_OK;
 }
 
@@ -287,6 +292,7 @@ int map_write_block(map_pool* pool, int leaf, const double* u) {
   CK(cudaMemcpyAsync(pool->staging, u, interior_elems(pool) * sizeof(double), cudaMemcpyHostToDevice, pool->stream));
   pool->have_dt = false;
   pool->alpha_ready = false;
+  pool->pushed[pool->cur] = false;
   return pack(pool, pool->dt.leaf_ids + leaf, 1, 1);
 }
 
@@ -309,6 +315,7 @@ int map_write_leaves(map_pool* pool, const double* u) {
                      pool->stream));
   pool->have_dt = false;
   pool->alpha_ready = false;
+  pool->pushed[pool->cur] = false;
   return pack(pool, pool->dt.leaf_ids, n, 1);
 }
 
@@ -324,10 +331,13 @@ int map_read_leaves(map_pool* pool, double* u) {
   return MAP_OK;
 }
 
-// ghost fill on state buffer q: restriction bottom-up, then level passes top-down
+// ghost fill on state buffer q: restriction bottom-up, then level passes top-down.  When
+// the last step kernel writing buffer q already wrote the same-level copies, only the rest
+// is filled (and levels without any such region are skipped).
 static int fill_on(map_pool* pool, int q) {
   const HostTree& t = pool->tree;
   const DevTree& D = pool->dt;
+  const bool residual = pool->pushed[q];
   for (int L = t.maxlev - 1; L >= 0; --L) {
     RestrictLaunch R;
     R.u = pool->buf[q];
@@ -337,11 +347,13 @@ static int fill_on(map_pool* pool, int q) {
     CK(DISPATCH(pool, restrict, R));
   }
   for (int L = 0; L <= t.maxlev; ++L) {
+    if (residual && !t.level_has_residual[L]) continue;
     FillLaunch F;
     F.u = pool->buf[q];
     F.blocks = D.level_leaves + D.leaf_off[L];
     F.nblocks = D.leaf_off[L + 1] - D.leaf_off[L];
     F.regions = D.regions;
+    F.skip_pushed = residual ? 1 : 0;
     CK(DISPATCH(pool, fill, F));
   }
   return MAP_OK;
@@ -451,6 +463,7 @@ static int step_launches(map_pool* pool, const map_params* p, bool fused) {
   S.err_word = pool->err_word;
   S.sums = fused ? pool->sums : nullptr;
   S.dyn_next = fused ? pool->dyn : nullptr;
+  S.pushes = pool->dt.pushes;
   const int in = pool->cur, out = 1 - pool->cur;
   // the plain FP64 form launches once per level; the FP32 form once over all leaves
   auto run = [&](const void* uin, void* uout, const void* ubase, int stage, bool with_fused) -> int {
@@ -482,6 +495,7 @@ static int step_launches(map_pool* pool, const map_params* p, bool fused) {
   if (p->scheme == MAP_WENO) {
     rc = run(pool->buf[in], pool->buf[2], nullptr, 1, false);
     if (rc) return rc;
+    pool->pushed[2] = true;
     rc = fill_on(pool, 2);
     if (rc) return rc;
     rc = run(pool->buf[2], pool->buf[out], pool->buf[in], 2, fused);
@@ -491,6 +505,7 @@ static int step_launches(map_pool* pool, const map_params* p, bool fused) {
     if (rc) return rc;
   }
   pool->cur = out;
+  pool->pushed[out] = true;
   return MAP_OK;
 }
 
@@ -535,7 +550,8 @@ int map_advance(map_pool* pool, const map_params* p, int nsteps) {
   }
   for (int s = 0; s < nsteps; ++s) {
     const int q = pool->cur;
-    if (!pool->graph_valid[q]) {
+    const int gi = 2 * q + (pool->pushed[q] ? 1 : 0);
+    if (!pool->graph_valid[gi]) {
       // first step from this buffer: run eagerly (this also sets kernel attributes), then
       // capture the same sequence starting from buffer q for later replays
       rc = advance_once(pool, p);
@@ -552,9 +568,9 @@ int map_advance(map_pool* pool, const map_params* p, int nsteps) {
           cudaGraphGetNodes(g, nullptr, &nnodes);
           cudaGraphExec_t ex = nullptr;
           if (cudaGraphInstantiate(&ex, g, 0) == cudaSuccess) {
-            pool->graph[q] = ex;
-            pool->graph_valid[q] = true;
-            pool->graph_kernels[q] = pool->launches - before;
+            pool->graph[gi] = ex;
+            pool->graph_valid[gi] = true;
+            pool->graph_kernels[gi] = pool->launches - before;
             (void)nnodes;
           }
         }
@@ -566,9 +582,10 @@ int map_advance(map_pool* pool, const map_params* p, int nsteps) {
       if (rc) return rc;
       continue;
     }
-    CK(cudaGraphLaunch(pool->graph[q], pool->stream));
-    pool->launches += pool->graph_kernels[q];
+    CK(cudaGraphLaunch(pool->graph[gi], pool->stream));
+    pool->launches += pool->graph_kernels[gi];
     pool->cur = 1 - q;
+    pool->pushed[1 - q] = true;
   }
   pool->have_dt = false;
   return MAP_OK;
@@ -632,7 +649,7 @@ int map_regrid(map_pool* pool, const map_block_desc* leaves, int n) {
   CK(DISPATCH(pool, regrid, R));
   CK(cudaStreamSynchronize(pool->stream));
   pool->cur = 1 - pool->cur;
-  return install_tree(pool, t);   // also clears alpha_ready
+  return install_tree(pool, t);   // also clears alpha_ready and the pushed-ghost flags
 }
 
 int map_plan_regrid(map_pool* pool, const int8_t* flags, int max_level, map_block_desc* out, int cap,

@@ -34,6 +34,7 @@ cudaError_t launch_step_one(const StepLaunch& L, cudaStream_t s) {
   A.err_word = L.err_word;
   A.sums = L.sums;
   A.dyn_next = L.dyn_next;
+  A.pushes = L.pushes;
   const int grid = L.grid > 0 ? (L.grid < L.nblocks ? L.grid : L.nblocks) : L.nblocks;
   if (grid <= 0) return cudaSuccess;
   kern<<<grid, NB * NB, smem, s>>>(A);
@@ -90,7 +91,7 @@ cudaError_t launch_fill_T(const KernelConfig& kc, const FillLaunch& L, cudaStrea
   if (L.nblocks <= 0) return cudaSuccess;
   if (cnt) ++*cnt;
 #define CALL_FILL(ND, NBV)                                                                   \
-  fill_kernel<T, ND, NBV><<<grid_for(L.nblocks), 256, 0, s>>>((T*)L.u, L.blocks, L.nblocks, L.regions); \
+  fill_kernel<T, ND, NBV><<<grid_for(L.nblocks), 256, 0, s>>>((T*)L.u, L.blocks, L.nblocks, L.regions, L.skip_pushed); \
   return cudaGetLastError()
   MAPGB_GEO_DISPATCH(kc, CALL_FILL);
 #undef CALL_FILL

@@ -42,7 +42,16 @@ struct GhostRegion {
   int m[3];
   int a[3];
   int corg[3];
-  int pad;
+  int pushed;      // 1: a same-level leaf copy that the source's step kernel writes itself
+};
+
+// Per leaf and direction (dx+1) + 3(dy+1) + 9(dz+1): the same-level neighbour whose ghost
+// region facing this block copies from it, and the index shift from this block's padded
+// cell to that ghost cell (dst = -1: none).  The source cells are the two interior layers
+// next to the shared face, edge or corner.
+struct PushEntry {
+  int dst;
+  int off[3];
 };
 
 // Regrid task for one new leaf (Sec. 4.3 interpolation on the interior).
@@ -64,6 +73,8 @@ struct HostTree {
   std::vector<int> blk_problem, blk_level, blk_ijk;  // ijk: 3 per block
   std::vector<int> children;                // 8 per block (-1 if leaf)
   std::vector<GhostRegion> regions;         // 27 per block (valid for leaves)
+  std::vector<PushEntry> pushes;            // 27 per block (valid for leaves)
+  std::vector<char> level_has_residual;     // per level: a ghost region the fill must do
   std::vector<std::vector<int>> leaves_by_level;   // pool ids
   std::vector<std::vector<int>> parents_by_level;  // pool ids
   std::vector<int> all_leaves;              // pool ids, Morton order
@@ -104,6 +115,7 @@ struct StepLaunch {
   double* sums;            // optional FP64 conservation sums [nprob][9] of the output
   ProbDyn* dyn_next;       // optional: max alpha of the output into dyn_next[p].alpha_bits
   int grid;                // CTAs (0 = one per block)
+  const PushEntry* pushes; // optional: write boundary layers into same-level neighbours' ghosts
 };
 
 struct FillLaunch {
@@ -111,6 +123,7 @@ struct FillLaunch {
   const int* blocks;
   int nblocks;
   const GhostRegion* regions;
+  int skip_pushed;         // 1: leave regions the previous step kernel wrote
 };
 
 struct RestrictLaunch {

@@ -44,6 +44,7 @@ struct StepArgsT {
   unsigned* err_word;
   double* sums;
   ProbDyn* dyn_next;
+  const PushEntry* pushes;
 };
 
 template <int NDIM, int NB>
@@ -392,6 +393,7 @@ step_kernel(StepArgsT<T> A) {
   size_t nf = (size_t)2 * NV * NFACE;
   if (nf < (size_t)(NV + 1) * 32 * 2) nf = (size_t)(NV + 1) * 32 * 2;
   T* sj = sf + nf;
+  __shared__ PushEntry spush[27];
 
   const int tid = threadIdx.x;
   const int tx = tid % NB, ty = tid / NB;
@@ -451,6 +453,7 @@ step_kernel(StepArgsT<T> A) {
       kc[14] = (T)dy.damp;
       kc[15] = (T)dy.ch;
     }
+    if (A.pushes && tid < 27) spush[tid] = A.pushes[(size_t)blk * 27 + tid];   // read after the first barrier
     const T* ub = A.u_in + (size_t)blk * NV * S;
     T* ob = A.u_out + (size_t)blk * NV * S;
     const T* bb = (STAGE == 2) ? A.u_base + (size_t)blk * NV * S : nullptr;
@@ -857,6 +860,28 @@ step_kernel(StepArgsT<T> A) {
       }
 #pragma unroll
       for (int v = 0; v < NV; ++v) ob[(size_t)v * S + gofs] = out[v];
+      if (A.pushes) {
+        // the two interior layers next to a face/edge/corner go into the facing ghost
+        // region of the same-level neighbour there (padded 2,3 -> low side, NB,NB+1 -> high)
+        const int x = tx + NG, y = ty + NG;
+        const int fx = x < 2 * NG ? -1 : (x >= NB ? 1 : 0);
+        const int fy = y < 2 * NG ? -1 : (y >= NB ? 1 : 0);
+        const int fz = NDIM == 3 ? (z < 2 * NG ? -1 : (z >= NB ? 1 : 0)) : 0;
+        if (fx | fy | fz) {
+          for (int kz = 0; kz < (fz ? 2 : 1); ++kz)
+            for (int ky = 0; ky < (fy ? 2 : 1); ++ky)
+              for (int kx = 0; kx < (fx ? 2 : 1); ++kx) {
+                const int ex = kx ? fx : 0, ey = ky ? fy : 0, ez = kz ? fz : 0;
+                if (!(ex | ey | ez)) continue;
+                const PushEntry pe = spush[(ex + 1) + 3 * (ey + 1) + 9 * (ez + 1)];
+                if (pe.dst < 0) continue;
+                T* db = A.u_out + (size_t)pe.dst * NV * S;
+                const size_t dc = ((size_t)(z + pe.off[2]) * NP + (y + pe.off[1])) * NP + (x + pe.off[0]);
+#pragma unroll
+                for (int v = 0; v < NV; ++v) db[(size_t)v * S + dc] = out[v];
+              }
+        }
+      }
       if (STAGE != 1) {
         bool fin = true;
 #pragma unroll

@@ -300,6 +300,33 @@ std::string build_tree(int ndim, int nb, const std::vector<map_problem_desc>& pr
           t.regions[(size_t)id * 27 + rx + 3 * ry + 9 * rz] = g;
         }
   }
+  // pushes: a same-level leaf copy with an affine map in every dimension is written by the
+  // source block's step kernel into the destination's ghost region
+  t.pushes.assign((size_t)NB * 27, PushEntry{-1, {0, 0, 0}});
+  t.level_has_residual.assign(t.maxlev + 1, 0);
+  for (int id = 0; id < n; ++id) {
+    for (int rz = 0; rz < 3; ++rz)
+      for (int ry = 0; ry < 3; ++ry)
+        for (int rx = 0; rx < 3; ++rx) {
+          if (ndim == 2 && rz != 1) continue;
+          if (rx == 1 && ry == 1 && rz == 1) continue;
+          GhostRegion& g = t.regions[(size_t)id * 27 + rx + 3 * ry + 9 * rz];
+          g.pushed = 0;
+          bool affine = true;
+          for (int d = 0; d < ndim; ++d) affine = affine && g.m[d] == 1;
+          if (g.kind == 0 && affine && g.src < n && t.blk_level[g.src] == t.blk_level[id]) {
+            // seen from the source, this block lies in direction -(r - 1)
+            const int dir = (1 - (rx - 1)) + 3 * (1 - (ry - 1)) + 9 * (ndim == 3 ? 1 - (rz - 1) : 1);
+            PushEntry& pe = t.pushes[(size_t)g.src * 27 + dir];
+            if (pe.dst < 0) {
+              pe.dst = id;
+              for (int d = 0; d < 3; ++d) pe.off[d] = d < ndim ? -g.a[d] : 0;
+              g.pushed = 1;
+            }
+          }
+          if (!g.pushed) t.level_has_residual[t.blk_level[id]] = 1;
+        }
+  }
   // level lists, per-problem minimum spacing
   t.leaves_by_level.assign(t.maxlev + 1, {});
   t.parents_by_level.assign(t.maxlev + 1, {});

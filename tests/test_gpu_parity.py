@@ -165,6 +165,64 @@ def test_fp64_mixed_levels_every_scheme(gpulib, scheme):
     assert rel_max(pool.read_leaves(), orc.get_state()).max() <= 1e-12
 
 
+# --- same-level ghosts written by the step kernel itself -----------------------------------
+# After a step, same-level copy regions are written by the source block's step kernel and the
+# next fill only does the rest (prolongation, restriction-fed copies, outflow clamps).  Each
+# second and third step reads those ghosts, so any missing or misplaced cell shows here.
+
+_PUSH_GEOMS = {
+    "2d_periodic_3x2": lambda: w.uniform_mesh(2, 16, (3, 2)),
+    "2d_self_periodic_1x1": lambda: w.uniform_mesh(2, 16, (1, 1)),
+    "2d_outflow_2x3": lambda: w.uniform_mesh(2, 8, (2, 3), bc=w.mesh.OUTFLOW),
+    "3d_periodic_2x3x2": lambda: w.uniform_mesh(3, 8, (2, 3, 2)),
+    "3d_self_periodic_1x1x1": lambda: w.uniform_mesh(3, 8, (1, 1, 1)),
+    "3d_slab_mixed_bc": lambda: w.slab_amr_mesh(3, 8, (2, 4, 2), 1, half_widths=(0.1,)),
+    "2d_amr_outflow": lambda: w.radial_amr_mesh(2, 8, (2, 2), 2, radii=(0.16, 0.34)),
+    "3d_amr_outflow": lambda: w.radial_amr_mesh(3, 8, (4, 4, 4), 1, radii=(0.2,)),
+}
+
+
+@pytest.mark.parametrize("geom", sorted(_PUSH_GEOMS))
+@pytest.mark.parametrize("scheme", ["mmc", "weno"])
+def test_fp64_pushed_ghosts_three_steps(gpulib, geom, scheme):
+    from paper_1204_5849_gb300 import MAP_FP64
+    mesh = _PUSH_GEOMS[geom]()
+    U0 = w.evaluate_on_mesh(mesh, _smooth_2d if mesh.ndim == 2 else _smooth_3d)
+    p = P(scheme=scheme)
+    pool = pool_for(mesh, MAP_FP64, U0)
+    orc = Oracle(mesh, U0)
+    lockstep(pool, orc, p, 3)
+    assert rel_max(pool.read_leaves(), orc.get_state()).max() <= 1e-12
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_advance_write_advance(gpulib, prec):
+    """A host write between advances invalidates the pushed ghosts: the next step must fill
+    every region again, including under graph replay (graphs for both fill kinds)."""
+    mesh = w.radial_amr_mesh(2, 8, (2, 2), 1, radii=(0.3,), bc=w.mesh.PERIODIC,
+                             lo=(0, 0, 0), hi=(1, 1, 1), centre=(0.5, 0.5, 0))
+    U0 = w.evaluate_on_mesh(mesh, _smooth_2d)
+    p = P(scheme="lf", limiter="vanleer")
+    a = pool_for(mesh, prec, U0)
+    b = pool_for(mesh, prec, U0)
+    for rep in range(3):
+        a.advance(p, 3)
+        mid = a.read_leaves()
+        mid[:, 0] *= 1.0 + 0.01 * (rep + 1)
+        mid[:, 7] *= 1.0 + 0.02 * (rep + 1)
+        a.write_leaves(mid)
+        b.write_leaves(mid)
+    a.advance(p, 4)
+    for _ in range(4):
+        b.fill_ghosts(); b.cfl_dt(p); b.step(p)
+    if prec == 0:
+        orc = Oracle(mesh, mid)
+        orc.advance(p, 4)
+        assert rel_max(a.read_leaves(), orc.get_state()).max() <= 1e-12
+    np.testing.assert_array_equal(a.read_leaves(), b.read_leaves())
+    assert a.check() == 0
+
+
 # --- several independent problems of uneven sizes -----------------------------------------
 
 def test_fp64_ensemble(gpulib):
