@@ -24,6 +24,37 @@
 #include <stdlib.h>
 #include <string.h>
 
+/* Flop counting (built only into the separate counting library, see build.py): each
+ * routine adds the floating-point operations it executes (+ - * / sqrt exp log, one each;
+ * comparisons, fabs, min/max and negation are not counted) to one of three counters:
+ * 0 per-cell work on the one-cell ring around the interior (slopes, predictor),
+ * 1 per-face work, which the update loops evaluate once from each side of a face,
+ * 2 per-interior-cell work (update, sources, Runge-Kutta combination, damping).
+ * The predictor of MMC is counted as executed (each face from both sides) under 0. */
+#ifdef ORACLE_COUNT_FLOPS
+static unsigned long long g_flops[4];   /* [3]: outside the step (checks, ghost fill) */
+static int g_flcat = 2;
+#define FLOPS(n) (g_flops[g_flcat] += (unsigned long long)(n))
+#define FLCAT(c) (g_flcat = (c))
+#else
+#define FLOPS(n) ((void)0)
+#define FLCAT(c) ((void)0)
+#endif
+
+int orc_flop_counts(unsigned long long* out3, int reset) {
+#ifdef ORACLE_COUNT_FLOPS
+  for (int q = 0; q < 3; ++q) {
+    out3[q] = g_flops[q];
+    if (reset) g_flops[q] = 0;
+  }
+  return 1;
+#else
+  for (int q = 0; q < 3; ++q) out3[q] = 0;
+  (void)reset;
+  return 0;
+#endif
+}
+
 #define NV 9
 enum { RHO = 0, MX = 1, MY = 2, MZ = 3, BX = 4, BY = 5, BZ = 6, EN = 7, PSI = 8 };
 #define NG 2
@@ -58,6 +89,7 @@ static double pressure(const double* w, double gamma) {
   /* e = p/(gamma-1) + rho v^2/2 + B^2/2  (Sec. 2)  =>  p = (gamma-1)(e - m^2/(2 rho) - B^2/2) */
   double m2 = w[MX] * w[MX] + w[MY] * w[MY] + w[MZ] * w[MZ];
   double b2 = w[BX] * w[BX] + w[BY] * w[BY] + w[BZ] * w[BZ];
+  FLOPS(17);
   return (gamma - 1.0) * (w[EN] - 0.5 * m2 / w[RHO] - 0.5 * b2);
 }
 
@@ -78,6 +110,7 @@ void orc_flux(int d, const double* w, double gamma, double ch, double* f) {
   for (int j = 0; j < 3; ++j) f[BX + j] = (j == d) ? w[PSI] : v[d] * B[j] - B[d] * v[j];
   f[EN] = v[d] * (w[EN] + pt) - B[d] * vb;
   f[PSI] = ch * ch * B[d];
+  FLOPS(37);
 }
 
 /* Local maximum speed in direction d: |v_d| + fast magnetosonic speed (reading of the
@@ -94,6 +127,7 @@ double orc_alpha(int d, const double* w, double gamma) {
   double disc = s * s - 4.0 * a2 * bd2;
   if (disc < 0.0) disc = 0.0;
   double cf = sqrt(0.5 * (s + sqrt(disc)));
+  FLOPS(21);
   return fabs(w[MX + d] / rho) + cf;
 }
 
@@ -115,6 +149,7 @@ void orc_lf_flux(int d, const double* a, const double* b, double gamma, double c
     double s = comp_speed(v, d, alpha, ch);
     f[v] = 0.5 * ((fa[v] + fb[v]) - s * (b[v] - a[v]));
   }
+  FLOPS(5 * NV);
 }
 
 static double minmod(double a, double b) {
@@ -131,7 +166,12 @@ static double minmod(double a, double b) {
  * denominator gives 0. */
 double orc_limiter(int kind, double a, double b) {
   if (kind == 0) return minmod(a, b);
-  if (kind == 1) return (a * b > 0.0) ? (2.0 * a * b) / (a + b) : 0.0;
+  if (kind == 1) {
+    FLOPS(1);
+    if (!(a * b > 0.0)) return 0.0;
+    FLOPS(4);
+    return (2.0 * a * b) / (a + b);
+  }
   if (b == 0.0) return 0.0;
   return (fabs(a) <= fabs(b)) ? a : b;
 }
@@ -147,6 +187,7 @@ void orc_weno_faces(double um, double u0, double up, double* minus_right, double
   double am = 1.0 / ((eps + dm * dm) * (eps + dm * dm));
   double wm = 0.5 * (u0 + up), vm = 0.5 * (3.0 * u0 - um);
   double wp = 0.5 * (3.0 * u0 - up), vp = 0.5 * (u0 + um);
+  FLOPS(38);
   *minus_right = (2.0 * ap * wm + am * vm) / (2.0 * ap + am);
   *plus_left = (ap * wp + 2.0 * am * vp) / (ap + 2.0 * am);
 }
@@ -154,6 +195,7 @@ void orc_weno_faces(double um, double u0, double up, double* minus_right, double
 /* Conservative linear prolongation along one axis (Sec. 4.3, Matsumoto 2007): fine cell
  * value from the coarse cell and its two neighbours; odd = fine cell on the + side. */
 double orc_prolong_1d(double um, double u0, double up, int odd) {
+  FLOPS(4);
   return u0 + minmod(up - u0, u0 - um) * (odd ? 0.25 : -0.25);
 }
 
@@ -205,12 +247,14 @@ static void eglm_source(const geom* g, const double* u, int c, const double* dx,
   }
   for (int j = 0; j < 3; ++j) s[MX + j] += -divb * u[(BX + j) * g->S + c];
   s[EN] += -bgpsi;
+  FLOPS(9 * g->ndim + 7);
 }
 
 /* central difference of field f (one component, stride S) along d, 0 outside ndim */
 static double cdiff(const geom* g, const double* f, int c, int d, const double* dx) {
   if (d >= g->ndim) return 0.0;
   int o = g->off[d];
+  FLOPS(3);
   return (f[c + o] - f[c - o]) / (2.0 * dx[d]);
 }
 
@@ -225,6 +269,7 @@ static void current_density(const geom* g, const double* u, const double* dx, do
     J[0 * g->S + c] = cdiff(g, bz, c, 1, dx) - cdiff(g, by, c, 2, dx);
     J[1 * g->S + c] = cdiff(g, bx, c, 2, dx) - cdiff(g, bz, c, 0, dx);
     J[2 * g->S + c] = cdiff(g, by, c, 0, dx) - cdiff(g, bx, c, 1, dx);
+    FLOPS(3);
   }
 }
 
@@ -261,6 +306,7 @@ static void resistive_source(const geom* g, const double* u, const double* J, in
   s[BY] += ry;
   s[BZ] += rz;
   s[EN] += re;
+  FLOPS(13 + 12 * g->ndim);
 }
 
 /* ------------------------------------------------------------------------------------ */
@@ -270,7 +316,27 @@ typedef struct {
   double gamma, ch, dt, eta;
   int eglm, limiter;
   double dx[3];
+  double* freg;   /* face register of the block (reflux), or NULL */
+  double fw;      /* weight of this update's fluxes in the register (1, or 1/2 per RK2 stage) */
 } stepctx;
+
+/* Face register (reflux, Sec. 4.2 step (2)): the flux through every boundary face cell of a
+ * block, summed over the step's flux evaluations with weight fw.  Layout
+ * [side][NV][nb][nb], side = 2d (low face of dimension d) or 2d + 1 (high face); the face
+ * cell is indexed t0 + nb t1 by its interior coordinates in the two other dimensions, in
+ * increasing dimension order (t1 = 0 in 2D). */
+static void record_face(const geom* g, const stepctx* s, int d, int side, int k, int j, int i,
+                        const double* f) {
+  if (!s->freg) return;
+  int x = i - NG, y = j - NG, z = g->ndim == 3 ? k - NG : 0;
+  int t0 = d == 0 ? y : x, t1 = d == 2 ? y : z;
+  size_t nb2 = (size_t)g->nb * g->nb;
+  double* r = s->freg + (size_t)(2 * d + side) * NV * nb2 + (size_t)t1 * g->nb + t0;
+  for (int v = 0; v < NV; ++v) r[v * nb2] += s->fw * f[v];
+}
+
+/* Interior coordinate of padded cell (k, j, i) along d. */
+static int icoord(int d, int k, int j, int i) { return (d == 0 ? i : d == 1 ? j : k) - NG; }
 
 /* MMC (Sec. 3.1).  Split fluxes f^+- = (f +- alpha u)/2.  Reading of the local speeds:
  * each face i+1/2 carries alpha = max(alpha(u_i), alpha(u_{i+1})) and
@@ -278,8 +344,8 @@ typedef struct {
  * (h and the four g's) is evaluated with the speeds of that face, so a face flux needs
  * u_{i-1..i+2} and u~_{i..i+1} only and the scheme stays conservative (one flux per face).
  * The (B_d, psi) pair uses c_h for both. */
-static double splitp(double f, double a, double u) { return 0.5 * (f + a * u); }
-static double splitm(double f, double a, double u) { return 0.5 * (f - a * u); }
+static double splitp(double f, double a, double u) { FLOPS(3); return 0.5 * (f + a * u); }
+static double splitm(double f, double a, double u) { FLOPS(3); return 0.5 * (f - a * u); }
 
 static void mmc_h(const geom* g, const stepctx* s, int d, const double* u, int cl, double* h) {
   double wl[NV], wr[NV], fl[NV], fr[NV];
@@ -293,6 +359,7 @@ static void mmc_h(const geom* g, const stepctx* s, int d, const double* u, int c
     double a = comp_speed(v, d, alpha, s->ch);
     h[v] = splitp(fl[v], a, wl[v]) + splitm(fr[v], a, wr[v]);
   }
+  FLOPS(NV);
 }
 
 static void mmc_face(const geom* g, const stepctx* s, int d, const double* u, const double* ut,
@@ -322,12 +389,14 @@ static void mmc_face(const geom* g, const stepctx* s, int d, const double* u, co
     double gm_r = splitm(fu[3][v], a, w[3][v]) - splitm(ft[1][v], at, t[1][v]); /* g-_{i+3/2} */
     fhat[v] = h + 0.5 * (orc_limiter(s->limiter, gp_l, gp_c) - orc_limiter(s->limiter, gm_r, gm_c));
   }
+  FLOPS(8 * NV);
 }
 
 static void mmc_block(const geom* g, const stepctx* s, const double* u, double* out) {
   double* ut = (double*)calloc((size_t)NV * g->S, sizeof(double));
   double* J = (double*)calloc((size_t)3 * g->S, sizeof(double));
   /* predictor u~ = u - sum_d dt/dx_d (h_{i+1/2} - h_{i-1/2})  on the margin-1 region */
+  FLCAT(0);
   FOR_REGION(g, 1, k, j, i) {
     int c = cidx(g, k, j, i);
     double acc[NV], hp[NV], hm[NV];
@@ -337,24 +406,33 @@ static void mmc_block(const geom* g, const stepctx* s, const double* u, double* 
       mmc_h(g, s, d, u, c - g->off[d], hm);
       double lam = s->dt / s->dx[d];
       for (int v = 0; v < NV; ++v) acc[v] -= lam * (hp[v] - hm[v]);
+      FLOPS(1 + 3 * NV);
     }
     for (int v = 0; v < NV; ++v) ut[v * g->S + c] = acc[v];
   }
+  FLCAT(0);
   if (s->eta > 0.0) current_density(g, u, s->dx, J);
+  FLCAT(2);
   /* corrector: u^{n+1} = u - sum_d dt/dx_d (fhat_{i+1/2} - fhat_{i-1/2}) + dt S(u^n) */
   FOR_REGION(g, NG, k, j, i) {
     int c = cidx(g, k, j, i);
     double acc[NV], fp[NV], fm[NV], src[NV] = {0};
     load(g, u, c, acc);
     for (int d = 0; d < g->ndim; ++d) {
+      FLCAT(1);
       mmc_face(g, s, d, u, ut, c, fp);
       mmc_face(g, s, d, u, ut, c - g->off[d], fm);
+      FLCAT(2);
+      if (icoord(d, k, j, i) == 0) record_face(g, s, d, 0, k, j, i, fm);
+      if (icoord(d, k, j, i) == g->nb - 1) record_face(g, s, d, 1, k, j, i, fp);
       double lam = s->dt / s->dx[d];
       for (int v = 0; v < NV; ++v) acc[v] -= lam * (fp[v] - fm[v]);
+      FLOPS(1 + 3 * NV);
     }
     if (s->eglm) eglm_source(g, u, c, s->dx, src);
     if (s->eta > 0.0) resistive_source(g, u, J, c, s->dx, s->eta, src);
     for (int v = 0; v < NV; ++v) out[v * g->S + c] = acc[v] + s->dt * src[v];
+    FLOPS(2 * NV);
   }
   free(ut);
   free(J);
@@ -370,6 +448,7 @@ static void lf_block(const geom* g, const stepctx* s, const double* u, double* o
   double* phi = (double*)calloc((size_t)3 * NV * g->S, sizeof(double));
   double* J = (double*)calloc((size_t)3 * g->S, sizeof(double));
   /* slopes phi_d = limiter(u_i - u_{i-1}, u_{i+1} - u_i) on the margin-1 region */
+  FLCAT(0);
   FOR_REGION(g, 1, k, j, i) {
     int c = cidx(g, k, j, i);
     for (int d = 0; d < g->ndim; ++d) {
@@ -377,6 +456,7 @@ static void lf_block(const geom* g, const stepctx* s, const double* u, double* o
       for (int v = 0; v < NV; ++v) {
         const double* f = u + v * g->S;
         phi[(d * NV + v) * g->S + c] = orc_limiter(s->limiter, f[c] - f[c - o], f[c + o] - f[c]);
+        FLOPS(2);
       }
     }
   }
@@ -396,11 +476,14 @@ static void lf_block(const geom* g, const stepctx* s, const double* u, double* o
       orc_flux(d, wm, s->gamma, s->ch, fm);
       double lamh = (0.5 * s->dt) / s->dx[d];
       for (int v = 0; v < NV; ++v) acc[v] -= lamh * (fp[v] - fm[v]);
+      FLOPS(4 * NV + 2 + 3 * NV);
     }
     if (s->eglm) eglm_source(g, u, c, s->dx, src);
     for (int v = 0; v < NV; ++v) ut[v * g->S + c] = acc[v] + (0.5 * s->dt) * src[v];
+    FLOPS(3 * NV);
   }
   if (s->eta > 0.0) current_density(g, u, s->dx, J);
+  FLCAT(2);
   FOR_REGION(g, NG, k, j, i) {
     int c = cidx(g, k, j, i);
     double acc[NV], src[NV] = {0};
@@ -409,6 +492,7 @@ static void lf_block(const geom* g, const stepctx* s, const double* u, double* o
       int o = g->off[d];
       double fl[NV], fr[NV];
       /* face i+1/2: left u~_i + phi_i/2, right u~_{i+1} - phi_{i+1}/2; face i-1/2 alike */
+      FLCAT(1);
       for (int side = 0; side < 2; ++side) {
         int cl = side ? c : c - o;
         double a[NV], b[NV];
@@ -416,14 +500,20 @@ static void lf_block(const geom* g, const stepctx* s, const double* u, double* o
           a[v] = ut[v * g->S + cl] + 0.5 * phi[(d * NV + v) * g->S + cl];
           b[v] = ut[v * g->S + cl + o] - 0.5 * phi[(d * NV + v) * g->S + cl + o];
         }
+        FLOPS(4 * NV);
         orc_lf_flux(d, a, b, s->gamma, s->ch, side ? fr : fl);
       }
+      FLCAT(2);
+      if (icoord(d, k, j, i) == 0) record_face(g, s, d, 0, k, j, i, fl);
+      if (icoord(d, k, j, i) == g->nb - 1) record_face(g, s, d, 1, k, j, i, fr);
       double lam = s->dt / s->dx[d];
       for (int v = 0; v < NV; ++v) acc[v] -= lam * (fr[v] - fl[v]);
+      FLOPS(1 + 3 * NV);
     }
     if (s->eglm) eglm_source(g, ut, c, s->dx, src);
     if (s->eta > 0.0) resistive_source(g, u, J, c, s->dx, s->eta, src);
     for (int v = 0; v < NV; ++v) out[v * g->S + c] = acc[v] + s->dt * src[v];
+    FLOPS(2 * NV);
   }
   free(ut);
   free(phi);
@@ -434,13 +524,16 @@ static void lf_block(const geom* g, const stepctx* s, const double* u, double* o
  * from the same state, summed): L = -sum_d (fhat_{i+1/2} - fhat_{i-1/2})/dx_d + S(w). */
 static void weno_rhs(const geom* g, const stepctx* s, const double* w, double* L) {
   double* J = (double*)calloc((size_t)3 * g->S, sizeof(double));
+  FLCAT(0);
   if (s->eta > 0.0) current_density(g, w, s->dx, J);
+  FLCAT(2);
   FOR_REGION(g, NG, k, j, i) {
     int c = cidx(g, k, j, i);
     double acc[NV] = {0}, src[NV] = {0};
     for (int d = 0; d < g->ndim; ++d) {
       int o = g->off[d];
       double fl[NV], fr[NV];
+      FLCAT(1);
       for (int side = 0; side < 2; ++side) {
         int cl = side ? c : c - o; /* face between cl and cl+o */
         double a[NV], b[NV], dummy;
@@ -451,11 +544,16 @@ static void weno_rhs(const geom* g, const stepctx* s, const double* w, double* L
         }
         orc_lf_flux(d, a, b, s->gamma, s->ch, side ? fr : fl);
       }
+      FLCAT(2);
+      if (icoord(d, k, j, i) == 0) record_face(g, s, d, 0, k, j, i, fl);
+      if (icoord(d, k, j, i) == g->nb - 1) record_face(g, s, d, 1, k, j, i, fr);
       for (int v = 0; v < NV; ++v) acc[v] -= (fr[v] - fl[v]) / s->dx[d];
+      FLOPS(3 * NV);
     }
     if (s->eglm) eglm_source(g, w, c, s->dx, src);
     if (s->eta > 0.0) resistive_source(g, w, J, c, s->dx, s->eta, src);
     for (int v = 0; v < NV; ++v) L[v * g->S + c] = acc[v] + src[v];
+    FLOPS(NV);
   }
   free(J);
 }
@@ -792,6 +890,7 @@ static int sample(const orc_mesh* m, int p, int L, const int* Gin, double* w) {
 int orc_fill_ghosts(orc_mesh* m) {
   geom g = mesh_geom(m);
   int nd = m->ndim, nb = m->nb;
+  FLCAT(3);
   restrict_all(m);
   int status = 0;
   for (int L = 0; L <= m->maxlev; ++L) {
@@ -811,6 +910,7 @@ int orc_fill_ghosts(orc_mesh* m) {
       }
     }
   }
+  FLCAT(2);
   return status;
 }
 
@@ -893,7 +993,70 @@ static stepctx make_ctx(const orc_mesh* m, const orc_params* pr, const oblk* o) 
   s.gamma = pr->gamma; s.eta = pr->eta; s.eglm = pr->eglm; s.limiter = pr->limiter;
   s.dt = m->dt[o->problem]; s.ch = m->ch[o->problem];
   block_dx(m, o, s.dx);
+  s.freg = NULL;
+  s.fw = 1.0;
   return s;
+}
+
+/* Reflux (Sec. 4.2 step (2), after Berger and Colella): a coarse leaf whose same-level
+ * neighbour across a face is refined has updated its cells next to that face with its own
+ * flux there, while the fine leaves on the other side used theirs.  The coarse flux of each
+ * face cell is replaced by the mean of the 2^(ndim-1) fine fluxes covering it:
+ *   u_c += lam (F_fine - F_coarse) on a low face,  u_c -= lam (F_fine - F_coarse) on a high
+ * face, lam = dt / dx_d of the coarse block, so every face carries one flux on both sides.
+ * Faces are applied in the order (d, low then high); fine means sum in the order
+ * (t0, t0+1) and, in 3D, ((f[t1][t0] + f[t1][t0+1]) + (f[t1+1][t0] + f[t1+1][t0+1])). */
+static void apply_reflux(orc_mesh* m, const double* freg) {
+  const int nd = m->ndim, nb = m->nb, h = nb / 2;
+  const size_t nb2 = (size_t)nb * nb, per = (size_t)2 * nd * NV * nb2;
+  geom g = mesh_geom(m);
+  for (int q = 0; q < m->nblocks; ++q) {
+    oblk* o = &m->b[q];
+    if (o->leaf < 0) continue;
+    const int L = o->level, p = o->problem;
+    double dx[3];
+    block_dx(m, o, dx);
+    for (int d = 0; d < nd; ++d)
+      for (int side = 0; side < 2; ++side) {
+        int nbc[3] = {o->ijk[0], o->ijk[1], o->ijk[2]};
+        nbc[d] += side ? 1 : -1;
+        const int n = nblk_dim(m, p, L, d);
+        if (nbc[d] < 0 || nbc[d] >= n) {
+          if (m->probs[p].bc[d][side] != 0) continue;        /* outflow: no neighbour */
+          nbc[d] = (nbc[d] % n + n) % n;
+        }
+        const int nq = lookup(m, p, L, nbc[0], nbc[1], nbc[2]);
+        if (nq < 0 || m->b[nq].leaf >= 0) continue;           /* coarser or same level */
+        const oblk* nbk = &m->b[nq];
+        const int da = d == 0 ? 1 : 0, db = d == 2 ? 1 : 2;
+        const double lam = m->dt[p] / dx[d];
+        const double* rc = freg + (size_t)q * per + (size_t)(2 * d + side) * NV * nb2;
+        for (int t1 = 0; t1 < (nd == 3 ? nb : 1); ++t1)
+          for (int t0 = 0; t0 < nb; ++t0) {
+            int bits[3] = {0, 0, 0};
+            bits[d] = side ? 0 : 1;
+            bits[da] = t0 / h;
+            if (nd == 3) bits[db] = t1 / h;
+            const int cq = nbk->child[bits[0] | (bits[1] << 1) | (bits[2] << 2)];
+            const double* rf = freg + (size_t)cq * per + (size_t)(2 * d + 1 - side) * NV * nb2;
+            const int f0 = 2 * (t0 - bits[da] * h), f1 = nd == 3 ? 2 * (t1 - bits[db] * h) : 0;
+            int ci[3];
+            ci[d] = side ? nb - 1 : 0;
+            ci[da] = t0;
+            if (nd == 3) ci[db] = t1;
+            const int c = cidx(&g, nd == 3 ? ci[2] + NG : 0, ci[1] + NG, ci[0] + NG);
+            for (int v = 0; v < NV; ++v) {
+              const double* fv = rf + v * nb2;
+              double ff;
+              if (nd == 2) ff = 0.5 * (fv[f0] + fv[f0 + 1]);
+              else ff = 0.25 * ((fv[(size_t)f1 * nb + f0] + fv[(size_t)f1 * nb + f0 + 1]) +
+                                (fv[(size_t)(f1 + 1) * nb + f0] + fv[(size_t)(f1 + 1) * nb + f0 + 1]));
+              const double corr = lam * (ff - rc[v * nb2 + (size_t)t1 * nb + t0]);
+              o->u[v * g.S + c] = side ? o->u[v * g.S + c] - corr : o->u[v * g.S + c] + corr;
+            }
+          }
+      }
+  }
 }
 
 static void copy_interior(const geom* g, const double* src, double* dst) {
@@ -906,12 +1069,16 @@ static void copy_interior(const geom* g, const double* src, double* dst) {
 int orc_step(orc_mesh* m, const orc_params* pr) {
   if (!m->have_dt) return -1;
   geom g = mesh_geom(m);
+  /* face registers for reflux, only where a coarse/fine face can exist */
+  const size_t per = (size_t)2 * m->ndim * NV * m->nb * m->nb;
+  double* freg = (pr->reflux && m->maxlev > 0) ? (double*)calloc((size_t)m->nblocks * per, sizeof(double)) : NULL;
   if (pr->scheme == 0 || pr->scheme == 1) {
 #pragma omp parallel for schedule(dynamic)
     for (int q = 0; q < m->nblocks; ++q) {
       oblk* o = &m->b[q];
       if (o->leaf < 0) continue;
       stepctx s = make_ctx(m, pr, o);
+      if (freg) s.freg = freg + (size_t)q * per;
       double* out = (double*)calloc((size_t)NV * g.S, sizeof(double));
       if (pr->scheme == 0) mmc_block(&g, &s, o->u, out);
       else lf_block(&g, &s, o->u, out);
@@ -926,11 +1093,14 @@ int orc_step(orc_mesh* m, const orc_params* pr) {
       oblk* o = &m->b[q];
       if (o->leaf < 0) continue;
       stepctx s = make_ctx(m, pr, o);
+      if (freg) s.freg = freg + (size_t)q * per;
+      s.fw = 0.5;
       double* L = (double*)calloc((size_t)NV * g.S, sizeof(double));
       weno_rhs(&g, &s, o->u, L);
       FOR_REGION(&g, NG, k, j, i) {
         int c = cidx(&g, k, j, i);
         for (int v = 0; v < NV; ++v) o->u1[v * g.S + c] = o->u[v * g.S + c] + s.dt * L[v * g.S + c];
+        FLOPS(2 * NV);
       }
       free(L);
     }
@@ -941,6 +1111,8 @@ int orc_step(orc_mesh* m, const orc_params* pr) {
       oblk* o = &m->b[q];
       if (o->leaf < 0) continue;
       stepctx s = make_ctx(m, pr, o);
+      if (freg) s.freg = freg + (size_t)q * per;
+      s.fw = 0.5;
       double* L = (double*)calloc((size_t)NV * g.S, sizeof(double));
       weno_rhs(&g, &s, o->u, L);
       FOR_REGION(&g, NG, k, j, i) {
@@ -949,12 +1121,18 @@ int orc_step(orc_mesh* m, const orc_params* pr) {
           double un = o->u1[v * g.S + c], us = o->u[v * g.S + c];
           o->u1[v * g.S + c] = 0.5 * ((un + us) + s.dt * L[v * g.S + c]);
         }
+        FLOPS(4 * NV);
       }
       free(L);
     }
     for (int q = 0; q < m->nblocks; ++q) { double* t = m->b[q].u; m->b[q].u = m->b[q].u1; m->b[q].u1 = t; }
   } else {
+    free(freg);
     return -1;
+  }
+  if (freg) {
+    apply_reflux(m, freg);
+    free(freg);
   }
   /* psi damping, exact operator split once per step: psi <- psi exp(-dt c_h^2/c_p^2)
    * (eq. MHD-5 source; equals c_d when c_p comes from the same dt). */
@@ -962,10 +1140,16 @@ int orc_step(orc_mesh* m, const orc_params* pr) {
     oblk* o = &m->b[q];
     if (o->leaf < 0) continue;
     double damp = m->damp[o->problem];
-    FOR_REGION(&g, NG, k, j, i) o->u[PSI * g.S + cidx(&g, k, j, i)] *= damp;
+    FOR_REGION(&g, NG, k, j, i) {
+      o->u[PSI * g.S + cidx(&g, k, j, i)] *= damp;
+      FLOPS(1);
+    }
   }
   m->have_dt = 0;
-  return check_state(m, pr->gamma);
+  FLCAT(3);
+  const int rc = check_state(m, pr->gamma);
+  FLCAT(2);
+  return rc;
 }
 
 int orc_block_step(int ndim, int nb, const orc_params* pr, const double* dx, double dt,
@@ -976,6 +1160,8 @@ int orc_block_step(int ndim, int nb, const orc_params* pr, const double* dx, dou
   s.gamma = pr->gamma; s.eta = pr->eta; s.eglm = pr->eglm; s.limiter = pr->limiter;
   s.dt = dt; s.ch = ch;
   for (int d = 0; d < 3; ++d) s.dx[d] = dx[d];
+  s.freg = NULL;
+  s.fw = 1.0;
   double* out = (double*)calloc((size_t)NV * g.S, sizeof(double));
   if (pr->scheme == 0) mmc_block(&g, &s, in, out);
   else lf_block(&g, &s, in, out);

@@ -32,6 +32,7 @@ typedef struct {
   int scheme;       /* 0 MMC, 1 LF, 2 WENO */
   int limiter;      /* 0 minmod, 1 van Leer, 2 literal Roe form (MMC only) */
   double dt_override; /* > 0: use this dt */
+  int reflux;       /* 1: coarse fluxes at coarse/fine faces replaced by the fine ones */
 } orc_params;
 
 typedef struct {
@@ -67,6 +68,11 @@ int orc_flags(orc_mesh* m, const orc_params* p, const orc_refine* r, signed char
               double* est_max);
 int orc_conservation(const orc_mesh* m, double* sums);
 orc_mesh* orc_regrid(orc_mesh* m, int nleaves, const int* leaves, int* err);
+
+/* Floating-point operation counters of the counting build (liboracle_flops.so): out3 =
+ * {ring-cell work, per-face work counted from both sides, interior-cell work}; reset = 1
+ * zeroes them.  Returns 1 in the counting build, 0 (and zeros) in the normal one. */
+int orc_flop_counts(unsigned long long* out3, int reset);
 
 /* one MMC/LF step of a single ghost-filled block with given dt, c_h and damping factor */
 int orc_block_step(int ndim, int nb, const orc_params* p, const double* dx, double dt,

@@ -24,7 +24,8 @@ class orc_params(C.Structure):
     _fields_ = [("gamma", C.c_double), ("c_cfl", C.c_double), ("ch_mode", C.c_int),
                 ("ch", C.c_double), ("cp_mode", C.c_int), ("c_d", C.c_double),
                 ("cp", C.c_double), ("eta", C.c_double), ("eglm", C.c_int),
-                ("scheme", C.c_int), ("limiter", C.c_int), ("dt_override", C.c_double)]
+                ("scheme", C.c_int), ("limiter", C.c_int), ("dt_override", C.c_double),
+                ("reflux", C.c_int)]
 
 
 class orc_problem(C.Structure):
@@ -40,13 +41,26 @@ class orc_refine(C.Structure):
 
 
 _lib = None
+_flop_lib = None
 
 
 def lib():
     global _lib
     if _lib is None:
-        path = _build.build()
-        L = C.CDLL(path)
+        _lib = _declare(C.CDLL(_build.build()))
+    return _lib
+
+
+def flop_lib():
+    """The counting build (same source, flop counters compiled in, one thread)."""
+    global _flop_lib
+    if _flop_lib is None:
+        _flop_lib = _declare(C.CDLL(_build.build_flop_counter()))
+    return _flop_lib
+
+
+def _declare(L):
+    if True:
         dp = C.POINTER(C.c_double)
         ip = C.POINTER(C.c_int)
         L.orc_create.restype = C.c_void_p
@@ -75,8 +89,8 @@ def lib():
         L.orc_weno_faces.argtypes = [C.c_double, C.c_double, C.c_double, dp, dp]
         L.orc_prolong_1d.restype = C.c_double
         L.orc_prolong_1d.argtypes = [C.c_double, C.c_double, C.c_double, C.c_int]
-        _lib = L
-    return _lib
+        L.orc_flop_counts.argtypes = [C.POINTER(C.c_ulonglong), C.c_int]
+    return L
 
 
 def _dp(a: np.ndarray):
@@ -89,7 +103,7 @@ def make_params(p: Dict) -> orc_params:
                       CP_MODES[p.get("cp_mode", "cd")], float(p.get("c_d", 0.18)),
                       float(p.get("cp", 0.0)), float(p.get("eta", 0.0)), int(p.get("eglm", 1)),
                       SCHEMES[p.get("scheme", "mmc")], LIMITERS[p.get("limiter", "minmod")],
-                      float(p.get("dt_override", 0.0)))
+                      float(p.get("dt_override", 0.0)), int(p.get("reflux", 1)))
 
 
 def make_refine(r: Dict) -> orc_refine:
@@ -372,3 +386,45 @@ def plan_regrid(mesh, flags, max_level: int) -> np.ndarray:
         else:
             out.append(lf)
     return np.asarray(out, dtype=np.int32).reshape(-1, 5)
+
+
+def count_step_flops(mesh, state: np.ndarray, params: Dict) -> Dict[str, float]:
+    """Floating-point operations of one oracle step on ``mesh``, from the counting build.
+
+    Returns the three raw counters and the per-cell-update figure in which every face is
+    counted once: ring / ring cells + faces / (2 interior cells) + cell / interior cells.
+    The update loops evaluate each face from both of its cells, so halving the face counter
+    gives exactly one evaluation per face on a periodic single-level mesh.  Operations of
+    the time-step reduction, the ghost fill and the state check are not counted.
+    """
+    L = flop_lib()
+    leaves = np.ascontiguousarray(mesh.leaves, dtype=np.int32)
+    err = C.c_int(0)
+    probs = _problems(mesh)
+    h = L.orc_create(mesh.ndim, mesh.nb, len(mesh.problems), probs, mesh.nleaves,
+                     leaves.ctypes.data_as(C.POINTER(C.c_int)), C.byref(err))
+    if not h:
+        raise ValueError(f"oracle rejected the mesh (code {err.value})")
+    cnt = (C.c_ulonglong * 3)()
+    try:
+        U = np.ascontiguousarray(state, dtype=np.float64)
+        for q in range(mesh.nleaves):
+            L.orc_set_leaf(h, q, _dp(np.ascontiguousarray(U[q])))
+        L.orc_fill_ghosts(h)
+        dt = np.zeros(len(mesh.problems))
+        pr = make_params(params)
+        L.orc_cfl(h, C.byref(pr), _dp(dt))
+        if L.orc_flop_counts(cnt, 1) != 1:
+            raise RuntimeError("the flop-counting oracle build has no counters")
+        rc = L.orc_step(h, C.byref(pr))
+        if rc != 0:
+            raise RuntimeError(f"oracle step failed ({rc})")
+        L.orc_flop_counts(cnt, 1)
+    finally:
+        L.orc_destroy(h)
+    nb, nd = mesh.nb, mesh.ndim
+    cells = mesh.nleaves * nb ** nd
+    ring = mesh.nleaves * (nb + 2) ** nd
+    ring_f, face_f, cell_f = (float(c) for c in cnt)
+    return {"ring": ring_f, "face": face_f, "cell": cell_f, "cells": cells,
+            "per_cell_update": ring_f / ring + face_f / (2.0 * cells) + cell_f / cells}
