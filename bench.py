@@ -34,6 +34,16 @@ METRIC = "cell-updates/s"
 WORKLOAD = "alfven3d_256^3_lf_vanleer_eglm"
 BYTES_PER_CELL_F32 = 72.0     # read 9 x 4 B + write 9 x 4 B per cell-update
 BYTES_PER_CELL_F64 = 144.0
+# Floating-point operations per cell-update of this workload's step (TVD-LF, van Leer,
+# EGLM, 3D), counted by the flop-counting build of the oracle on the 256^3 initial state
+# with every face counted once (1651.9; the van Leer branch makes it data-dependent, by
+# under 1% between 32^3 and 256^3).
+FLOPS_PER_CELL = 1652.0
+# FP32 peak of the CUDA cores: 152 SMs x 128 FP32 lanes x 2 flop per FMA x SM clock.
+SMS, FP32_LANES_PER_SM = 152, 128
+# DRAM bytes (read + write) of one step-kernel launch on the 128^3 case (512 blocks),
+# from an ncu capture of the current kernel; traffic grows with the block count.
+STEP_KERNEL_DRAM_BYTES_512_BLOCKS = 160.870656e6 + 105.497088e6
 
 
 def peaks():
@@ -42,6 +52,13 @@ def peaks():
         d = json.load(open(path))
         return float(d.get("hbm_gbs", 6800.0)), "measured"
     return 6800.0, "fallback"
+
+
+def sm_max_mhz():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        return float(json.load(open(path)).get("sm_max_mhz", 2070.0)), "measured sm_max_mhz"
+    return 2070.0, "nominal maximum SM clock"
 
 
 class ClockSampler:
@@ -296,13 +313,16 @@ def main():
     clocks.start()
     barrier()
     l0 = pool.kernel_launches()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
-    for _ in range(args.steps):
+    # one event before every step and one after the last: the per-step intervals time the
+    # graph replay of each step (finalize, a 72-byte memset and the step kernel)
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    evs[0].record(stream)
+    for i in range(args.steps):
         pool.advance(params, 1)
-    ev1.record(stream)
+        evs[i + 1].record(stream)
     barrier()
-    ms = ev0.elapsed_time(ev1)
+    ms = evs[0].elapsed_time(evs[-1])
+    step_ms = [evs[i].elapsed_time(evs[i + 1]) for i in range(args.steps)]
     launches = pool.kernel_launches() - l0
     t = torch.tensor([ms], device="cuda")
     if dist is not None:
@@ -311,7 +331,7 @@ def main():
     value = world * ncells * args.steps / (ms_max * 1e-3)
     assert pool.check() == 0, "device error word set during the benchmark"
 
-    # -------- step kernel alone, live CUDA events on the launching stream --------
+    # -------- step kernel alone (map_step, without the fused reductions) ----------------
     pool.fill_ghosts()
     pool.cfl_dt(params)
     nk = min(args.steps, 100)
@@ -324,16 +344,23 @@ def main():
         pool.fill_ghosts()
         pool.cfl_dt(params)
     torch.cuda.synchronize()
-    k_ms = statistics.mean(a.elapsed_time(b) for a, b in kev)
+    k_ms_alone = statistics.mean(a.elapsed_time(b) for a, b in kev)
+    # the dominant kernel's launch duration in the timed region: the mean per-step interval
+    # (an upper bound: it also holds the finalize kernel and the memset, about 10 us)
+    k_ms = statistics.mean(step_ms)
     hbm, peak_kind = peaks()
     achieved = BYTES_PER_CELL_F32 * ncells / (k_ms * 1e-3) / 1e9
+    mhz, mhz_src = sm_max_mhz()
+    fp32_peak = SMS * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12            # TFLOP/s
+    tflops = FLOPS_PER_CELL * ncells / (k_ms * 1e-3) / 1e12
+    traffic = STEP_KERNEL_DRAM_BYTES_512_BLOCKS * mesh.nleaves / 512.0
 
     if args.quick:
         clocks.stop()
         if rank == 0:
             print(json.dumps({"metric": METRIC, "value": value, "ms_per_step": ms_max / args.steps,
-                              "kernel_ms": k_ms, "achieved_gbs": achieved, "cells": ncells,
-                              "gpu_launches": launches}))
+                              "kernel_ms": k_ms, "kernel_ms_alone": k_ms_alone, "achieved_gbs": achieved,
+                              "achieved_tflops": tflops, "cells": ncells, "gpu_launches": launches}))
         return
 
     # -------- end to end through the public API: pinned H2D of the inputs, D2H result ----
@@ -414,10 +441,17 @@ def main():
                    "block": "16^3 + 2 ghost layers", "form": "fp32+fp64-fix batched, graph-replayed",
                    "l2": "state (1.2 GB) larger than L2; no flush",
                    "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                     "frac": achieved / hbm, "traffic": None, "kernel": "step_kernel<float,3,16,LF>",
-                     "kernel_ms": k_ms, "bytes_per_cell": BYTES_PER_CELL_F32,
-                     "peak_source": f"{peak_kind} hbm_gbs"},
+        "roofline": {"bound": "alu", "achieved": tflops, "peak": fp32_peak, "unit": "TFLOP/s",
+                     "frac": tflops / fp32_peak, "traffic": traffic,
+                     "kernel": "step_kernel<float,3,16,LF,vanleer>", "kernel_ms": k_ms,
+                     "kernel_ms_alone": k_ms_alone, "flops_per_cell": FLOPS_PER_CELL,
+                     "peak_source": f"{SMS} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flop/FMA x "
+                                    f"{mhz:.0f} MHz ({mhz_src})",
+                     "traffic_source": "ncu dram bytes of the 512-block launch x blocks/512",
+                     "hbm": {"achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                             "bytes_per_cell": BYTES_PER_CELL_F32, "peak_source": f"{peak_kind} hbm_gbs",
+                             "dram_gbs": traffic / (k_ms * 1e-3) / 1e9,
+                             "dram_frac": traffic / (k_ms * 1e-3) / 1e9 / hbm}},
         "e2e": {"value": e2e_val, "unit": METRIC, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
         "clocks": clk,
