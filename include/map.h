@@ -94,6 +94,9 @@ typedef struct {
   int limiter;        /* MAP_MINMOD, MAP_VANLEER */
   double dt_override; /* > 0: use this dt instead of the CFL dt */
   double fp64_fix_tau;/* FP32 pools: recompute p in FP64 where e_int < tau * e */
+  int reflux;         /* 1: at every coarse/fine face the coarse leaf's flux is replaced by
+                         the mean of the fine fluxes covering it (Sec. 4.2, boundary step
+                         (2)), so the face carries one flux on both sides; 0: off */
 } map_params;
 
 /* Refinement estimator parameters (Sec. 4.5). */
@@ -209,6 +212,12 @@ int map_get_leaves(map_pool* pool, map_block_desc* out, int cap, int* n_out);
 /* FP64 conservation sums: sums_out[n_problems][9] = sum over leaf cells of U * cell
  * volume.  Synchronises. */
 int map_conservation(map_pool* pool, double* sums_out);
+
+/* The FP64 conservation sums (same layout as map_conservation) that the last map_advance
+ * step reduced inside its kernels for the state it produced, without another pass over
+ * the pool.  MAP_ESTATE when the state changed otherwise since (a write, map_step, a
+ * regrid).  Synchronises. */
+int map_last_sums(map_pool* pool, double* sums_out);
 
 /* Per problem: dt, c_h, c_p, psi damping factor, alpha_g of the last CFL reduction
  * (out[n_problems][5]).  Synchronises. */

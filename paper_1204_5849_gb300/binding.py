@@ -46,7 +46,7 @@ class map_params(C.Structure):
     _fields_ = [("gamma", C.c_double), ("c_cfl", C.c_double), ("ch_mode", C.c_int),
                 ("ch", C.c_double), ("cp_mode", C.c_int), ("c_d", C.c_double), ("cp", C.c_double),
                 ("eta", C.c_double), ("eglm", C.c_int), ("scheme", C.c_int), ("limiter", C.c_int),
-                ("dt_override", C.c_double), ("fp64_fix_tau", C.c_double)]
+                ("dt_override", C.c_double), ("fp64_fix_tau", C.c_double), ("reflux", C.c_int)]
 
 
 class map_refine_params(C.Structure):
@@ -83,6 +83,7 @@ _SIGS = {
                                   C.c_void_p, C.c_void_p]),
     "map_regrid": (C.c_int, [C.c_void_p, C.POINTER(map_block_desc), C.c_int]),
     "map_conservation": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "map_last_sums": (C.c_int, [C.c_void_p, C.c_void_p]),
     "map_get_speeds": (C.c_int, [C.c_void_p, C.c_void_p]),
     "map_kernel_launches": (C.c_longlong, [C.c_void_p]),
     "map_last_error": (C.c_char_p, [C.c_void_p]),
@@ -140,7 +141,8 @@ def make_params(p: Dict) -> map_params:
                       CP_MODES[p.get("cp_mode", "cd")], float(p.get("c_d", 0.18)),
                       float(p.get("cp", 0.0)), float(p.get("eta", 0.0)), int(p.get("eglm", 1)),
                       SCHEMES[p.get("scheme", "mmc")], LIMITERS[p.get("limiter", "minmod")],
-                      float(p.get("dt_override", 0.0)), float(p.get("fp64_fix_tau", 1e-2)))
+                      float(p.get("dt_override", 0.0)), float(p.get("fp64_fix_tau", 1e-2)),
+                      int(p.get("reflux", 1)))
 
 
 def make_refine(r: Dict) -> map_refine_params:
@@ -322,6 +324,12 @@ class Pool:
     def conservation(self) -> np.ndarray:
         out = np.zeros((len(self.mesh.problems), 9))
         self._ck(load().map_conservation(self.h, _ptr(out)), "map_conservation")
+        return out
+
+    def last_sums(self) -> np.ndarray:
+        """Conservation sums reduced by the last map_advance step (no extra pass)."""
+        out = np.zeros((len(self.mesh.problems), 9))
+        self._ck(load().map_last_sums(self.h, _ptr(out)), "map_last_sums")
         return out
 
     def speeds(self) -> np.ndarray:

@@ -407,4 +407,170 @@ __global__ void __launch_bounds__(256) regrid_kernel(RegridLaunch L) {
   }
 }
 
+
+// Reflux (Sec. 4.2, boundary step (2), after Berger and Colella): one CTA per coarse leaf
+// with coarse/fine faces.  For every face cell of such a face the coarse flux recorded by the
+// step kernel is replaced by the mean of the fine fluxes covering the cell:
+//   u_c += lam (F_fine - F_coarse) on a low face, u_c -= lam (F_fine - F_coarse) on a high one
+// (lam = dt / dx_d of the coarse leaf; psi's correction carries the damping factor the step
+// already applied).  Faces go in the order (d, low then high) with a barrier between them, so a
+// cell on two such faces is corrected in a fixed order.  Then every corrected cell is checked
+// and stored again into the ghost regions of the same-level leaves that copy it, and, in the
+// fused form, added to alpha_g and the FP64 sums (the step kernel left these cells out).
+template <typename T, int NDIM, int NB>
+__global__ void __launch_bounds__(256) reflux_kernel(RefluxLaunch L) {
+  using G = Geo<NDIM, NB>;
+  constexpr int NP = G::NP, S = G::S;
+  constexpr int NF = NDIM == 3 ? NB * NB : NB;          // face cells per face
+  constexpr int H = NB / 2;
+  constexpr size_t NB2 = (size_t)NB * NB;
+  constexpr size_t PER = (size_t)2 * NDIM * NV * NB2;   // one register slot
+  __shared__ double red[NV + 1][32];
+  const RefluxTask& tk = L.tasks[blockIdx.x];
+  const int q = tk.coarse;
+  const BlockGeo gg = L.geo[q];
+  const ProbDyn dy = L.dyn[gg.problem];
+  T* ub = (T*)L.u + (size_t)q * NV * S;
+  const T* freg = (const T*)L.freg;
+  const T damp = (T)dy.damp;
+  int mask = 0;
+  for (int f = 0; f < 2 * NDIM; ++f)
+    if (tk.fslot[f][0] >= 0) mask |= 1 << f;
+  // padded offset of the coarse cell on face (d, side) at face cell (t0, t1)
+  auto cell_of = [&](int d, int side, int t0, int t1, int* ci) {
+    const int da = d == 0 ? 1 : 0, db = d == 2 ? 1 : 2;
+    ci[0] = ci[1] = ci[2] = 0;
+    ci[d] = side ? NB - 1 : 0;
+    ci[da] = t0;
+    if (NDIM == 3) ci[db] = t1;
+    return ((NDIM == 3 ? ci[2] + NG : 0) * NP + ci[1] + NG) * NP + ci[0] + NG;
+  };
+  for (int d = 0; d < NDIM; ++d)
+    for (int side = 0; side < 2; ++side) {
+      const int f = 2 * d + side;
+      if (!((mask >> f) & 1)) continue;
+      const T lam = (T)(dy.dt / gg.dx[d]);
+      const T* rc = freg + (size_t)tk.cslot * PER + (size_t)f * NV * NB2;
+      for (int idx = threadIdx.x; idx < NF; idx += blockDim.x) {
+        const int t0 = idx % NB, t1 = NDIM == 3 ? idx / NB : 0;
+        const int k = t0 / H + (NDIM == 3 ? 2 * (t1 / H) : 0);
+        const T* rf = freg + (size_t)tk.fslot[f][k] * PER + (size_t)(2 * d + 1 - side) * NV * NB2;
+        const int f0 = 2 * (t0 - (t0 / H) * H), f1 = NDIM == 3 ? 2 * (t1 - (t1 / H) * H) : 0;
+        int ci[3];
+        const int c = cell_of(d, side, t0, t1, ci);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+          const T* fv = rf + (size_t)v * NB2;
+          T ff;
+          if (NDIM == 2) ff = T(0.5) * (fv[f0] + fv[f0 + 1]);
+          else ff = T(0.25) * ((fv[f1 * NB + f0] + fv[f1 * NB + f0 + 1]) +
+                               (fv[(f1 + 1) * NB + f0] + fv[(f1 + 1) * NB + f0 + 1]));
+          T corr = lam * (ff - rc[(size_t)v * NB2 + t1 * NB + t0]);
+          if (v == PSI) corr = corr * damp;
+          T* cell = ub + (size_t)v * S + c;
+          *cell = side ? *cell - corr : *cell + corr;
+        }
+      }
+      __syncthreads();
+    }
+  // checks, pushes and fused diagnostics, once per corrected cell (a cell on several such
+  // faces is taken with the first of them)
+  Phys<T> P;
+  P.gamma = (T)L.gamma;
+  P.gm1 = (T)(L.gamma - 1.0);
+  P.ch = T(0);
+  P.tau = (T)L.tau;
+  unsigned errbits = 0;
+  T am = T(0);
+  double sum[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) sum[v] = 0.0;
+  for (int d = 0; d < NDIM; ++d)
+    for (int side = 0; side < 2; ++side) {
+      const int f = 2 * d + side;
+      if (!((mask >> f) & 1)) continue;
+      for (int idx = threadIdx.x; idx < NF; idx += blockDim.x) {
+        const int t0 = idx % NB, t1 = NDIM == 3 ? idx / NB : 0;
+        int ci[3];
+        const int c = cell_of(d, side, t0, t1, ci);
+        bool first = true;
+        for (int f2 = 0; f2 < f; ++f2)
+          if (((mask >> f2) & 1) && ci[f2 >> 1] == ((f2 & 1) ? NB - 1 : 0)) first = false;
+        if (!first) continue;
+        T w[NV];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) w[v] = ub[(size_t)v * S + c];
+        bool fin = true;
+#pragma unroll
+        for (int v = 0; v < NV; ++v) fin = fin && isfinite(w[v]);
+        if (!fin) {
+          errbits |= 1u;
+          am = (T)NAN;
+        } else {
+          const T pr = pressure<T>(w, P);
+          if (!(w[RHO] > T(0)) || pr < T(0)) errbits |= 2u;
+          T a = alpha_p<T, 0>(w, pr, P);
+          a = dmax<T>(a, alpha_p<T, 1>(w, pr, P));
+          if (NDIM == 3) a = dmax<T>(a, alpha_p<T, 2>(w, pr, P));
+          if (!(am != am)) am = dmax<T>(am, a);
+        }
+#pragma unroll
+        for (int v = 0; v < NV; ++v) sum[v] += (double)w[v];
+        // the same-level leaves that copy this cell into their ghosts
+        const int x = ci[0] + NG, y = ci[1] + NG, z = NDIM == 3 ? ci[2] + NG : 0;
+        const int fx = x < 2 * NG ? -1 : (x >= NB ? 1 : 0);
+        const int fy = y < 2 * NG ? -1 : (y >= NB ? 1 : 0);
+        const int fz = NDIM == 3 ? (z < 2 * NG ? -1 : (z >= NB ? 1 : 0)) : 0;
+        for (int kz = 0; kz < (fz ? 2 : 1); ++kz)
+          for (int ky = 0; ky < (fy ? 2 : 1); ++ky)
+            for (int kx = 0; kx < (fx ? 2 : 1); ++kx) {
+              const int ex = kx ? fx : 0, ey = ky ? fy : 0, ez = kz ? fz : 0;
+              if (!(ex | ey | ez)) continue;
+              const PushEntry pe = L.pushes[(size_t)q * 27 + (ex + 1) + 3 * (ey + 1) + 9 * (ez + 1)];
+              if (pe.dst < 0) continue;
+              T* db = (T*)L.u + (size_t)pe.dst * NV * S;
+              const size_t dc = ((size_t)(z + pe.off[2]) * NP + (y + pe.off[1])) * NP + (x + pe.off[0]);
+#pragma unroll
+              for (int v = 0; v < NV; ++v) db[(size_t)v * S + dc] = w[v];
+            }
+      }
+    }
+  unsigned e = errbits;
+  for (int o = 16; o > 0; o >>= 1) e |= __shfl_xor_sync(0xffffffffu, e, o);
+  if ((threadIdx.x & 31) == 0 && e) atomicOr(L.err_word, e);
+  if (!L.dyn_next && !L.sums) return;
+  double a2 = (double)am;
+  for (int o = 16; o > 0; o >>= 1) {
+    const double t = __shfl_xor_sync(0xffffffffu, a2, o);
+    a2 = (t != t || a2 != a2) ? __longlong_as_double(0x7ff8000000000000ll) : fmax(a2, t);
+  }
+#pragma unroll
+  for (int v = 0; v < NV; ++v)
+    for (int o = 16; o > 0; o >>= 1) sum[v] += __shfl_xor_sync(0xffffffffu, sum[v], o);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) {
+    red[NV][wid] = a2;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) red[v][wid] = sum[v];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const int nw = (blockDim.x + 31) / 32;
+    double a = 0.0;
+    for (int w2 = 0; w2 < nw; ++w2) {
+      const double t = red[NV][w2];
+      a = (t != t || a != a) ? __longlong_as_double(0x7ff8000000000000ll) : fmax(a, t);
+    }
+    if (L.dyn_next) atomicMax(&L.dyn_next[gg.problem].alpha_bits, (unsigned long long)__double_as_longlong(a));
+    if (L.sums) {
+      const double vol = gg.dx[0] * gg.dx[1] * (NDIM == 3 ? gg.dx[2] : 1.0);
+      for (int v = 0; v < NV; ++v) {
+        double t = 0.0;
+        for (int w2 = 0; w2 < nw; ++w2) t += red[v][w2];
+        atomicAdd(&L.sums[gg.problem * NV + v], t * vol);
+      }
+    }
+  }
+}
+
 }  // namespace mapgb

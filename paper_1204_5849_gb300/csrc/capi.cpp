@@ -20,6 +20,10 @@ struct DevTree {
   int* level_leaves = nullptr; // concatenated by level
   int* level_parents = nullptr;
   PushEntry* pushes = nullptr;
+  RefluxLeaf* refl = nullptr;
+  RefluxTask* rtasks = nullptr;
+  int nrtasks = 0;
+  void* freg = nullptr;        // face registers, tree.nslots slots
   std::vector<int> leaf_off, parent_off;  // offsets per level (host)
 };
 
@@ -48,6 +52,7 @@ struct map_pool {
   bool have_dt = false;
   bool alpha_ready = false;   // dyn.alpha_bits holds alpha_g of the current state
   bool pushed[3] = {false, false, false};  // buffer q: same-level ghosts written by the last step
+  bool sums_valid = false;   // sums holds the conservation sums of the current state
   long long launches = 0;
   std::string err;
   // graph cache, one per starting buffer parity q and fill kind (2q + 1: residual fill)
@@ -93,6 +98,9 @@ static void free_tree(map_pool* pool) {
   cudaFree(pool->dt.level_leaves);
   cudaFree(pool->dt.level_parents);
   cudaFree(pool->dt.pushes);
+  cudaFree(pool->dt.refl);
+  cudaFree(pool->dt.rtasks);
+  cudaFree(pool->dt.freg);
   pool->dt = DevTree();
 }
 
@@ -214,6 +222,12 @@ static int install_tree(map_pool* pool, HostTree& t) {
   CK(upload(&D.leaf_ids, t.leaf_to_block, pool->stream));
   CK(upload(&D.all_leaves, t.all_leaves, pool->stream));
   CK(upload(&D.pushes, t.pushes, pool->stream));
+  CK(upload(&D.refl, t.refl, pool->stream));
+  if (!t.reflux_tasks.empty()) {
+    CK(upload(&D.rtasks, t.reflux_tasks, pool->stream));
+    D.nrtasks = (int)t.reflux_tasks.size();
+    CK(cudaMalloc(&D.freg, (size_t)t.nslots * 2 * pool->ndim * kNV * pool->nb * pool->nb * pool->elem));
+  }
   std::vector<int> ll, pl;
   D.leaf_off.assign(t.maxlev + 2, 0);
   D.parent_off.assign(t.maxlev + 2, 0);
@@ -258,6 +272,7 @@ static int install_tree(map_pool* pool, HostTree& t) {
   pool->have_dt = false;
   pool->alpha_ready = false;
   for (int q = 0; q < 3; ++q) pool->pushed[q] = false;
+  pool->sums_valid = false;
   return MAP_OK;
 }
 
@@ -293,6 +308,7 @@ int map_write_block(map_pool* pool, int leaf, const double* u) {
   pool->have_dt = false;
   pool->alpha_ready = false;
   pool->pushed[pool->cur] = false;
+  pool->sums_valid = false;
   return pack(pool, pool->dt.leaf_ids + leaf, 1, 1);
 }
 
@@ -316,6 +332,7 @@ int map_write_leaves(map_pool* pool, const double* u) {
   pool->have_dt = false;
   pool->alpha_ready = false;
   pool->pushed[pool->cur] = false;
+  pool->sums_valid = false;
   return pack(pool, pool->dt.leaf_ids, n, 1);
 }
 
@@ -407,7 +424,7 @@ static bool params_equal(const map_params& a, const map_params& b) {
   return a.gamma == b.gamma && a.c_cfl == b.c_cfl && a.ch_mode == b.ch_mode && a.ch == b.ch &&
          a.cp_mode == b.cp_mode && a.c_d == b.c_d && a.cp == b.cp && a.eta == b.eta && a.eglm == b.eglm &&
          a.scheme == b.scheme && a.limiter == b.limiter && a.dt_override == b.dt_override &&
-         a.fp64_fix_tau == b.fp64_fix_tau;
+         a.fp64_fix_tau == b.fp64_fix_tau && a.reflux == b.reflux;
 }
 
 static int check_params(map_pool* pool, const map_params* p) {
@@ -464,6 +481,9 @@ static int step_launches(map_pool* pool, const map_params* p, bool fused) {
   S.sums = fused ? pool->sums : nullptr;
   S.dyn_next = fused ? pool->dyn : nullptr;
   S.pushes = pool->dt.pushes;
+  const bool reflux = p->reflux != 0 && pool->dt.nrtasks > 0;
+  S.freg = reflux ? pool->dt.freg : nullptr;
+  S.refl = reflux ? pool->dt.refl : nullptr;
   const int in = pool->cur, out = 1 - pool->cur;
   // the plain FP64 form launches once per level; the FP32 form once over all leaves
   auto run = [&](const void* uin, void* uout, const void* ubase, int stage, bool with_fused) -> int {
@@ -504,6 +524,22 @@ static int step_launches(map_pool* pool, const map_params* p, bool fused) {
     rc = run(pool->buf[in], pool->buf[out], nullptr, 0, fused);
     if (rc) return rc;
   }
+  if (reflux) {
+    RefluxLaunch R;
+    R.u = pool->buf[out];
+    R.tasks = pool->dt.rtasks;
+    R.ntasks = pool->dt.nrtasks;
+    R.freg = pool->dt.freg;
+    R.geo = pool->dt.geo;
+    R.dyn = pool->dyn;
+    R.pushes = pool->dt.pushes;
+    R.gamma = p->gamma;
+    R.tau = S.tau;
+    R.err_word = pool->err_word;
+    R.sums = fused ? pool->sums : nullptr;
+    R.dyn_next = fused ? pool->dyn : nullptr;
+    CK(DISPATCH(pool, reflux, R));
+  }
   pool->cur = out;
   pool->pushed[out] = true;
   return MAP_OK;
@@ -521,6 +557,7 @@ int map_step(map_pool* pool, const map_params* p) {
   rc = step_launches(pool, p, false);
   pool->have_dt = false;
   pool->alpha_ready = false;
+  pool->sums_valid = false;
   return rc;
 }
 
@@ -588,6 +625,7 @@ int map_advance(map_pool* pool, const map_params* p, int nsteps) {
     pool->pushed[1 - q] = true;
   }
   pool->have_dt = false;
+  pool->sums_valid = true;
   return MAP_OK;
 }
 
@@ -714,6 +752,15 @@ int map_conservation(map_pool* pool, double* sums_out) {
   L.geo = pool->dt.geo;
   L.sums = pool->sums;
   CK(DISPATCH(pool, sums, L));
+  CK(cudaMemcpyAsync(sums_out, pool->sums, sizeof(double) * kNV * pool->nprob, cudaMemcpyDeviceToHost, pool->stream));
+  CK(cudaStreamSynchronize(pool->stream));
+  pool->sums_valid = true;
+  return MAP_OK;
+}
+
+int map_last_sums(map_pool* pool, double* sums_out) {
+  if (!pool || !sums_out) return fail(pool, MAP_EINVAL, "null argument");
+  if (!pool->sums_valid) return fail(pool, MAP_ESTATE, "the state changed since the last map_advance step");
   CK(cudaMemcpyAsync(sums_out, pool->sums, sizeof(double) * kNV * pool->nprob, cudaMemcpyDeviceToHost, pool->stream));
   CK(cudaStreamSynchronize(pool->stream));
   return MAP_OK;

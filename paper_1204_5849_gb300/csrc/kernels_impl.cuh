@@ -35,6 +35,8 @@ cudaError_t launch_step_one(const StepLaunch& L, cudaStream_t s) {
   A.sums = L.sums;
   A.dyn_next = L.dyn_next;
   A.pushes = L.pushes;
+  A.freg = (T*)L.freg;
+  A.refl = L.freg ? L.refl : nullptr;
   const int grid = L.grid > 0 ? (L.grid < L.nblocks ? L.grid : L.nblocks) : L.nblocks;
   if (grid <= 0) return cudaSuccess;
   kern<<<grid, NB * NB, smem, s>>>(A);
@@ -165,6 +167,17 @@ cudaError_t launch_regrid_T(const KernelConfig& kc, const RegridLaunch& L, cudaS
 }
 
 template <typename T>
+cudaError_t launch_reflux_T(const KernelConfig& kc, const RefluxLaunch& L, cudaStream_t s, long long* cnt) {
+  if (L.ntasks <= 0) return cudaSuccess;
+  if (cnt) ++*cnt;
+#define CALL_REFLUX(ND, NBV)                                              \
+  reflux_kernel<T, ND, NBV><<<L.ntasks, 256, 0, s>>>(L);                  \
+  return cudaGetLastError()
+  MAPGB_GEO_DISPATCH(kc, CALL_REFLUX);
+#undef CALL_REFLUX
+}
+
+template <typename T>
 cudaError_t launch_cfl_partial_T(const KernelConfig& kc, const void* u, int nblocks, double gamma, double* partial,
                                  cudaStream_t s) {
   if (nblocks <= 0) return cudaSuccess;
@@ -188,6 +201,7 @@ cudaError_t launch_cfl_partial_T(const KernelConfig& kc, const void* u, int nblo
   cudaError_t launch_sums_##SUFFIX(const KernelConfig& k, const SumLaunch& l, cudaStream_t s, long long* c) { return launch_sums_T<T>(k, l, s, c); } \
   cudaError_t launch_pack_##SUFFIX(const KernelConfig& k, const PackLaunch& l, cudaStream_t s, long long* c) { return launch_pack_T<T>(k, l, s, c); } \
   cudaError_t launch_regrid_##SUFFIX(const KernelConfig& k, const RegridLaunch& l, cudaStream_t s, long long* c) { return launch_regrid_T<T>(k, l, s, c); } \
+  cudaError_t launch_reflux_##SUFFIX(const KernelConfig& k, const RefluxLaunch& l, cudaStream_t s, long long* c) { return launch_reflux_T<T>(k, l, s, c); } \
   size_t step_smem_##SUFFIX(const KernelConfig& k, int scheme, int res) { return step_smem_T<T>(k, scheme, res); } \
   cudaError_t launch_cfl_partial_##SUFFIX(const KernelConfig& k, const void* u, int n, double g, double* part, cudaStream_t s) { return launch_cfl_partial_T<T>(k, u, n, g, part, s); } \
   }

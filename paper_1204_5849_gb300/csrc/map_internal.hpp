@@ -54,6 +54,23 @@ struct PushEntry {
   int off[3];
 };
 
+// Reflux (Sec. 4.2, boundary step (2)).  Leaves on either side of a coarse/fine face own a
+// face register: the flux through each of their boundary face cells over the step, laid
+// out [side 2d+s][var][t1][t0] (nb*nb per side and variable; t0, t1 the face cell's
+// interior coordinates in the other two dimensions, increasing order).
+struct RefluxLeaf {
+  int slot;          // face-register slot, -1: none
+  int coarse_mask;   // bit 2d+s: this leaf is the coarse side of a coarse/fine face there
+};
+
+// One coarse leaf with at least one coarse/fine face: the register slots of the fine leaves
+// covering each such face, indexed by their tangential child bits (t0 half + 2 * t1 half).
+struct RefluxTask {
+  int coarse;        // pool id
+  int cslot;         // its register slot
+  int fslot[6][4];   // per side 2d+s; fslot[side][0] < 0: not a coarse/fine face
+};
+
 // Regrid task for one new leaf (Sec. 4.3 interpolation on the interior).
 //   kind 0 copy interior of old block src
 //   kind 1 prolong from old leaf src; child bits in cb (x | y<<1 | z<<2)
@@ -75,6 +92,9 @@ struct HostTree {
   std::vector<GhostRegion> regions;         // 27 per block (valid for leaves)
   std::vector<PushEntry> pushes;            // 27 per block (valid for leaves)
   std::vector<char> level_has_residual;     // per level: a ghost region the fill must do
+  std::vector<RefluxLeaf> refl;             // per block
+  std::vector<RefluxTask> reflux_tasks;     // per coarse leaf at a coarse/fine face
+  int nslots = 0;                           // face-register slots
   std::vector<std::vector<int>> leaves_by_level;   // pool ids
   std::vector<std::vector<int>> parents_by_level;  // pool ids
   std::vector<int> all_leaves;              // pool ids, Morton order
@@ -116,6 +136,22 @@ struct StepLaunch {
   ProbDyn* dyn_next;       // optional: max alpha of the output into dyn_next[p].alpha_bits
   int grid;                // CTAs (0 = one per block)
   const PushEntry* pushes; // optional: write boundary layers into same-level neighbours' ghosts
+  void* freg;              // optional: face registers (reflux); with refl
+  const RefluxLeaf* refl;  // per block slot and coarse-side mask
+};
+
+struct RefluxLaunch {
+  void* u;                 // output state of the step (corrected in place)
+  const RefluxTask* tasks;
+  int ntasks;
+  const void* freg;
+  const BlockGeo* geo;
+  const ProbDyn* dyn;      // dt, damping
+  const PushEntry* pushes; // re-push corrected cells to same-level neighbours' ghosts
+  double gamma, tau;
+  unsigned* err_word;
+  double* sums;            // optional: FP64 sums of the corrected cells (fused form)
+  ProbDyn* dyn_next;       // optional: alpha max of the corrected cells (fused form)
 };
 
 struct FillLaunch {
@@ -198,6 +234,7 @@ struct KernelConfig {
   cudaError_t launch_sums_##SUFFIX(const KernelConfig&, const SumLaunch&, cudaStream_t, long long*); \
   cudaError_t launch_pack_##SUFFIX(const KernelConfig&, const PackLaunch&, cudaStream_t, long long*); \
   cudaError_t launch_regrid_##SUFFIX(const KernelConfig&, const RegridLaunch&, cudaStream_t, long long*); \
+  cudaError_t launch_reflux_##SUFFIX(const KernelConfig&, const RefluxLaunch&, cudaStream_t, long long*); \
   size_t step_smem_##SUFFIX(const KernelConfig&, int scheme, int resistive); \
   cudaError_t launch_cfl_partial_##SUFFIX(const KernelConfig&, const void* u, int nblocks, double gamma, \
                                           double* partial, cudaStream_t);

@@ -45,6 +45,8 @@ struct StepArgsT {
   double* sums;
   ProbDyn* dyn_next;
   const PushEntry* pushes;
+  T* freg;
+  const RefluxLeaf* refl;
 };
 
 template <int NDIM, int NB>
@@ -454,6 +456,7 @@ step_kernel(StepArgsT<T> A) {
       kc[15] = (T)dy.ch;
     }
     if (A.pushes && tid < 27) spush[tid] = A.pushes[(size_t)blk * 27 + tid];   // read after the first barrier
+    const RefluxLeaf rl = A.refl ? A.refl[blk] : RefluxLeaf{-1, 0};
     const T* ub = A.u_in + (size_t)blk * NV * S;
     T* ob = A.u_out + (size_t)blk * NV * S;
     const T* bb = (STAGE == 2) ? A.u_base + (size_t)blk * NV * S : nullptr;
@@ -777,6 +780,27 @@ step_kernel(StepArgsT<T> A) {
       }
       const T* P0 = uslot(z);
       const T* T0 = HAS_T ? tslot(z) : nullptr;
+      if (rl.slot >= 0) {
+        // face register (reflux, Sec. 4.2): the flux through this block's boundary face
+        // cells; a WENO step holds half of each stage's flux
+        T* R = A.freg + (size_t)rl.slot * (2 * NDIM * NV * NB * NB);
+        const int tz = NDIM == 3 ? z - NG : 0;
+        auto put = [&](int side, int t0, int t1, const T* f, int stride) {
+          T* r = R + (size_t)side * NV * NB * NB + t1 * NB + t0;
+#pragma unroll
+          for (int v = 0; v < NV; ++v) {
+            const T x = f[v * stride];
+            T* rv = r + (size_t)v * NB * NB;
+            *rv = STAGE == 0 ? x : (STAGE == 1 ? T(0.5) * x : *rv + T(0.5) * x);
+          }
+        };
+        if (tx == 0) put(0, ty, tz, sfx + ty * (NB + 1), NFACE);
+        if (tx == NB - 1) put(1, ty, tz, sfx + ty * (NB + 1) + NB, NFACE);
+        if (ty == 0) put(2, tx, tz, sfy + tx, NFACE);
+        if (ty == NB - 1) put(3, tx, tz, sfy + NB * NB + tx, NFACE);
+        if (NDIM == 3 && z == NG) put(4, tx, ty, Fzlo, 1);
+        if (NDIM == 3 && z == NB + NG - 1) put(5, tx, ty, Fzhi, 1);
+      }
       T acc[NV];
       if (SCHEME == SCH_WENO) {
 #pragma unroll
@@ -882,7 +906,13 @@ step_kernel(StepArgsT<T> A) {
               }
         }
       }
-      if (STAGE != 1) {
+      // cells next to a face where this block is the coarse side change again in the reflux
+      // pass, which checks them and adds them to the fused diagnostics itself
+      const int cm = rl.coarse_mask;
+      const bool refluxed = cm != 0 && (((cm & 1) && tx == 0) || ((cm & 2) && tx == NB - 1) ||
+                                        ((cm & 4) && ty == 0) || ((cm & 8) && ty == NB - 1) ||
+                                        (NDIM == 3 && (((cm & 16) && z == NG) || ((cm & 32) && z == NB + NG - 1))));
+      if (STAGE != 1 && !refluxed) {
         bool fin = true;
 #pragma unroll
         for (int v = 0; v < NV; ++v) fin = fin && isfinite(out[v]);

@@ -327,6 +327,64 @@ std::string build_tree(int ndim, int nb, const std::vector<map_problem_desc>& pr
           if (!g.pushed) t.level_has_residual[t.blk_level[id]] = 1;
         }
   }
+  // reflux: the coarse leaf of every coarse/fine face gets a task naming the fine leaves
+  // covering that face; both sides get a face-register slot
+  t.refl.assign((size_t)NB, RefluxLeaf{-1, 0});
+  t.reflux_tasks.clear();
+  {
+    std::vector<char> need(n, 0);
+    for (int id = 0; id < n; ++id) {
+      const int p = t.blk_problem[id], L = t.blk_level[id];
+      const int* c = &t.blk_ijk[3 * id];
+      RefluxTask tk;
+      tk.coarse = id;
+      tk.cslot = -1;
+      for (int s6 = 0; s6 < 6; ++s6)
+        for (int k = 0; k < 4; ++k) tk.fslot[s6][k] = -1;
+      bool coarse_side = false;
+      for (int d = 0; d < ndim; ++d)
+        for (int side = 0; side < 2; ++side) {
+          int q[3] = {c[0], c[1], c[2]};
+          const int nblk = probs[p].nbase[d] << L;
+          q[d] += side ? 1 : -1;
+          if (q[d] < 0 || q[d] >= nblk) {
+            if (probs[p].bc[d][side] != MAP_BC_PERIODIC) continue;
+            q[d] = (q[d] + nblk) % nblk;
+          }
+          const int nbid = t.find(p, L, q[0], q[1], q[2]);
+          if (nbid >= n) {                        // refined neighbour: this leaf is coarse
+            coarse_side = true;
+            t.refl[id].coarse_mask |= 1 << (2 * d + side);
+            const int da = d == 0 ? 1 : 0, db = d == 2 ? 1 : 2;
+            for (int k = 0; k < (1 << (ndim - 1)); ++k) {
+              int bits[3] = {0, 0, 0};
+              bits[d] = side ? 0 : 1;
+              bits[da] = k & 1;
+              if (ndim == 3) bits[db] = (k >> 1) & 1;
+              const int ch = t.children[(size_t)nbid * 8 + (bits[0] | (bits[1] << 1) | (bits[2] << 2))];
+              if (ch < 0 || ch >= n) return fmt("coarse/fine face without fine leaves", p, L, c);
+              tk.fslot[2 * d + side][k] = ch;     // pool id for now
+              need[ch] = 1;
+            }
+          } else if (nbid < 0) {
+            need[id] = 1;                         // coarser neighbour: this leaf is fine
+          }
+        }
+      if (coarse_side) {
+        need[id] = 1;
+        t.reflux_tasks.push_back(tk);
+      }
+    }
+    t.nslots = 0;
+    for (int id = 0; id < n; ++id)
+      if (need[id]) t.refl[id].slot = t.nslots++;
+    for (RefluxTask& tk : t.reflux_tasks) {
+      tk.cslot = t.refl[tk.coarse].slot;
+      for (int s6 = 0; s6 < 6; ++s6)
+        for (int k = 0; k < 4; ++k)
+          if (tk.fslot[s6][k] >= 0) tk.fslot[s6][k] = t.refl[tk.fslot[s6][k]].slot;
+    }
+  }
   // level lists, per-problem minimum spacing
   t.leaves_by_level.assign(t.maxlev + 1, {});
   t.parents_by_level.assign(t.maxlev + 1, {});

@@ -223,6 +223,80 @@ def test_advance_write_advance(gpulib, prec):
     assert a.check() == 0
 
 
+# --- reflux at coarse/fine faces (Sec. 4.2, boundary step (2)) ---------------------------
+
+_REFLUX_MESHES = {
+    "2d_nb8_periodic": lambda: w.radial_amr_mesh(2, 8, (2, 2), 2, radii=(0.16, 0.34), bc=w.mesh.PERIODIC,
+                                                 lo=(0, 0, 0), hi=(1, 1, 1), centre=(0.5, 0.5, 0)),
+    "2d_nb16_outflow": lambda: w.radial_amr_mesh(2, 16, (2, 2), 2, radii=(0.16, 0.34)),
+    "3d_nb8_periodic": lambda: w.radial_amr_mesh(3, 8, (4, 4, 4), 1, radii=(0.2,), bc=w.mesh.PERIODIC,
+                                                 lo=(0, 0, 0), hi=(1, 1, 1), centre=(0.5, 0.5, 0.5)),
+}
+FLUX_ONLY = dict(eglm=0, cp_mode="fixed", cp=0.0, eta=0.0)
+
+
+def _mixed_state(mesh):
+    return w.evaluate_on_mesh(mesh, w.problems.ensemble_problem, seed=5)
+
+
+@pytest.mark.parametrize("geom", sorted(_REFLUX_MESHES))
+@pytest.mark.parametrize("scheme", ["mmc", "lf", "weno"])
+def test_fp64_reflux_matches_oracle(gpulib, geom, scheme):
+    from paper_1204_5849_gb300 import MAP_FP64
+    mesh = _REFLUX_MESHES[geom]()
+    assert len(set(mesh.leaves[:, 1].tolist())) > 1
+    U0 = _mixed_state(mesh)
+    p = P(scheme=scheme, reflux=1)
+    pool = pool_for(mesh, MAP_FP64, U0)
+    orc = Oracle(mesh, U0)
+    lockstep(pool, orc, p, 3)
+    assert rel_max(pool.read_leaves(), orc.get_state()).max() <= 1e-12
+    assert pool.check() == 0
+
+
+def test_fp64_reflux_off_matches_oracle(gpulib):
+    from paper_1204_5849_gb300 import MAP_FP64
+    mesh = _REFLUX_MESHES["3d_nb8_periodic"]()
+    U0 = _mixed_state(mesh)
+    p = P(scheme="lf", reflux=0)
+    pool = pool_for(mesh, MAP_FP64, U0)
+    orc = Oracle(mesh, U0)
+    lockstep(pool, orc, p, 2)
+    assert rel_max(pool.read_leaves(), orc.get_state()).max() <= 1e-12
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("scheme", ["mmc", "lf", "weno"])
+def test_reflux_conserves_on_gpu(gpulib, prec, scheme):
+    """Every source off: the totals hold to round-off with reflux (the batched form, whose
+    sums are reduced inside the kernels, and a fresh reduction agree), and drift without."""
+    mesh = _REFLUX_MESHES["3d_nb8_periodic"]()
+    U0 = _mixed_state(mesh)
+    drift = {}
+    for rf in (0, 1):
+        pool = pool_for(mesh, prec, U0)
+        s0 = pool.conservation()
+        pool.advance(P(scheme=scheme, reflux=rf, **FLUX_ONLY), 4)
+        fused = pool.last_sums()
+        s1 = pool.conservation()
+        tol = 1e-13 if prec == 0 else 1e-6
+        assert np.abs(fused - s1).max() <= tol * np.abs(s1).max()
+        drift[rf] = (np.abs(s1 - s0) / np.maximum(np.abs(s0), 1e-3)).max()
+        assert pool.check() == 0
+    assert drift[1] <= (2e-14 if prec == 0 else 2e-6), drift
+    assert drift[0] >= 1e-5, drift
+
+
+def test_last_sums_needs_an_advance_step(gpulib):
+    from paper_1204_5849_gb300 import MAP_FP64, MapError
+    mesh = w.uniform_mesh(2, 16, (2, 2))
+    pool = pool_for(mesh, MAP_FP64, _mixed_state(mesh))
+    with pytest.raises(MapError):
+        pool.last_sums()
+    pool.advance(P(scheme="lf"), 1)
+    np.testing.assert_allclose(pool.last_sums(), pool.conservation(), rtol=1e-13, atol=1e-15)
+
+
 # --- several independent problems of uneven sizes -----------------------------------------
 
 def test_fp64_ensemble(gpulib):
