@@ -152,6 +152,107 @@ void orc_lf_flux(int d, const double* a, const double* b, double gamma, double c
   FLOPS(5 * NV);
 }
 
+/* Fast magnetosonic speed along d (the c_f of orc_alpha, without |v_d|). */
+static double fast_speed(int d, const double* w, double gamma) {
+  double rho = w[RHO];
+  double p = pressure(w, gamma);
+  if (p < 0.0) p = 0.0;
+  double a2 = gamma * p / rho;
+  double b2 = (w[BX] * w[BX] + w[BY] * w[BY] + w[BZ] * w[BZ]) / rho;
+  double bd2 = w[BX + d] * w[BX + d] / rho;
+  double s = a2 + b2;
+  double disc = s * s - 4.0 * a2 * bd2;
+  if (disc < 0.0) disc = 0.0;
+  FLOPS(19);
+  return sqrt(0.5 * (s + sqrt(disc)));
+}
+
+/* HLLC flux for MHD (the approximate Riemann solver of Gurski that the paper uses for LF
+ * and WENO in 2D/3D, Sec. 3.2-3.3; the paper does not print it).  Steps:
+ * 1. The linear (B_d, psi) subsystem keeps its exact upwind flux, as in f_m:
+ *    F(B_d) = (psi_a + psi_b - c_h (B_d,b - B_d,a))/2, F(psi) = c_h^2 B_m, with the interface
+ *    normal field B_m = (B_d,a + B_d,b)/2 - (psi_b - psi_a)/(2 c_h) (the plain mean if c_h = 0).
+ * 2. Both states take B_d = B_m at unchanged gas pressure: E' = E + (B_m^2 - B_d^2)/2.
+ * 3. Speed bounds S_L = min(u_a - c_f,a, u_b - c_f,b), S_R = max(u_a + c_f,a, u_b + c_f,b)
+ *    (u = v_d, c_f the fast speed along d of the modified states).
+ * 4. S_L >= 0: F(a'); S_R <= 0: F(b'); otherwise the star state on the side of the contact
+ *    speed S_M = (rho u)_HLL / rho_HLL, with, for K the side taken and S_K its bound,
+ *      rho* = rho_K (S_K - u_K)/(S_K - S_M),  m*_d = rho* S_M,
+ *      p_T* = p_T,K + rho_K (S_K - u_K)(S_M - u_K),
+ *      B*_t = B_t of the HLL state,  B*_d = B_m,
+ *      m*_t = rho* v_t,K - B_m (B*_t - B_t,K)/(S_K - S_M),
+ *      E* = (E_K (S_K - u_K) - p_T,K u_K + p_T* S_M + B_m (v_K.B_K - v*.B*))/(S_K - S_M)
+ *    (Rankine-Hugoniot across S_K), and F = F(K') + S_K (U* - U_K') for rho, m, B_t and E. */
+void orc_hllc_flux(int d, const double* a, const double* b, double gamma, double ch, double* f) {
+  double bm;
+  if (ch > 0.0) bm = 0.5 * (a[BX + d] + b[BX + d]) - (b[PSI] - a[PSI]) / (2.0 * ch);
+  else bm = 0.5 * (a[BX + d] + b[BX + d]);
+  double w[2][NV], F[2][NV], u[2], cf[2], pt[2];
+  for (int k = 0; k < 2; ++k) {
+    const double* q = k ? b : a;
+    for (int v = 0; v < NV; ++v) w[k][v] = q[v];
+    const double p = pressure(q, gamma);
+    w[k][BX + d] = bm;
+    w[k][EN] = q[EN] + 0.5 * (bm * bm - q[BX + d] * q[BX + d]);
+    orc_flux(d, w[k], gamma, ch, F[k]);
+    u[k] = w[k][MX + d] / w[k][RHO];
+    cf[k] = fast_speed(d, w[k], gamma);
+    pt[k] = p + 0.5 * (w[k][BX] * w[k][BX] + w[k][BY] * w[k][BY] + w[k][BZ] * w[k][BZ]);
+    FLOPS(15);
+  }
+  const double sl = fmin(u[0] - cf[0], u[1] - cf[1]);
+  const double sr = fmax(u[0] + cf[0], u[1] + cf[1]);
+  FLOPS(4);
+  if (sl >= 0.0) {
+    for (int v = 0; v < NV; ++v) f[v] = F[0][v];
+  } else if (sr <= 0.0) {
+    for (int v = 0; v < NV; ++v) f[v] = F[1][v];
+  } else {
+    const double ra = w[0][RHO], rb = w[1][RHO];
+    const double sm = (rb * u[1] * (sr - u[1]) - ra * u[0] * (sl - u[0]) - pt[1] + pt[0]) /
+                      (rb * (sr - u[1]) - ra * (sl - u[0]));
+    const int t1 = d == 0 ? 1 : 0, t2 = d == 2 ? 1 : 2;     /* tangential dimensions */
+    double bt[3];
+    bt[d] = bm;
+    for (int t = 0; t < 2; ++t) {
+      const int j = t ? t2 : t1;
+      bt[j] = (sr * w[1][BX + j] - sl * w[0][BX + j] - (F[1][BX + j] - F[0][BX + j])) / (sr - sl);
+    }
+    const int k = sm >= 0.0 ? 0 : 1;
+    const double sk = k ? sr : sl;
+    const double* wk = w[k];
+    const double uk = u[k], dk = sk - uk, ds = sk - sm;
+    const double rs = wk[RHO] * dk / ds;
+    const double pts = pt[k] + wk[RHO] * dk * (sm - uk);
+    double us[NV];
+    us[RHO] = rs;
+    us[MX + d] = rs * sm;
+    double vb_k = 0.0, vb_s = sm * bm;
+    for (int j = 0; j < 3; ++j) vb_k += (wk[MX + j] / wk[RHO]) * wk[BX + j];
+    for (int t = 0; t < 2; ++t) {
+      const int j = t ? t2 : t1;
+      us[MX + j] = rs * (wk[MX + j] / wk[RHO]) - bm * (bt[j] - wk[BX + j]) / ds;
+      vb_s += (us[MX + j] / rs) * bt[j];
+    }
+    for (int j = 0; j < 3; ++j) us[BX + j] = bt[j];
+    us[EN] = (wk[EN] * dk - pt[k] * uk + pts * sm + bm * (vb_k - vb_s)) / ds;
+    us[PSI] = wk[PSI];
+    for (int v = 0; v < NV; ++v) f[v] = F[k][v] + sk * (us[v] - wk[v]);
+    FLOPS(16 + 2 * 7 + 4 + 5 + 3 * 3 + 2 * 9 + 10 + 2 * NV);
+  }
+  /* the (B_d, psi) pair: exact upwind flux of the linear GLM subsystem (as in f_m) */
+  f[BX + d] = 0.5 * ((a[PSI] + b[PSI]) - ch * (b[BX + d] - a[BX + d]));
+  f[PSI] = 0.5 * ((ch * ch * a[BX + d] + ch * ch * b[BX + d]) - ch * (b[PSI] - a[PSI]));
+  FLOPS(11);
+}
+
+/* Interface flux of LF and WENO: f_m (Equ:LFFlux) or HLLC. */
+static void riemann_flux(int riemann, int d, const double* a, const double* b, double gamma, double ch,
+                         double* f) {
+  if (riemann == 1) orc_hllc_flux(d, a, b, gamma, ch, f);
+  else orc_lf_flux(d, a, b, gamma, ch, f);
+}
+
 static double minmod(double a, double b) {
   /* minmod(a,b) = sgn(a) max(0, min(|a|, sgn(a) b))  (eq. minmod, Sec. 3.2) */
   if (a > 0.0) { double m = a < b ? a : b; return m > 0.0 ? m : 0.0; }
@@ -316,6 +417,7 @@ typedef struct {
   double gamma, ch, dt, eta;
   int eglm, limiter;
   double dx[3];
+  int riemann;    /* interface flux of LF and WENO: 0 f_m (Lax-Friedrichs), 1 HLLC */
   double* freg;   /* face register of the block (reflux), or NULL */
   double fw;      /* weight of this update's fluxes in the register (1, or 1/2 per RK2 stage) */
 } stepctx;
@@ -501,7 +603,7 @@ static void lf_block(const geom* g, const stepctx* s, const double* u, double* o
           b[v] = ut[v * g->S + cl + o] - 0.5 * phi[(d * NV + v) * g->S + cl + o];
         }
         FLOPS(4 * NV);
-        orc_lf_flux(d, a, b, s->gamma, s->ch, side ? fr : fl);
+        riemann_flux(s->riemann, d, a, b, s->gamma, s->ch, side ? fr : fl);
       }
       FLCAT(2);
       if (icoord(d, k, j, i) == 0) record_face(g, s, d, 0, k, j, i, fl);
@@ -542,7 +644,7 @@ static void weno_rhs(const geom* g, const stepctx* s, const double* w, double* L
           orc_weno_faces(f[cl - o], f[cl], f[cl + o], &a[v], &dummy);
           orc_weno_faces(f[cl], f[cl + o], f[cl + 2 * o], &dummy, &b[v]);
         }
-        orc_lf_flux(d, a, b, s->gamma, s->ch, side ? fr : fl);
+        riemann_flux(s->riemann, d, a, b, s->gamma, s->ch, side ? fr : fl);
       }
       FLCAT(2);
       if (icoord(d, k, j, i) == 0) record_face(g, s, d, 0, k, j, i, fl);
@@ -993,6 +1095,7 @@ static stepctx make_ctx(const orc_mesh* m, const orc_params* pr, const oblk* o) 
   s.gamma = pr->gamma; s.eta = pr->eta; s.eglm = pr->eglm; s.limiter = pr->limiter;
   s.dt = m->dt[o->problem]; s.ch = m->ch[o->problem];
   block_dx(m, o, s.dx);
+  s.riemann = pr->riemann;
   s.freg = NULL;
   s.fw = 1.0;
   return s;
@@ -1160,6 +1263,7 @@ int orc_block_step(int ndim, int nb, const orc_params* pr, const double* dx, dou
   s.gamma = pr->gamma; s.eta = pr->eta; s.eglm = pr->eglm; s.limiter = pr->limiter;
   s.dt = dt; s.ch = ch;
   for (int d = 0; d < 3; ++d) s.dx[d] = dx[d];
+  s.riemann = pr->riemann;
   s.freg = NULL;
   s.fw = 1.0;
   double* out = (double*)calloc((size_t)NV * g.S, sizeof(double));

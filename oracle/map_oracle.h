@@ -33,6 +33,7 @@ typedef struct {
   int limiter;      /* 0 minmod, 1 van Leer, 2 literal Roe form (MMC only) */
   double dt_override; /* > 0: use this dt */
   int reflux;       /* 1: coarse fluxes at coarse/fine faces replaced by the fine ones */
+  int riemann;      /* interface flux of LF and WENO: 0 f_m (Lax-Friedrichs), 1 HLLC */
 } orc_params;
 
 typedef struct {
@@ -81,6 +82,7 @@ int orc_block_step(int ndim, int nb, const orc_params* p, const double* dx, doub
 /* point-wise pieces, exposed for the pins */
 void orc_flux(int d, const double* w, double gamma, double ch, double* f);
 double orc_alpha(int d, const double* w, double gamma);
+void orc_hllc_flux(int d, const double* a, const double* b, double gamma, double ch, double* f);
 void orc_lf_flux(int d, const double* a, const double* b, double gamma, double ch, double* f);
 double orc_limiter(int kind, double a, double b);
 void orc_weno_faces(double um, double u0, double up, double* minus_right, double* plus_left);

@@ -14,6 +14,7 @@ import numpy as np
 from . import build as _build
 
 SCHEMES = {"mmc": 0, "lf": 1, "weno": 2}
+RIEMANN = {"lf": 0, "hllc": 1}
 LIMITERS = {"minmod": 0, "vanleer": 1, "roe": 2}
 CH_MODES = {"auto": 0, "paper": 1, "fixed": 2}
 CP_MODES = {"cd": 0, "fixed": 1}
@@ -25,7 +26,7 @@ class orc_params(C.Structure):
                 ("ch", C.c_double), ("cp_mode", C.c_int), ("c_d", C.c_double),
                 ("cp", C.c_double), ("eta", C.c_double), ("eglm", C.c_int),
                 ("scheme", C.c_int), ("limiter", C.c_int), ("dt_override", C.c_double),
-                ("reflux", C.c_int)]
+                ("reflux", C.c_int), ("riemann", C.c_int)]
 
 
 class orc_problem(C.Structure):
@@ -84,6 +85,7 @@ def _declare(L):
         L.orc_alpha.restype = C.c_double
         L.orc_alpha.argtypes = [C.c_int, dp, C.c_double]
         L.orc_lf_flux.argtypes = [C.c_int, dp, dp, C.c_double, C.c_double, dp]
+        L.orc_hllc_flux.argtypes = [C.c_int, dp, dp, C.c_double, C.c_double, dp]
         L.orc_limiter.restype = C.c_double
         L.orc_limiter.argtypes = [C.c_int, C.c_double, C.c_double]
         L.orc_weno_faces.argtypes = [C.c_double, C.c_double, C.c_double, dp, dp]
@@ -103,7 +105,8 @@ def make_params(p: Dict) -> orc_params:
                       CP_MODES[p.get("cp_mode", "cd")], float(p.get("c_d", 0.18)),
                       float(p.get("cp", 0.0)), float(p.get("eta", 0.0)), int(p.get("eglm", 1)),
                       SCHEMES[p.get("scheme", "mmc")], LIMITERS[p.get("limiter", "minmod")],
-                      float(p.get("dt_override", 0.0)), int(p.get("reflux", 1)))
+                      float(p.get("dt_override", 0.0)), int(p.get("reflux", 1)),
+                      RIEMANN[p.get("riemann", "lf")])
 
 
 def make_refine(r: Dict) -> orc_refine:
@@ -245,6 +248,14 @@ def lf_flux(d: int, a, b, gamma: float, ch: float) -> np.ndarray:
     b = np.ascontiguousarray(b, dtype=np.float64)
     f = np.zeros(9)
     lib().orc_lf_flux(d, _dp(a), _dp(b), gamma, ch, _dp(f))
+    return f
+
+
+def hllc_flux(d: int, a, b, gamma: float, ch: float) -> np.ndarray:
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    f = np.zeros(9)
+    lib().orc_hllc_flux(d, _dp(a), _dp(b), gamma, ch, _dp(f))
     return f
 
 
