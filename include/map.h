@@ -45,6 +45,9 @@ typedef enum {
 enum { MAP_FP64 = 0, MAP_FP32_FIX64 = 1 };   /* pool precision */
 enum { MAP_MMC = 0, MAP_LF = 1, MAP_WENO = 2 };
 enum { MAP_MINMOD = 0, MAP_VANLEER = 1 };
+/* Interface flux of LF and WENO (Sec. 3.2-3.3): the Lax-Friedrichs f_m (Equ:LFFlux) or the
+ * HLLC approximate Riemann solver for MHD the paper uses in 2D and 3D. */
+enum { MAP_RIEMANN_LF = 0, MAP_RIEMANN_HLLC = 1 };
 enum { MAP_BC_PERIODIC = 0, MAP_BC_OUTFLOW = 1 };
 enum { MAP_CH_AUTO = 0, MAP_CH_PAPER = 1, MAP_CH_FIXED = 2 };
 enum { MAP_CP_FROM_CD = 0, MAP_CP_FIXED = 1 };
@@ -97,6 +100,11 @@ typedef struct {
   int reflux;         /* 1: at every coarse/fine face the coarse leaf's flux is replaced by
                          the mean of the fine fluxes covering it (Sec. 4.2, boundary step
                          (2)), so the face carries one flux on both sides; 0: off */
+  int riemann;        /* MAP_RIEMANN_LF or MAP_RIEMANN_HLLC (LF and WENO; MMC takes only
+                         MAP_RIEMANN_LF, else MAP_EINVAL).  HLLC: the (B_d, psi) pair keeps
+                         the exact upwind flux of its linear system, which also fixes the
+                         interface normal field; the other seven components come from the
+                         HLLC star states with Davis speed bounds */
 } map_params;
 
 /* Refinement estimator parameters (Sec. 4.5). */

@@ -25,6 +25,8 @@ NVCC_COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", IN
 UNITS = {
     "kernels_f64.cu": ["-fmad=false"],
     "kernels_f32.cu": ["-ftz=true", "-prec-div=false", "-prec-sqrt=false"],
+    "kernels_f64_hllc.cu": ["-fmad=false"],
+    "kernels_f32_hllc.cu": ["-ftz=true", "-prec-div=false", "-prec-sqrt=false"],
     "common.cu": ["-fmad=false"],
     "noalloc.cu": ["-fmad=false"],
 }

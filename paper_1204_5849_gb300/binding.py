@@ -21,6 +21,7 @@ STATUS = {0: "MAP_OK", -1: "MAP_EINVAL", -2: "MAP_ENOMEM", -3: "MAP_ECUDA", -4: 
 MAP_FP64, MAP_FP32_FIX64 = 0, 1
 SCHEMES = {"mmc": 0, "lf": 1, "weno": 2}
 LIMITERS = {"minmod": 0, "vanleer": 1}
+RIEMANN = {"lf": 0, "hllc": 1}
 CH_MODES = {"auto": 0, "paper": 1, "fixed": 2}
 CP_MODES = {"cd": 0, "fixed": 1}
 REFINE_VARS = {"rho": 1, "p": 2, "j": 4}
@@ -46,7 +47,8 @@ class map_params(C.Structure):
     _fields_ = [("gamma", C.c_double), ("c_cfl", C.c_double), ("ch_mode", C.c_int),
                 ("ch", C.c_double), ("cp_mode", C.c_int), ("c_d", C.c_double), ("cp", C.c_double),
                 ("eta", C.c_double), ("eglm", C.c_int), ("scheme", C.c_int), ("limiter", C.c_int),
-                ("dt_override", C.c_double), ("fp64_fix_tau", C.c_double), ("reflux", C.c_int)]
+                ("dt_override", C.c_double), ("fp64_fix_tau", C.c_double), ("reflux", C.c_int),
+                ("riemann", C.c_int)]
 
 
 class map_refine_params(C.Structure):
@@ -142,7 +144,7 @@ def make_params(p: Dict) -> map_params:
                       float(p.get("cp", 0.0)), float(p.get("eta", 0.0)), int(p.get("eglm", 1)),
                       SCHEMES[p.get("scheme", "mmc")], LIMITERS[p.get("limiter", "minmod")],
                       float(p.get("dt_override", 0.0)), float(p.get("fp64_fix_tau", 1e-2)),
-                      int(p.get("reflux", 1)))
+                      int(p.get("reflux", 1)), RIEMANN[p.get("riemann", "lf")])
 
 
 def make_refine(r: Dict) -> map_refine_params:

@@ -424,7 +424,7 @@ static bool params_equal(const map_params& a, const map_params& b) {
   return a.gamma == b.gamma && a.c_cfl == b.c_cfl && a.ch_mode == b.ch_mode && a.ch == b.ch &&
          a.cp_mode == b.cp_mode && a.c_d == b.c_d && a.cp == b.cp && a.eta == b.eta && a.eglm == b.eglm &&
          a.scheme == b.scheme && a.limiter == b.limiter && a.dt_override == b.dt_override &&
-         a.fp64_fix_tau == b.fp64_fix_tau && a.reflux == b.reflux;
+         a.fp64_fix_tau == b.fp64_fix_tau && a.reflux == b.reflux && a.riemann == b.riemann;
 }
 
 static int check_params(map_pool* pool, const map_params* p) {
@@ -434,6 +434,9 @@ static int check_params(map_pool* pool, const map_params* p) {
   if (p->ch_mode < 0 || p->ch_mode > 2 || p->cp_mode < 0 || p->cp_mode > 1) return fail(pool, MAP_EINVAL, "bad c_h / c_p mode");
   if (p->cp_mode == MAP_CP_FROM_CD && !(p->c_d > 0.0 && p->c_d < 1.0)) return fail(pool, MAP_EINVAL, "c_d must lie in (0,1)");
   if (p->eta < 0.0) return fail(pool, MAP_EINVAL, "eta must be >= 0");
+  if (p->riemann != MAP_RIEMANN_LF && p->riemann != MAP_RIEMANN_HLLC) return fail(pool, MAP_EINVAL, "bad riemann");
+  if (p->riemann == MAP_RIEMANN_HLLC && p->scheme == MAP_MMC)
+    return fail(pool, MAP_EINVAL, "HLLC is an interface flux of LF and WENO; MMC takes MAP_RIEMANN_LF");
   if (!pool->have_tree) return fail(pool, MAP_ESTATE, "no tree");
   size_t smem = is64(pool) ? step_smem_f64(kcfg(pool), p->scheme, p->eta > 0.0)
                            : step_smem_f32(kcfg(pool), p->scheme, p->eta > 0.0);
@@ -477,6 +480,7 @@ static int step_launches(map_pool* pool, const map_params* p, bool fused) {
   S.eglm = p->eglm;
   S.scheme = p->scheme;
   S.limiter = p->limiter;
+  S.riemann = p->riemann;
   S.err_word = pool->err_word;
   S.sums = fused ? pool->sums : nullptr;
   S.dyn_next = fused ? pool->dyn : nullptr;

@@ -135,6 +135,7 @@ struct StepLaunch {
   double* sums;            // optional FP64 conservation sums [nprob][9] of the output
   ProbDyn* dyn_next;       // optional: max alpha of the output into dyn_next[p].alpha_bits
   int grid;                // CTAs (0 = one per block)
+  int riemann;             // interface flux of LF and WENO: 0 f_m, 1 HLLC
   const PushEntry* pushes; // optional: write boundary layers into same-level neighbours' ghosts
   void* freg;              // optional: face registers (reflux); with refl
   const RefluxLeaf* refl;  // per block slot and coarse-side mask
@@ -241,6 +242,8 @@ struct KernelConfig {
 
 MAPGB_DECLARE_LAUNCHERS(f64)
 MAPGB_DECLARE_LAUNCHERS(f32)
+cudaError_t launch_step_hllc_f64(const KernelConfig&, const StepLaunch&, cudaStream_t, long long*);
+cudaError_t launch_step_hllc_f32(const KernelConfig&, const StepLaunch&, cudaStream_t, long long*);
 
 cudaError_t launch_finalize(const FinalizeLaunch&, cudaStream_t, long long*);
 cudaError_t launch_zero_alpha(ProbDyn* dyn, int nprob, cudaStream_t, long long*);

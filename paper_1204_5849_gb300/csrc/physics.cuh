@@ -118,6 +118,110 @@ __device__ __forceinline__ T alpha_dir(int d, const T* w, T p, const Phys<T>& P)
   return d == 0 ? alpha_p<T, 0>(w, p, P) : (d == 1 ? alpha_p<T, 1>(w, p, P) : alpha_p<T, 2>(w, p, P));
 }
 
+// Fast magnetosonic speed along D (c_f of alpha_p without |v_d|); p = pressure of w.
+template <typename T, int D>
+__device__ __forceinline__ T fast_speed(const T* w, T p, const Phys<T>& P) {
+  T rho = w[RHO];
+  if (p < T(0)) p = T(0);
+  if constexpr (std::is_same<T, float>::value) {
+    const T ir = T(1) / rho;
+    T a2 = P.gamma * p * ir;
+    T b2 = (w[BX] * w[BX] + w[BY] * w[BY] + w[BZ] * w[BZ]) * ir;
+    T bd2 = w[BX + D] * w[BX + D] * ir;
+    T s = a2 + b2;
+    T disc = s * s - T(4) * a2 * bd2;
+    if (disc < T(0)) disc = T(0);
+    return sqrtf(T(0.5) * (s + sqrtf(disc)));
+  } else {
+    T a2 = P.gamma * p / rho;
+    T b2 = (w[BX] * w[BX] + w[BY] * w[BY] + w[BZ] * w[BZ]) / rho;
+    T bd2 = w[BX + D] * w[BX + D] / rho;
+    T s = a2 + b2;
+    T disc = s * s - T(4) * a2 * bd2;
+    if (disc < T(0)) disc = T(0);
+    return sqrt(T(0.5) * (s + sqrt(disc)));
+  }
+}
+
+// HLLC interface flux for MHD (Gurski's solver, which the paper names for LF and WENO in
+// 2D/3D, Sec. 3.2-3.3):
+// 1. the linear (B_d, psi) pair keeps its exact upwind flux, the same as in f_m, and fixes
+//    the interface normal field B_m = (B_d,a + B_d,b)/2 - (psi_b - psi_a)/(2 c_h);
+// 2. both states take B_d = B_m at unchanged gas pressure, E' = E + (B_m^2 - B_d^2)/2;
+// 3. speed bounds S_L = min(u - c_f), S_R = max(u + c_f) over the two states (u = v_d);
+// 4. S_L >= 0 or S_R <= 0: the upwind physical flux; otherwise the star state on the side
+//    of the contact speed S_M = (rho u)_HLL / rho_HLL, whose density, normal momentum and
+//    total pressure follow from mass and momentum across S_K, tangential B from the HLL
+//    state, tangential momentum and energy from the jump conditions across S_K, and
+//    F = F_K + S_K (U*_K - U_K).
+template <typename T, int D>
+__device__ __forceinline__ void hllc_flux(const T* a, const T* b, const Phys<T>& P, T* f) {
+  const T ch = P.ch;
+  const T bm = ch > T(0) ? T(0.5) * (a[BX + D] + b[BX + D]) - (b[PSI] - a[PSI]) / (T(2) * ch)
+                         : T(0.5) * (a[BX + D] + b[BX + D]);
+  T w[2][NV], F[2][NV], u[2], cf[2], pt[2];
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const T* q = k ? b : a;
+    const T p = pressure<T>(q, P);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) w[k][v] = q[v];
+    w[k][BX + D] = bm;
+    w[k][EN] = q[EN] + T(0.5) * (bm * bm - q[BX + D] * q[BX + D]);
+    const T pw = pressure<T>(w[k], P);
+    flux_p<T, D>(w[k], pw, P, F[k]);
+    u[k] = w[k][MX + D] / w[k][RHO];
+    cf[k] = fast_speed<T, D>(w[k], pw, P);
+    pt[k] = p + T(0.5) * (w[k][BX] * w[k][BX] + w[k][BY] * w[k][BY] + w[k][BZ] * w[k][BZ]);
+  }
+  const T sl = fmin(u[0] - cf[0], u[1] - cf[1]);
+  const T sr = fmax(u[0] + cf[0], u[1] + cf[1]);
+  if (sl >= T(0)) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) f[v] = F[0][v];
+  } else if (sr <= T(0)) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) f[v] = F[1][v];
+  } else {
+    const T ra = w[0][RHO], rb = w[1][RHO];
+    const T sm = (rb * u[1] * (sr - u[1]) - ra * u[0] * (sl - u[0]) - pt[1] + pt[0]) /
+                 (rb * (sr - u[1]) - ra * (sl - u[0]));
+    constexpr int T1 = D == 0 ? 1 : 0, T2 = D == 2 ? 1 : 2;   // tangential dimensions
+    const T bt1 = (sr * w[1][BX + T1] - sl * w[0][BX + T1] - (F[1][BX + T1] - F[0][BX + T1])) / (sr - sl);
+    const T bt2 = (sr * w[1][BX + T2] - sl * w[0][BX + T2] - (F[1][BX + T2] - F[0][BX + T2])) / (sr - sl);
+    const int k = sm >= T(0) ? 0 : 1;
+    const T sk = k ? sr : sl;
+    T wk[NV], Fk[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      wk[v] = k ? w[1][v] : w[0][v];
+      Fk[v] = k ? F[1][v] : F[0][v];
+    }
+    const T uk = k ? u[1] : u[0], ptk = k ? pt[1] : pt[0];
+    const T dk = sk - uk, ds = sk - sm;
+    const T rs = wk[RHO] * dk / ds;
+    const T pts = ptk + wk[RHO] * dk * (sm - uk);
+    const T vbk = (wk[MX] / wk[RHO]) * wk[BX] + (wk[MX + 1] / wk[RHO]) * wk[BY] + (wk[MX + 2] / wk[RHO]) * wk[BZ];
+    T us[NV];
+    us[RHO] = rs;
+    us[MX + D] = rs * sm;
+    us[MX + T1] = rs * (wk[MX + T1] / wk[RHO]) - bm * (bt1 - wk[BX + T1]) / ds;
+    us[MX + T2] = rs * (wk[MX + T2] / wk[RHO]) - bm * (bt2 - wk[BX + T2]) / ds;
+    T vbs = sm * bm;
+    vbs += (us[MX + T1] / rs) * bt1;
+    vbs += (us[MX + T2] / rs) * bt2;
+    us[BX + D] = bm;
+    us[BX + T1] = bt1;
+    us[BX + T2] = bt2;
+    us[EN] = (wk[EN] * dk - ptk * uk + pts * sm + bm * (vbk - vbs)) / ds;
+    us[PSI] = wk[PSI];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) f[v] = Fk[v] + sk * (us[v] - wk[v]);
+  }
+  f[BX + D] = T(0.5) * ((a[PSI] + b[PSI]) - ch * (b[BX + D] - a[BX + D]));
+  f[PSI] = T(0.5) * ((ch * ch * a[BX + D] + ch * ch * b[BX + D]) - ch * (b[PSI] - a[PSI]));
+}
+
 // Dissipation speed of component v in direction D: the (B_d, psi) pair uses c_h.
 template <int D>
 __device__ __forceinline__ bool glm_pair(int v) { return v == BX + D || v == PSI; }

@@ -27,6 +27,7 @@
 namespace mapgb {
 
 enum { SCH_MMC = 0, SCH_LF = 1, SCH_WENO = 2 };
+enum { FLX_LF = 0, FLX_HLLC = 1 };   // interface flux of LF and WENO: f_m or HLLC
 
 template <typename T>
 struct StepArgsT {
@@ -378,7 +379,7 @@ __device__ __forceinline__ void two_sum_acc(T& hi, T& lo, T h2, T l2) {
   hi = s;
 }
 
-template <typename T, int NDIM, int NB, int SCHEME, int LIM, int STAGE>
+template <typename T, int NDIM, int NB, int SCHEME, int LIM, int STAGE, int FLX>
 __global__ void __launch_bounds__(NB * NB, sizeof(T) == 4 ? (NB == 16 ? 2 : 8) : 1)
 step_kernel(StepArgsT<T> A) {
   using G = Geo<NDIM, NB>;
@@ -608,7 +609,7 @@ step_kernel(StepArgsT<T> A) {
         ldw<T, RING>(tp, rl, t0);
         ldw<T, RING>(tp, rl + rs, t1);
         mmc_face<T, D, LIM>(w0, w1, w2, w3, t0, t1, P, F);
-      } else if (std::is_same<T, float>::value && SCHEME == SCH_LF) {
+      } else if (std::is_same<T, float>::value && SCHEME == SCH_LF && FLX == FLX_LF) {
         float2 ab[NV];
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
@@ -636,7 +637,8 @@ step_kernel(StepArgsT<T> A) {
             b[v] = weno_plus_left<T>(u1, u2, u3);
           }
         }
-        lf_flux<T, D>(a, b, P, F);
+        if (FLX == FLX_HLLC) hllc_flux<T, D>(a, b, P, F);
+        else lf_flux<T, D>(a, b, P, F);
       }
     };
 
@@ -674,7 +676,7 @@ step_kernel(StepArgsT<T> A) {
         ldw<T, RING>(tslot(z), rown, t0);
         ldw<T, RING>(tslot(z + 1), rown, t1);
         mmc_face<T, 2, LIM>(um1, w1, w2, w3, t0, t1, P, F);
-      } else if (std::is_same<T, float>::value && SCHEME == SCH_LF) {
+      } else if (std::is_same<T, float>::value && SCHEME == SCH_LF && FLX == FLX_LF) {
         float2 ab[NV];
         const T* t0p = tslot(z);
         const T* t1p = tslot(z + 1);
@@ -703,7 +705,8 @@ step_kernel(StepArgsT<T> A) {
             b[v] = weno_plus_left<T>(u1, u2, u3);
           }
         }
-        lf_flux<T, 2>(a, b, P, F);
+        if (FLX == FLX_HLLC) hllc_flux<T, 2>(a, b, P, F);
+        else lf_flux<T, 2>(a, b, P, F);
       }
     };
 

@@ -297,6 +297,72 @@ def test_last_sums_needs_an_advance_step(gpulib):
     np.testing.assert_allclose(pool.last_sums(), pool.conservation(), rtol=1e-13, atol=1e-15)
 
 
+# --- HLLC interface flux for LF and WENO (Sec. 3.2-3.3) -----------------------------------
+
+@pytest.mark.parametrize("scheme,limiter", [("lf", "minmod"), ("lf", "vanleer"), ("weno", "minmod")])
+@pytest.mark.parametrize("geom", [(2, 16, (3, 2, 1)), (3, 8, (2, 3, 2)), (3, 16, (2, 1, 2))])
+def test_fp64_hllc_matches_oracle(gpulib, scheme, limiter, geom):
+    from paper_1204_5849_gb300 import MAP_FP64
+    ndim, nb, nbase = geom
+    mesh = w.uniform_mesh(ndim, nb, nbase)
+    U0 = w.evaluate_on_mesh(mesh, _smooth_2d if ndim == 2 else _smooth_3d)
+    p = P(scheme=scheme, limiter=limiter, riemann="hllc")
+    pool = pool_for(mesh, MAP_FP64, U0)
+    orc = Oracle(mesh, U0)
+    lockstep(pool, orc, p, 2)
+    assert rel_max(pool.read_leaves(), orc.get_state()).max() <= TOL1
+    assert pool.check() == 0
+
+
+@pytest.mark.parametrize("scheme", ["lf", "weno"])
+def test_fp64_hllc_amr_reflux_matches_oracle(gpulib, scheme):
+    from paper_1204_5849_gb300 import MAP_FP64
+    mesh = _REFLUX_MESHES["3d_nb8_periodic"]()
+    U0 = _mixed_state(mesh)
+    p = P(scheme=scheme, riemann="hllc")
+    pool = pool_for(mesh, MAP_FP64, U0)
+    orc = Oracle(mesh, U0)
+    lockstep(pool, orc, p, 3)
+    assert rel_max(pool.read_leaves(), orc.get_state()).max() <= 1e-12
+
+
+def test_fp64_hllc_brio_wu_matches_oracle(gpulib):
+    """Strong shocks exercise every branch (supersonic sides, both star states)."""
+    from paper_1204_5849_gb300 import MAP_FP64
+    n = 256
+    mesh = w.uniform_mesh(2, 16, (n // 16, 1), lo=(-0.5, 0, 0), hi=(0.5, 16.0 / n, 1),
+                          bc=((w.mesh.OUTFLOW, w.mesh.OUTFLOW), (0, 0), (0, 0)))
+    U0 = w.evaluate_on_mesh(mesh, w.problems.brio_wu)
+    p = P(gamma=2.0, scheme="lf", riemann="hllc")
+    pool = pool_for(mesh, MAP_FP64, U0)
+    orc = Oracle(mesh, U0)
+    lockstep(pool, orc, p, 40)
+    assert rel_max(pool.read_leaves(), orc.get_state()).max() <= 1e-10
+
+
+def test_fp32_hllc_alfven_l1(gpulib):
+    from paper_1204_5849_gb300 import MAP_FP32_FIX64
+    mesh = w.uniform_mesh(3, 16, (2, 2, 2))
+    U0 = w.evaluate_on_mesh(mesh, _smooth_3d)
+    p = P(scheme="lf", limiter="vanleer", riemann="hllc")
+    pool = pool_for(mesh, MAP_FP32_FIX64, U0)
+    pool.advance(p, 10)
+    orc = Oracle(mesh, U0)
+    orc.advance(p, 10)
+    assert rel_l1(pool.read_leaves(), orc.get_state()).max() <= 1e-5
+    assert pool.check() == 0
+
+
+def test_hllc_rejected_for_mmc(gpulib):
+    from paper_1204_5849_gb300 import MAP_FP64, MapError
+    mesh = w.uniform_mesh(2, 16, (2, 2))
+    pool = pool_for(mesh, MAP_FP64, _mixed_state(mesh))
+    pool.fill_ghosts()
+    with pytest.raises(MapError) as ei:
+        pool.cfl_dt(P(scheme="mmc", riemann="hllc"))
+    assert ei.value.code == -1
+
+
 # --- several independent problems of uneven sizes -----------------------------------------
 
 def test_fp64_ensemble(gpulib):
