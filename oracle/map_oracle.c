@@ -79,6 +79,7 @@ struct orc_mesh {
   int maxlev;
   int* order; /* blocks sorted by key */
   double *dt, *ch, *cp, *damp, *alpha_g;
+  double* dtc;    /* thermal-conduction time step of the last CFL reduction */
   int have_dt;
 };
 
@@ -856,6 +857,7 @@ orc_mesh* orc_create(int ndim, int nb, int nprob, const orc_problem* probs, int 
   m->cp = (double*)calloc((size_t)nprob, sizeof(double));
   m->damp = (double*)calloc((size_t)nprob, sizeof(double));
   m->alpha_g = (double*)calloc((size_t)nprob, sizeof(double));
+  m->dtc = (double*)calloc((size_t)nprob, sizeof(double));
   return m;
 }
 
@@ -863,7 +865,7 @@ void orc_destroy(orc_mesh* m) {
   if (!m) return;
   for (int q = 0; q < m->nblocks; ++q) { free(m->b[q].u); free(m->b[q].u1); }
   free(m->b); free(m->order); free(m->leaf_block); free(m->probs);
-  free(m->dt); free(m->ch); free(m->cp); free(m->damp); free(m->alpha_g);
+  free(m->dt); free(m->ch); free(m->cp); free(m->damp); free(m->alpha_g); free(m->dtc);
   free(m);
 }
 
@@ -1019,11 +1021,26 @@ int orc_fill_ghosts(orc_mesh* m) {
 /* ------------------------------------------------------------------------------------ */
 /* Time step (Sec. 3.7 and Sec. 2: c_h, c_p).                                               */
 
+/* Temperature T = p / rho (p clamped at 0) and conductivity kappa = kappa0 T^(5/2). */
+static double temperature(const double* w, double gamma) {
+  double p = pressure(w, gamma);
+  if (p < 0.0) p = 0.0;
+  return p / w[RHO];
+}
+
+static double kappa_of(double T, double kappa0) { return kappa0 * (T * T * sqrt(T)); }
+
+/* The rate in the conduction time step: kappa T / p, written kappa / rho (equal for p > 0,
+ * and finite at p = 0). */
+static double conduction_rate(const double* w, const orc_params* pr) {
+  return kappa_of(temperature(w, pr->gamma), pr->kappa0) / w[RHO];
+}
+
 int orc_cfl(orc_mesh* m, const orc_params* pr, double* dt_out) {
   geom g = mesh_geom(m);
   int nd = m->ndim;
   for (int p = 0; p < m->nprob; ++p) {
-    double ag = 0.0, mindx = INFINITY;
+    double ag = 0.0, mindx = INFINITY, kmax = 0.0;
     for (int q = 0; q < m->nblocks; ++q) {
       const oblk* o = &m->b[q];
       if (o->leaf < 0 || o->problem != p) continue;
@@ -1037,6 +1054,10 @@ int orc_cfl(orc_mesh* m, const orc_params* pr, double* dt_out) {
           double a = orc_alpha(d, w, pr->gamma);
           if (a > ag || a != a) ag = a;
         }
+        if (pr->conduction) {
+          const double kt = conduction_rate(w, pr);
+          if (kt > kmax || kt != kt) kmax = kt;
+        }
       }
     }
     /* alpha_g: global maximal wave speed; a fixed c_h is a signal speed too */
@@ -1047,7 +1068,13 @@ int orc_cfl(orc_mesh* m, const orc_params* pr, double* dt_out) {
       double dtr = pr->c_cfl * mindx * mindx / (2.0 * (double)nd * pr->eta);
       if (dtr < dt) dt = dtr;
     }
+    /* thermal conduction (Sec. 3.6): dt_c = c_cfl min(dx)^2 / (n_dim max(kappa T / p)); without
+     * the subcycle it bounds the step itself */
+    double dtc = INFINITY;
+    if (pr->conduction && kmax > 0.0) dtc = pr->c_cfl * mindx * mindx / ((double)nd * kmax);
+    if (pr->conduction && !pr->subcycle && dtc < dt) dt = dtc;
     if (pr->dt_override > 0.0) dt = pr->dt_override;
+    m->dtc[p] = dtc;
     double ch;
     if (pr->ch_mode == 0) ch = ag;
     else if (pr->ch_mode == 1) ch = pr->c_cfl * mindx / dt;
@@ -1169,6 +1196,175 @@ static void copy_interior(const geom* g, const double* src, double* dst) {
   }
 }
 
+/* ------------------------------------------------------------------------------------ */
+/* Thermal conduction (Sec. 3.6, and the field-aligned form of the Sec. 5 test).            */
+
+/* One conduction update of the energy of a ghost-filled block over h (interior written to
+ * e_out[nz*nb*nb]):  e_i += h sum_d (F_d,i+1/2 - F_d,i-1/2) / dx_d  with
+ *   isotropic:     F = sqrt(kappa_i kappa_i+1) (T_i+1 - T_i) / dx_d   (the paper's scheme),
+ *   field-aligned: F = sqrt(kappa_i kappa_i+1) b_d (b . grad T)   at the face, b = B_f/|B_f|
+ *                  with B_f the mean of the two cells' B, the normal derivative as above and
+ *                  each transverse derivative the mean of the two cells' central differences
+ *                  (no flux where B_f = 0).
+ * A face temperature gradient beyond gradT_max (> 0) is clipped to it.  Boundary face fluxes go
+ * to the face register (energy slot) when one is given. */
+static void conduction_block(const geom* g, const stepctx* s, const orc_params* pr, const double* u,
+                             double h, double* e_out) {
+  const int nd = g->ndim, nb = g->nb;
+  double* T = (double*)calloc((size_t)g->S, sizeof(double));
+  double* K = (double*)calloc((size_t)g->S, sizeof(double));
+  FOR_REGION(g, 1, k, j, i) {
+    const int c = cidx(g, k, j, i);
+    double w[NV];
+    load(g, u, c, w);
+    T[c] = temperature(w, pr->gamma);
+    K[c] = kappa_of(T[c], pr->kappa0);
+  }
+  int q = 0;
+  FOR_REGION(g, NG, k, j, i) {
+    const int c = cidx(g, k, j, i);
+    double acc = 0.0;
+    for (int d = 0; d < nd; ++d) {
+      const int o = g->off[d];
+      double F[2];
+      for (int side = 0; side < 2; ++side) {
+        const int cl = side ? c : c - o, cr = cl + o;      /* face between cl and cr */
+        double gn = (T[cr] - T[cl]) / s->dx[d];
+        if (pr->grad_t_max > 0.0) gn = fmax(-pr->grad_t_max, fmin(pr->grad_t_max, gn));
+        const double kf = sqrt(K[cl] * K[cr]);
+        if (pr->conduction == 1) {
+          F[side] = kf * gn;
+        } else {
+          double bf[3], b2 = 0.0;
+          for (int j2 = 0; j2 < 3; ++j2) {
+            bf[j2] = 0.5 * (u[(BX + j2) * g->S + cl] + u[(BX + j2) * g->S + cr]);
+            b2 += bf[j2] * bf[j2];
+          }
+          if (!(b2 > 0.0)) {
+            F[side] = 0.0;
+          } else {
+            double bg = bf[d] * gn;
+            for (int t = 0; t < nd; ++t) {
+              if (t == d) continue;
+              const int ot = g->off[t];
+              double gt = 0.5 * ((T[cl + ot] - T[cl - ot]) / (2.0 * s->dx[t]) +
+                                 (T[cr + ot] - T[cr - ot]) / (2.0 * s->dx[t]));
+              if (pr->grad_t_max > 0.0) gt = fmax(-pr->grad_t_max, fmin(pr->grad_t_max, gt));
+              bg += bf[t] * gt;
+            }
+            F[side] = kf * bf[d] * bg / b2;
+          }
+        }
+      }
+      if (icoord(d, k, j, i) == 0 && s->freg) {
+        double f9[NV] = {0};
+        f9[EN] = -F[0];                    /* as a flux of e along +d: e -= h dF/dx */
+        record_face(g, s, d, 0, k, j, i, f9);
+      }
+      if (icoord(d, k, j, i) == nb - 1 && s->freg) {
+        double f9[NV] = {0};
+        f9[EN] = -F[1];
+        record_face(g, s, d, 1, k, j, i, f9);
+      }
+      acc += (F[1] - F[0]) / s->dx[d];
+    }
+    e_out[q++] = u[EN * g->S + c] + h * acc;
+  }
+  free(T);
+  free(K);
+}
+
+/* The conduction part of a step over dt: n substeps of dt/n, n = ceil(dt / dt_c) with the
+ * subcycle (dt_c of the last CFL reduction, i.e. the state before the MHD update), else one.
+ * Each substep refills the ghosts and, on AMR, refluxes the energy at coarse/fine faces. */
+static void conduction_step(orc_mesh* m, const orc_params* pr) {
+  geom g = mesh_geom(m);
+  const int nd = m->ndim, nb = m->nb;
+  const int ncell = (nd == 3 ? nb : 1) * nb * nb;
+  const size_t per = (size_t)2 * nd * NV * nb * nb;
+  int nsub = 1;
+  for (int p = 0; p < m->nprob; ++p)
+    if (pr->subcycle && m->dtc[p] < m->dt[p]) {
+      const int n = (int)ceil(m->dt[p] / m->dtc[p]);
+      if (n > nsub) nsub = n;
+    }
+  double* hsub = (double*)malloc(sizeof(double) * (size_t)m->nprob);
+  double* dtsave = (double*)malloc(sizeof(double) * (size_t)m->nprob);
+  for (int p = 0; p < m->nprob; ++p) {
+    int n = 1;
+    if (pr->subcycle && m->dtc[p] < m->dt[p]) n = (int)ceil(m->dt[p] / m->dtc[p]);
+    hsub[p] = m->dt[p] / (double)n;
+    dtsave[p] = m->dt[p];
+  }
+  double* enew = (double*)malloc(sizeof(double) * (size_t)m->nblocks * ncell);
+  double* freg = (pr->reflux && m->maxlev > 0) ? (double*)malloc((size_t)m->nblocks * per * sizeof(double)) : NULL;
+  for (int it = 0; it < nsub; ++it) {
+    orc_fill_ghosts(m);
+    if (freg) memset(freg, 0, (size_t)m->nblocks * per * sizeof(double));
+#pragma omp parallel for schedule(dynamic)
+    for (int q = 0; q < m->nblocks; ++q) {
+      oblk* o = &m->b[q];
+      if (o->leaf < 0) continue;
+      int n = 1;
+      if (pr->subcycle && m->dtc[o->problem] < m->dt[o->problem]) n = (int)ceil(m->dt[o->problem] / m->dtc[o->problem]);
+      if (it >= n) continue;                       /* this problem needs fewer substeps */
+      stepctx s = make_ctx(m, pr, o);
+      if (freg) s.freg = freg + (size_t)q * per;
+      conduction_block(&g, &s, pr, o->u, hsub[o->problem], enew + (size_t)q * ncell);
+    }
+    for (int q = 0; q < m->nblocks; ++q) {
+      oblk* o = &m->b[q];
+      if (o->leaf < 0) continue;
+      int n = 1;
+      if (pr->subcycle && m->dtc[o->problem] < m->dt[o->problem]) n = (int)ceil(m->dt[o->problem] / m->dtc[o->problem]);
+      if (it >= n) continue;
+      int c = 0;
+      FOR_REGION(&g, NG, k, j, i) o->u[EN * g.S + cidx(&g, k, j, i)] = enew[(size_t)q * ncell + c++];
+    }
+    if (freg) {
+      /* the energy flux of this substep, refluxed with lam = h / dx */
+      for (int p = 0; p < m->nprob; ++p) m->dt[p] = hsub[p];
+      apply_reflux(m, freg);
+      for (int p = 0; p < m->nprob; ++p) m->dt[p] = dtsave[p];
+    }
+  }
+  free(enew);
+  free(freg);
+  free(hsub);
+  free(dtsave);
+}
+
+/* The conduction part alone over dt (its time step from the current state), for the pins. */
+int orc_conduct(orc_mesh* m, const orc_params* pr, double dt) {
+  geom g = mesh_geom(m);
+  const int nd = m->ndim;
+  for (int p = 0; p < m->nprob; ++p) {
+    double mindx = INFINITY, kmax = 0.0;
+    for (int q = 0; q < m->nblocks; ++q) {
+      const oblk* o = &m->b[q];
+      if (o->leaf < 0 || o->problem != p) continue;
+      double dx[3];
+      block_dx(m, o, dx);
+      for (int d = 0; d < nd; ++d) if (dx[d] < mindx) mindx = dx[d];
+      FOR_REGION(&g, NG, k, j, i) {
+        double w[NV];
+        load(&g, o->u, cidx(&g, k, j, i), w);
+        const double kt = conduction_rate(w, pr);
+        if (kt > kmax || kt != kt) kmax = kt;
+      }
+    }
+    m->dtc[p] = kmax > 0.0 ? pr->c_cfl * mindx * mindx / ((double)nd * kmax) : INFINITY;
+    m->dt[p] = dt;
+  }
+  conduction_step(m, pr);
+  return check_state(m, pr->gamma);
+}
+
+int orc_get_dtc(const orc_mesh* m, double* out) {
+  for (int p = 0; p < m->nprob; ++p) out[p] = m->dtc[p];
+  return 0;
+}
+
 int orc_step(orc_mesh* m, const orc_params* pr) {
   if (!m->have_dt) return -1;
   geom g = mesh_geom(m);
@@ -1248,6 +1444,7 @@ int orc_step(orc_mesh* m, const orc_params* pr) {
       FLOPS(1);
     }
   }
+  if (pr->conduction) conduction_step(m, pr);
   m->have_dt = 0;
   FLCAT(3);
   const int rc = check_state(m, pr->gamma);

@@ -34,6 +34,10 @@ typedef struct {
   double dt_override; /* > 0: use this dt */
   int reflux;       /* 1: coarse fluxes at coarse/fine faces replaced by the fine ones */
   int riemann;      /* interface flux of LF and WENO: 0 f_m (Lax-Friedrichs), 1 HLLC */
+  int conduction;   /* thermal conduction: 0 off, 1 isotropic, 2 along B (kappa0 T^(5/2)) */
+  double kappa0;
+  int subcycle;     /* 1: conduction subcycled within each step; 0: it bounds dt */
+  double grad_t_max;/* > 0: face temperature gradients clipped to +-grad_t_max */
 } orc_params;
 
 typedef struct {
@@ -65,6 +69,10 @@ int orc_fill_ghosts(orc_mesh* m);
 int orc_cfl(orc_mesh* m, const orc_params* p, double* dt_out);
 int orc_get_speeds(const orc_mesh* m, double* out /* [nprob][5]: dt ch cp damp alpha_g */);
 int orc_step(orc_mesh* m, const orc_params* p);
+/* Thermal conduction alone over dt (Sec. 3.6), with its own time step and subcycle. */
+int orc_conduct(orc_mesh* m, const orc_params* p, double dt);
+/* Conduction time step per problem of the last reduction (orc_cfl or orc_conduct). */
+int orc_get_dtc(const orc_mesh* m, double* out);
 int orc_flags(orc_mesh* m, const orc_params* p, const orc_refine* r, signed char* flags,
               double* est_max);
 int orc_conservation(const orc_mesh* m, double* sums);

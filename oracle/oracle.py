@@ -15,6 +15,7 @@ from . import build as _build
 
 SCHEMES = {"mmc": 0, "lf": 1, "weno": 2}
 RIEMANN = {"lf": 0, "hllc": 1}
+CONDUCTION = {"off": 0, "isotropic": 1, "aligned": 2}
 LIMITERS = {"minmod": 0, "vanleer": 1, "roe": 2}
 CH_MODES = {"auto": 0, "paper": 1, "fixed": 2}
 CP_MODES = {"cd": 0, "fixed": 1}
@@ -26,7 +27,8 @@ class orc_params(C.Structure):
                 ("ch", C.c_double), ("cp_mode", C.c_int), ("c_d", C.c_double),
                 ("cp", C.c_double), ("eta", C.c_double), ("eglm", C.c_int),
                 ("scheme", C.c_int), ("limiter", C.c_int), ("dt_override", C.c_double),
-                ("reflux", C.c_int), ("riemann", C.c_int)]
+                ("reflux", C.c_int), ("riemann", C.c_int), ("conduction", C.c_int),
+                ("kappa0", C.c_double), ("subcycle", C.c_int), ("grad_t_max", C.c_double)]
 
 
 class orc_problem(C.Structure):
@@ -74,6 +76,8 @@ def _declare(L):
         L.orc_cfl.argtypes = [C.c_void_p, C.POINTER(orc_params), dp]
         L.orc_get_speeds.argtypes = [C.c_void_p, dp]
         L.orc_step.argtypes = [C.c_void_p, C.POINTER(orc_params)]
+        L.orc_conduct.argtypes = [C.c_void_p, C.POINTER(orc_params), C.c_double]
+        L.orc_get_dtc.argtypes = [C.c_void_p, dp]
         L.orc_flags.argtypes = [C.c_void_p, C.POINTER(orc_params), C.POINTER(orc_refine),
                                 C.POINTER(C.c_byte), dp]
         L.orc_conservation.argtypes = [C.c_void_p, dp]
@@ -106,7 +110,9 @@ def make_params(p: Dict) -> orc_params:
                       float(p.get("cp", 0.0)), float(p.get("eta", 0.0)), int(p.get("eglm", 1)),
                       SCHEMES[p.get("scheme", "mmc")], LIMITERS[p.get("limiter", "minmod")],
                       float(p.get("dt_override", 0.0)), int(p.get("reflux", 1)),
-                      RIEMANN[p.get("riemann", "lf")])
+                      RIEMANN[p.get("riemann", "lf")], CONDUCTION[p.get("conduction", "off")],
+                      float(p.get("kappa0", 0.0)), int(p.get("subcycle", 1)),
+                      float(p.get("grad_t_max", 0.0)))
 
 
 def make_refine(r: Dict) -> orc_refine:
@@ -186,6 +192,15 @@ class Oracle:
         dt = np.zeros(len(self.mesh.problems))
         self._rc = lib().orc_cfl(self.h, C.byref(make_params(params)), _dp(dt))
         return dt
+
+    def conduct(self, params: Dict, dt: float) -> int:
+        """Thermal conduction alone over dt (its own time step and subcycle)."""
+        return lib().orc_conduct(self.h, C.byref(make_params(params)), float(dt))
+
+    def dtc(self) -> np.ndarray:
+        out = np.zeros(len(self.mesh.problems))
+        lib().orc_get_dtc(self.h, _dp(out))
+        return out
 
     def speeds(self) -> np.ndarray:
         out = np.zeros((len(self.mesh.problems), 5))
