@@ -48,6 +48,9 @@ enum { MAP_MINMOD = 0, MAP_VANLEER = 1 };
 /* Interface flux of LF and WENO (Sec. 3.2-3.3): the Lax-Friedrichs f_m (Equ:LFFlux) or the
  * HLLC approximate Riemann solver for MHD the paper uses in 2D and 3D. */
 enum { MAP_RIEMANN_LF = 0, MAP_RIEMANN_HLLC = 1 };
+/* Thermal conduction (Sec. 3.6): off, isotropic, or along the field (the form of the paper's
+ * conduction test, Sec. 5), kappa = kappa0 T^(5/2) with T = p / rho. */
+enum { MAP_COND_OFF = 0, MAP_COND_ISOTROPIC = 1, MAP_COND_ALIGNED = 2 };
 enum { MAP_BC_PERIODIC = 0, MAP_BC_OUTFLOW = 1 };
 enum { MAP_CH_AUTO = 0, MAP_CH_PAPER = 1, MAP_CH_FIXED = 2 };
 enum { MAP_CP_FROM_CD = 0, MAP_CP_FIXED = 1 };
@@ -105,6 +108,16 @@ typedef struct {
                          the exact upwind flux of its linear system, which also fixes the
                          interface normal field; the other seven components come from the
                          HLLC star states with Davis speed bounds */
+  int conduction;     /* MAP_COND_*: after each step the energy takes the conduction update
+                         e += h sum_d dF_d/dx_d, F = sqrt(kappa_l kappa_r)(T_r - T_l)/dx (along
+                         B: times b_d (b . grad T)/|grad_d T| with b from the face-mean B) */
+  double kappa0;      /* conduction coefficient (> 0 when conduction is on) */
+  int subcycle;       /* 1: n = ceil(dt/dt_c) conduction substeps of dt/n inside each step,
+                         dt_c = c_cfl min(dx)^2 / (n_dim max(kappa/rho)); 0: dt <= dt_c and
+                         one update.  With conduction, map_advance reads dt back every step
+                         to size the loop and is not graph-replayed */
+  double grad_t_max;  /* > 0: face temperature gradients clipped to +-grad_t_max (Sec. 3.6
+                         threshold); 0: none */
 } map_params;
 
 /* Refinement estimator parameters (Sec. 4.5). */

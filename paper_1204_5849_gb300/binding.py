@@ -22,6 +22,7 @@ MAP_FP64, MAP_FP32_FIX64 = 0, 1
 SCHEMES = {"mmc": 0, "lf": 1, "weno": 2}
 LIMITERS = {"minmod": 0, "vanleer": 1}
 RIEMANN = {"lf": 0, "hllc": 1}
+CONDUCTION = {"off": 0, "isotropic": 1, "aligned": 2}
 CH_MODES = {"auto": 0, "paper": 1, "fixed": 2}
 CP_MODES = {"cd": 0, "fixed": 1}
 REFINE_VARS = {"rho": 1, "p": 2, "j": 4}
@@ -48,7 +49,8 @@ class map_params(C.Structure):
                 ("ch", C.c_double), ("cp_mode", C.c_int), ("c_d", C.c_double), ("cp", C.c_double),
                 ("eta", C.c_double), ("eglm", C.c_int), ("scheme", C.c_int), ("limiter", C.c_int),
                 ("dt_override", C.c_double), ("fp64_fix_tau", C.c_double), ("reflux", C.c_int),
-                ("riemann", C.c_int)]
+                ("riemann", C.c_int), ("conduction", C.c_int), ("kappa0", C.c_double),
+                ("subcycle", C.c_int), ("grad_t_max", C.c_double)]
 
 
 class map_refine_params(C.Structure):
@@ -144,7 +146,9 @@ def make_params(p: Dict) -> map_params:
                       float(p.get("cp", 0.0)), float(p.get("eta", 0.0)), int(p.get("eglm", 1)),
                       SCHEMES[p.get("scheme", "mmc")], LIMITERS[p.get("limiter", "minmod")],
                       float(p.get("dt_override", 0.0)), float(p.get("fp64_fix_tau", 1e-2)),
-                      int(p.get("reflux", 1)), RIEMANN[p.get("riemann", "lf")])
+                      int(p.get("reflux", 1)), RIEMANN[p.get("riemann", "lf")],
+                      CONDUCTION[p.get("conduction", "off")], float(p.get("kappa0", 0.0)),
+                      int(p.get("subcycle", 1)), float(p.get("grad_t_max", 0.0)))
 
 
 def make_refine(r: Dict) -> map_refine_params:

@@ -50,7 +50,8 @@ struct Shell {
 
 template <typename T, int NDIM, int NB>
 __global__ void __launch_bounds__(256) fill_kernel(T* __restrict__ u, const int* __restrict__ blocks,
-                                                   int n, const GhostRegion* __restrict__ regions, int skip_pushed) {
+                                                   int n, const GhostRegion* __restrict__ regions, int skip_pushed,
+                                                   int v0, int v1) {
   using G = Geo<NDIM, NB>;
   using SH = Shell<NDIM, NB>;
   constexpr int NP = G::NP, P2 = G::P2, S = G::S;
@@ -77,9 +78,11 @@ __global__ void __launch_bounds__(256) fill_kernel(T* __restrict__ u, const int*
         const int sc = (sk * NP + sj) * NP + si;
         T val[NV];
 #pragma unroll
-        for (int v = 0; v < NV; ++v) val[v] = sb[(size_t)v * S + sc];
+        for (int v = 0; v < NV; ++v)
+          if (v >= v0 && v < v1) val[v] = sb[(size_t)v * S + sc];
 #pragma unroll
-        for (int v = 0; v < NV; ++v) ub[(size_t)v * S + c] = val[v];
+        for (int v = 0; v < NV; ++v)
+          if (v >= v0 && v < v1) ub[(size_t)v * S + c] = val[v];
       } else {
         const int gi = gr.m[0] * i + gr.a[0], gj = gr.m[1] * j + gr.a[1];
         const int gk = NDIM == 3 ? gr.m[2] * k + gr.a[2] : 0;
@@ -91,6 +94,7 @@ __global__ void __launch_bounds__(256) fill_kernel(T* __restrict__ u, const int*
         const T oz = (gk & 1) ? T(0.25) : T(-0.25);
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
+          if (v < v0 || v >= v1) continue;
           const T* f = sb + (size_t)v * S;
           T val = f[cc];
           val += minmod<T>(f[cc + 1] - f[cc], f[cc] - f[cc - 1]) * ox;
@@ -145,11 +149,12 @@ __device__ __forceinline__ void load_global(const T* b, size_t S, int c, T* w) {
 // alpha_g: max over leaf interior cells and directions of |v_d| + c_f,d (Sec. 3.7).
 template <typename T, int NDIM, int NB>
 __global__ void __launch_bounds__(256) cfl_kernel(const T* __restrict__ u, const int* __restrict__ blocks, int n,
-                                                  const BlockGeo* __restrict__ geo, ProbDyn* dyn, T gamma, T gm1) {
+                                                  const BlockGeo* __restrict__ geo, ProbDyn* dyn, T gamma, T gm1,
+                                                  double kappa0) {
   using G = Geo<NDIM, NB>;
   constexpr int NP = G::NP, S = G::S;
   constexpr int NI = NDIM == 3 ? NB * NB * NB : NB * NB;
-  __shared__ double red[32];
+  __shared__ double red[32], redk[32];
   Phys<T> P;
   P.gamma = gamma;
   P.gm1 = gm1;
@@ -158,7 +163,7 @@ __global__ void __launch_bounds__(256) cfl_kernel(const T* __restrict__ u, const
   for (int bi = blockIdx.x; bi < n; bi += gridDim.x) {
     const int blk = blocks[bi];
     const T* ub = u + (size_t)blk * NV * S;
-    double am = 0.0;
+    double am = 0.0, km = 0.0;
     for (int c = threadIdx.x; c < NI; c += blockDim.x) {
       const int i = c % NB, j = (c / NB) % NB, k = NDIM == 3 ? c / (NB * NB) : 0;
       const int cc = ((NDIM == 3 ? k + NG : 0) * NP + j + NG) * NP + i + NG;
@@ -170,17 +175,33 @@ __global__ void __launch_bounds__(256) cfl_kernel(const T* __restrict__ u, const
       if (NDIM == 3) a = fmax(a, (double)alpha_p<T, 2>(w, p, P));
       if (a != a) am = a;            // NaN wins
       else if (!(am != am)) am = fmax(am, a);
+      if (kappa0 > 0.0) {
+        // kappa T / p read as kappa / rho, kappa = kappa0 T^(5/2), T = max(p, 0) / rho
+        const T tt = (p < T(0) ? T(0) : p) / w[RHO];
+        const double kr = (double)((T)kappa0 * (tt * tt * sqrt(tt)) / w[RHO]);
+        if (kr != kr) km = kr;
+        else if (!(km != km)) km = fmax(km, kr);
+      }
     }
     for (int o = 16; o > 0; o >>= 1) {
       double t = __shfl_xor_sync(0xffffffffu, am, o);
       am = (t != t) ? t : fmax(am, t);
+      double t2 = __shfl_xor_sync(0xffffffffu, km, o);
+      km = (t2 != t2) ? t2 : fmax(km, t2);
     }
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = am;
+    if ((threadIdx.x & 31) == 0) {
+      red[threadIdx.x >> 5] = am;
+      redk[threadIdx.x >> 5] = km;
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
-      double a = 0.0;
-      for (int q = 0; q < (int)(blockDim.x + 31) / 32; ++q) a = (red[q] != red[q]) ? red[q] : fmax(a, red[q]);
+      double a = 0.0, kk = 0.0;
+      for (int q = 0; q < (int)(blockDim.x + 31) / 32; ++q) {
+        a = (red[q] != red[q]) ? red[q] : fmax(a, red[q]);
+        kk = (redk[q] != redk[q]) ? redk[q] : fmax(kk, redk[q]);
+      }
       atomicMax(&dyn[geo[blk].problem].alpha_bits, (unsigned long long)__double_as_longlong(a));
+      if (kappa0 > 0.0) atomicMax(&dyn[geo[blk].problem].kmax_bits, (unsigned long long)__double_as_longlong(kk));
     }
     __syncthreads();
   }
@@ -445,11 +466,13 @@ __global__ void __launch_bounds__(256) reflux_kernel(RefluxLaunch L) {
     if (NDIM == 3) ci[db] = t1;
     return ((NDIM == 3 ? ci[2] + NG : 0) * NP + ci[1] + NG) * NP + ci[0] + NG;
   };
+  if (L.nsub && L.it >= L.nsub[gg.problem]) return;        // no substep for this problem
+  const double dtp = L.hsub ? L.hsub[gg.problem] : dy.dt;
   for (int d = 0; d < NDIM; ++d)
     for (int side = 0; side < 2; ++side) {
       const int f = 2 * d + side;
       if (!((mask >> f) & 1)) continue;
-      const T lam = (T)(dy.dt / gg.dx[d]);
+      const T lam = (T)(dtp / gg.dx[d]);
       const T* rc = freg + (size_t)tk.cslot * PER + (size_t)f * NV * NB2;
       for (int idx = threadIdx.x; idx < NF; idx += blockDim.x) {
         const int t0 = idx % NB, t1 = NDIM == 3 ? idx / NB : 0;
@@ -460,6 +483,7 @@ __global__ void __launch_bounds__(256) reflux_kernel(RefluxLaunch L) {
         const int c = cell_of(d, side, t0, t1, ci);
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
+          if (v < L.v0 || v >= L.v1) continue;
           const T* fv = rf + (size_t)v * NB2;
           T ff;
           if (NDIM == 2) ff = T(0.5) * (fv[f0] + fv[f0 + 1]);
@@ -570,6 +594,110 @@ __global__ void __launch_bounds__(256) reflux_kernel(RefluxLaunch L) {
         atomicAdd(&L.sums[gg.problem * NV + v], t * vol);
       }
     }
+  }
+}
+
+
+// Thermal conduction (Sec. 3.6), one substep on one leaf per CTA, in place on the energy:
+//   e_i += h sum_d (F_d,i+1/2 - F_d,i-1/2) / dx_d,  kappa = kappa0 T^(5/2), T = max(p,0)/rho,
+//   isotropic:     F = sqrt(kappa_l kappa_r) (T_r - T_l) / dx_d,
+//   along B:       F = sqrt(kappa_l kappa_r) b_d (b . grad T), b = B_f / |B_f| with B_f the
+//                  mean of the two cells' B, transverse derivatives the mean of the two
+//                  cells' central differences (no flux where B_f = 0),
+// face gradients clipped to +-grad_t_max when it is > 0.  T and kappa of the interior and its
+// one-cell ring are staged in shared memory first; other leaves read this leaf's energy only
+// through their own ghost copies, so the in-place write is safe.  Boundary face fluxes go to
+// the face register's energy slot as fluxes of e along +d (-F) for reflux.
+template <typename T, int NDIM, int NB>
+__global__ void __launch_bounds__(256) conduction_kernel(CondLaunch L) {
+  using G = Geo<NDIM, NB>;
+  constexpr int NP = G::NP, S = G::S;
+  constexpr int R = NB + 2;
+  constexpr int NR = NDIM == 3 ? R * R * R : R * R;
+  constexpr int NI = NDIM == 3 ? NB * NB * NB : NB * NB;
+  constexpr size_t NB2 = (size_t)NB * NB;
+  extern __shared__ __align__(16) unsigned char csm[];
+  T* sT = reinterpret_cast<T*>(csm);
+  T* sK = sT + NR;
+  const int blk = L.blocks[blockIdx.x];
+  const BlockGeo gg = L.geo[blk];
+  if (L.it >= L.nsub[gg.problem]) return;
+  const T h = (T)L.hsub[gg.problem];
+  T* ub = (T*)L.u + (size_t)blk * NV * S;
+  Phys<T> P;
+  P.gamma = (T)L.gamma;
+  P.gm1 = (T)(L.gamma - 1.0);
+  P.ch = T(0);
+  P.tau = (T)L.tau;
+  const T k0 = (T)L.kappa0, gmax = (T)L.grad_t_max;
+  // region cell r = (ri, rj, rk) is padded cell (ri+1, rj+1, rk+1)
+  for (int r = threadIdx.x; r < NR; r += blockDim.x) {
+    const int ri = r % R, rj = (r / R) % R, rk = NDIM == 3 ? r / (R * R) : 0;
+    const int c = ((NDIM == 3 ? rk + 1 : 0) * NP + rj + 1) * NP + ri + 1;
+    T w[NV];
+    load_global<T>(ub, S, c, w);
+    T p = pressure<T>(w, P);
+    if (p < T(0)) p = T(0);
+    const T tt = p / w[RHO];
+    sT[r] = tt;
+    sK[r] = k0 * (tt * tt * sqrt(tt));
+  }
+  __syncthreads();
+  const int slot = L.freg ? L.refl[blk].slot : -1;
+  T* R0 = slot >= 0 ? (T*)L.freg + (size_t)slot * (2 * NDIM * NV * NB2) : nullptr;
+  const int ro[3] = {1, R, R * R};
+  const int po[3] = {1, NP, NP * NP};
+  for (int q = threadIdx.x; q < NI; q += blockDim.x) {
+    const int i = q % NB, j = (q / NB) % NB, k = NDIM == 3 ? q / (NB * NB) : 0;
+    const int r = ((NDIM == 3 ? k + 1 : 0) * R + j + 1) * R + i + 1;
+    const int c = ((NDIM == 3 ? k + NG : 0) * NP + j + NG) * NP + i + NG;
+    const int ic[3] = {i, j, k};
+    T acc = T(0);
+#pragma unroll
+    for (int d = 0; d < NDIM; ++d) {
+      T F[2];
+#pragma unroll
+      for (int side = 0; side < 2; ++side) {
+        const int rl = side ? r : r - ro[d], rr = rl + ro[d];
+        const int cl = side ? c : c - po[d], cr = cl + po[d];
+        T gn = (sT[rr] - sT[rl]) / (T)gg.dx[d];
+        if (gmax > T(0)) gn = fmax(-gmax, fmin(gmax, gn));
+        const T kf = sqrt(sK[rl] * sK[rr]);
+        if (L.mode == 1) {
+          F[side] = kf * gn;
+        } else {
+          T bf[3], b2 = T(0);
+#pragma unroll
+          for (int j2 = 0; j2 < 3; ++j2) {
+            bf[j2] = T(0.5) * (ub[(size_t)(BX + j2) * S + cl] + ub[(size_t)(BX + j2) * S + cr]);
+            b2 += bf[j2] * bf[j2];
+          }
+          if (!(b2 > T(0))) {
+            F[side] = T(0);
+          } else {
+            T bg = bf[d] * gn;
+#pragma unroll
+            for (int t = 0; t < NDIM; ++t) {
+              if (t == d) continue;
+              const T dxt = (T)gg.dx[t];
+              T gt = T(0.5) * ((sT[rl + ro[t]] - sT[rl - ro[t]]) / (T(2) * dxt) +
+                               (sT[rr + ro[t]] - sT[rr - ro[t]]) / (T(2) * dxt));
+              if (gmax > T(0)) gt = fmax(-gmax, fmin(gmax, gt));
+              bg += bf[t] * gt;
+            }
+            F[side] = kf * bf[d] * bg / b2;
+          }
+        }
+      }
+      if (R0) {
+        const int da = d == 0 ? 1 : 0, db = d == 2 ? 1 : 2;
+        const int t0 = ic[da], t1 = NDIM == 3 ? ic[db] : 0;
+        if (ic[d] == 0) R0[(size_t)(2 * d) * NV * NB2 + (size_t)EN * NB2 + t1 * NB + t0] = -F[0];
+        if (ic[d] == NB - 1) R0[(size_t)(2 * d + 1) * NV * NB2 + (size_t)EN * NB2 + t1 * NB + t0] = -F[1];
+      }
+      acc += (F[1] - F[0]) / (T)gg.dx[d];
+    }
+    ub[(size_t)EN * S + c] = ub[(size_t)EN * S + c] + h * acc;
   }
 }
 

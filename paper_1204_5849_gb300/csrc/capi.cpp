@@ -42,6 +42,10 @@ struct map_pool {
   ProbDyn* dyn = nullptr;
   unsigned* err_word = nullptr;
   double* sums = nullptr;
+  double* hsub = nullptr;    // conduction substep per problem (device)
+  int* nsub = nullptr;       // conduction substeps per problem (device)
+  std::vector<double> hsub_h;
+  std::vector<int> nsub_h;
   double* staging = nullptr;
   size_t staging_elems = 0;
   int8_t* flags = nullptr;
@@ -170,7 +174,9 @@ int map_create_pool(const map_pool_desc* d, void* stream, map_pool** out) {
     if (cudaMemsetAsync(pool->buf[q], 0, buf_bytes, pool->stream) != cudaSuccess) return cleanup(MAP_ECUDA, "memset failed");
   if (cudaMalloc(&pool->dyn, sizeof(ProbDyn) * pool->nprob) != cudaSuccess ||
       cudaMalloc(&pool->err_word, sizeof(unsigned)) != cudaSuccess ||
-      cudaMalloc(&pool->sums, sizeof(double) * kNV * pool->nprob) != cudaSuccess)
+      cudaMalloc(&pool->sums, sizeof(double) * kNV * pool->nprob) != cudaSuccess ||
+      cudaMalloc(&pool->hsub, sizeof(double) * pool->nprob) != cudaSuccess ||
+      cudaMalloc(&pool->nsub, sizeof(int) * pool->nprob) != cudaSuccess)
     return cleanup(MAP_ENOMEM, "cudaMalloc of the step constants failed");
   cudaMemsetAsync(pool->dyn, 0, sizeof(ProbDyn) * pool->nprob, pool->stream);
   cudaMemsetAsync(pool->err_word, 0, sizeof(unsigned), pool->stream);
@@ -187,6 +193,8 @@ int map_destroy_pool(map_pool* pool) {
   if (!pool->ext)
     for (int q = 0; q < 3; ++q) cudaFree(pool->buf[q]);
   cudaFree(pool->dyn);
+  cudaFree(pool->hsub);
+  cudaFree(pool->nsub);
   cudaFree(pool->err_word);
   cudaFree(pool->sums);
   cudaFree(pool->staging);
@@ -376,6 +384,32 @@ static int fill_on(map_pool* pool, int q) {
   return MAP_OK;
 }
 
+// ghosts of the energy alone on buffer q, every region (between conduction substeps)
+static int fill_energy_on(map_pool* pool, int q) {
+  const HostTree& t = pool->tree;
+  const DevTree& D = pool->dt;
+  for (int L = t.maxlev - 1; L >= 0; --L) {
+    RestrictLaunch R;
+    R.u = pool->buf[q];
+    R.parents = D.level_parents + D.parent_off[L];
+    R.nparents = D.parent_off[L + 1] - D.parent_off[L];
+    R.children = D.children;
+    CK(DISPATCH(pool, restrict, R));
+  }
+  for (int L = 0; L <= t.maxlev; ++L) {
+    FillLaunch F;
+    F.u = pool->buf[q];
+    F.blocks = D.level_leaves + D.leaf_off[L];
+    F.nblocks = D.leaf_off[L + 1] - D.leaf_off[L];
+    F.regions = D.regions;
+    F.skip_pushed = 0;
+    F.v0 = kEN;
+    F.v1 = kEN + 1;
+    CK(DISPATCH(pool, fill, F));
+  }
+  return MAP_OK;
+}
+
 int map_fill_ghosts(map_pool* pool) {
   if (!pool) return MAP_EINVAL;
   if (!pool->have_tree) return fail(pool, MAP_ESTATE, "no tree");
@@ -395,6 +429,8 @@ static FinalizeLaunch make_finalize(const map_pool* pool, const map_params* p) {
   F.dt_override = p->dt_override;
   F.ch_mode = p->ch_mode;
   F.cp_mode = p->cp_mode;
+  F.conduction = p->conduction;
+  F.subcycle = p->subcycle;
   return F;
 }
 
@@ -408,6 +444,7 @@ static int alpha_device(map_pool* pool, const map_params* p) {
   C.geo = pool->dt.geo;
   C.dyn = pool->dyn;
   C.gamma = p->gamma;
+  C.kappa0 = p->conduction ? p->kappa0 : 0.0;
   CK(DISPATCH(pool, cfl, C));
   return MAP_OK;
 }
@@ -424,7 +461,9 @@ static bool params_equal(const map_params& a, const map_params& b) {
   return a.gamma == b.gamma && a.c_cfl == b.c_cfl && a.ch_mode == b.ch_mode && a.ch == b.ch &&
          a.cp_mode == b.cp_mode && a.c_d == b.c_d && a.cp == b.cp && a.eta == b.eta && a.eglm == b.eglm &&
          a.scheme == b.scheme && a.limiter == b.limiter && a.dt_override == b.dt_override &&
-         a.fp64_fix_tau == b.fp64_fix_tau && a.reflux == b.reflux && a.riemann == b.riemann;
+         a.fp64_fix_tau == b.fp64_fix_tau && a.reflux == b.reflux && a.riemann == b.riemann &&
+         a.conduction == b.conduction && a.kappa0 == b.kappa0 && a.subcycle == b.subcycle &&
+         a.grad_t_max == b.grad_t_max;
 }
 
 static int check_params(map_pool* pool, const map_params* p) {
@@ -435,6 +474,9 @@ static int check_params(map_pool* pool, const map_params* p) {
   if (p->cp_mode == MAP_CP_FROM_CD && !(p->c_d > 0.0 && p->c_d < 1.0)) return fail(pool, MAP_EINVAL, "c_d must lie in (0,1)");
   if (p->eta < 0.0) return fail(pool, MAP_EINVAL, "eta must be >= 0");
   if (p->riemann != MAP_RIEMANN_LF && p->riemann != MAP_RIEMANN_HLLC) return fail(pool, MAP_EINVAL, "bad riemann");
+  if (p->conduction < MAP_COND_OFF || p->conduction > MAP_COND_ALIGNED) return fail(pool, MAP_EINVAL, "bad conduction mode");
+  if (p->conduction && !(p->kappa0 > 0.0)) return fail(pool, MAP_EINVAL, "conduction needs kappa0 > 0");
+  if (!(p->grad_t_max >= 0.0)) return fail(pool, MAP_EINVAL, "grad_t_max must be >= 0");
   if (p->riemann == MAP_RIEMANN_HLLC && p->scheme == MAP_MMC)
     return fail(pool, MAP_EINVAL, "HLLC is an interface flux of LF and WENO; MMC takes MAP_RIEMANN_LF");
   if (!pool->have_tree) return fail(pool, MAP_ESTATE, "no tree");
@@ -549,6 +591,74 @@ static int step_launches(map_pool* pool, const map_params* p, bool fused) {
   return MAP_OK;
 }
 
+// Thermal conduction over the step just taken (Sec. 3.6): n = ceil(dt / dt_c) substeps of
+// dt / n per problem with the subcycle (dt and dt_c of the reduction before the step), else
+// one; each refills the ghosts (the first all variables, then the energy alone), updates the
+// energy in place and refluxes it at coarse/fine faces.  Reads dt back to size the loop.
+static int conduction_launches(map_pool* pool, const map_params* p) {
+  const int np = pool->nprob;
+  std::vector<ProbDyn> dyn(np);
+  CK(cudaMemcpyAsync(dyn.data(), pool->dyn, sizeof(ProbDyn) * np, cudaMemcpyDeviceToHost, pool->stream));
+  CK(cudaStreamSynchronize(pool->stream));
+  pool->hsub_h.assign(np, 0.0);
+  pool->nsub_h.assign(np, 1);
+  int nmax = 1;
+  for (int q = 0; q < np; ++q) {
+    double n = 1.0;
+    if (p->subcycle && dyn[q].dtc < dyn[q].dt) n = ceil(dyn[q].dt / dyn[q].dtc);
+    if (!(n <= 1048576.0)) return fail(pool, MAP_EUNSUPPORTED, "thermal conduction would need more than 2^20 substeps");
+    pool->nsub_h[q] = (int)n;
+    pool->hsub_h[q] = dyn[q].dt / (double)(int)n;
+    if ((int)n > nmax) nmax = (int)n;
+  }
+  CK(cudaMemcpyAsync(pool->hsub, pool->hsub_h.data(), sizeof(double) * np, cudaMemcpyHostToDevice, pool->stream));
+  CK(cudaMemcpyAsync(pool->nsub, pool->nsub_h.data(), sizeof(int) * np, cudaMemcpyHostToDevice, pool->stream));
+  const bool rf = p->reflux != 0 && pool->dt.nrtasks > 0;
+  for (int it = 0; it < nmax; ++it) {
+    int rc = it == 0 ? fill_on(pool, pool->cur) : fill_energy_on(pool, pool->cur);
+    if (rc) return rc;
+    CondLaunch C;
+    C.u = pool->buf[pool->cur];
+    C.blocks = pool->dt.all_leaves;
+    C.nblocks = pool->tree.nleaves;
+    C.geo = pool->dt.geo;
+    C.gamma = p->gamma;
+    C.tau = is64(pool) ? 0.0 : (p->fp64_fix_tau > 0.0 ? p->fp64_fix_tau : 0.0);
+    C.kappa0 = p->kappa0;
+    C.grad_t_max = p->grad_t_max;
+    C.mode = p->conduction;
+    C.hsub = pool->hsub;
+    C.nsub = pool->nsub;
+    C.it = it;
+    C.freg = rf ? pool->dt.freg : nullptr;
+    C.refl = rf ? pool->dt.refl : nullptr;
+    CK(DISPATCH(pool, conduction, C));
+    if (rf) {
+      RefluxLaunch R;
+      R.u = pool->buf[pool->cur];
+      R.tasks = pool->dt.rtasks;
+      R.ntasks = pool->dt.nrtasks;
+      R.freg = pool->dt.freg;
+      R.geo = pool->dt.geo;
+      R.dyn = pool->dyn;
+      R.pushes = pool->dt.pushes;
+      R.gamma = p->gamma;
+      R.tau = C.tau;
+      R.err_word = pool->err_word;
+      R.sums = nullptr;
+      R.dyn_next = nullptr;
+      R.v0 = kEN;
+      R.v1 = kEN + 1;
+      R.hsub = pool->hsub;
+      R.nsub = pool->nsub;
+      R.it = it;
+      CK(DISPATCH(pool, reflux, R));
+    }
+  }
+  pool->pushed[pool->cur] = false;       // the energy ghosts are stale now
+  return MAP_OK;
+}
+
 int map_step(map_pool* pool, const map_params* p) {
   if (!pool) return MAP_EINVAL;
   int rc = check_params(pool, p);
@@ -559,6 +669,7 @@ int map_step(map_pool* pool, const map_params* p) {
     if (rc) return rc;
   }
   rc = step_launches(pool, p, false);
+  if (rc == MAP_OK && p->conduction) rc = conduction_launches(pool, p);
   pool->have_dt = false;
   pool->alpha_ready = false;
   pool->sums_valid = false;
@@ -580,6 +691,23 @@ int map_advance(map_pool* pool, const map_params* p, int nsteps) {
   int rc = check_params(pool, p);
   if (rc) return rc;
   if (nsteps <= 0) return MAP_OK;
+  if (p->conduction) {
+    // the substep count depends on dt: each step runs eagerly (fill, dt, update, conduction)
+    for (int s = 0; s < nsteps; ++s) {
+      rc = fill_on(pool, pool->cur);
+      if (rc) return rc;
+      rc = cfl_device(pool, p);
+      if (rc) return rc;
+      rc = step_launches(pool, p, false);
+      if (rc) return rc;
+      rc = conduction_launches(pool, p);
+      if (rc) return rc;
+    }
+    pool->have_dt = false;
+    pool->alpha_ready = false;
+    pool->sums_valid = false;
+    return MAP_OK;
+  }
   if (!params_equal(pool->graph_params, *p)) {
     drop_graphs(pool);
     pool->graph_params = *p;

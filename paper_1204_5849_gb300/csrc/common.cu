@@ -20,6 +20,12 @@ __global__ void finalize_kernel(FinalizeLaunch L) {
     const double dtr = L.c_cfl * d.mindx * d.mindx / (2.0 * (double)L.ndim * L.eta);
     if (dtr < dt) dt = dtr;
   }
+  // thermal conduction (Sec. 3.6): dt_c = c_cfl min(dx)^2 / (n_dim max(kappa T / p)), the
+  // rate read as kappa / rho; without the subcycle it bounds dt
+  double dtc = __longlong_as_double(0x7ff0000000000000ll);
+  const double kmax = __longlong_as_double((long long)d.kmax_bits);
+  if (L.conduction && kmax > 0.0) dtc = L.c_cfl * d.mindx * d.mindx / ((double)L.ndim * kmax);
+  if (L.conduction && !L.subcycle && dtc < dt) dt = dtc;
   if (L.dt_override > 0.0) dt = L.dt_override;
   double ch;
   if (L.ch_mode == MAP_CH_AUTO) ch = ag;
@@ -33,12 +39,17 @@ __global__ void finalize_kernel(FinalizeLaunch L) {
   d.damp = damp;
   d.alpha_g = ag;
   d.alpha_bits = 0ull;
+  d.kmax_bits = 0ull;
+  d.dtc = dtc;
   L.dyn[p] = d;
 }
 
 __global__ void zero_alpha_kernel(ProbDyn* dyn, int n) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p < n) dyn[p].alpha_bits = 0ull;
+  if (p < n) {
+    dyn[p].alpha_bits = 0ull;
+    dyn[p].kmax_bits = 0ull;
+  }
 }
 
 cudaError_t launch_finalize(const FinalizeLaunch& L, cudaStream_t s, long long* cnt) {

@@ -101,7 +101,8 @@ cudaError_t launch_fill_T(const KernelConfig& kc, const FillLaunch& L, cudaStrea
   if (L.nblocks <= 0) return cudaSuccess;
   if (cnt) ++*cnt;
 #define CALL_FILL(ND, NBV)                                                                   \
-  fill_kernel<T, ND, NBV><<<grid_for(L.nblocks), 256, 0, s>>>((T*)L.u, L.blocks, L.nblocks, L.regions, L.skip_pushed); \
+  fill_kernel<T, ND, NBV><<<grid_for(L.nblocks), 256, 0, s>>>((T*)L.u, L.blocks, L.nblocks, L.regions, L.skip_pushed, \
+                                                              L.v0, L.v1);                                \
   return cudaGetLastError()
   MAPGB_GEO_DISPATCH(kc, CALL_FILL);
 #undef CALL_FILL
@@ -124,7 +125,7 @@ cudaError_t launch_cfl_T(const KernelConfig& kc, const CflLaunch& L, cudaStream_
   if (cnt) ++*cnt;
 #define CALL_CFL(ND, NBV)                                                                     \
   cfl_kernel<T, ND, NBV><<<grid_for(L.nblocks), 256, 0, s>>>((const T*)L.u, L.blocks, L.nblocks, L.geo, L.dyn, \
-                                                             (T)L.gamma, (T)(L.gamma - 1.0)); \
+                                                             (T)L.gamma, (T)(L.gamma - 1.0), L.kappa0); \
   return cudaGetLastError()
   MAPGB_GEO_DISPATCH(kc, CALL_CFL);
 #undef CALL_CFL
@@ -185,6 +186,30 @@ cudaError_t launch_reflux_T(const KernelConfig& kc, const RefluxLaunch& L, cudaS
 #undef CALL_REFLUX
 }
 
+template <typename T, int NDIM, int NB>
+cudaError_t launch_conduction_one(const CondLaunch& L, cudaStream_t s) {
+  constexpr int R = NB + 2;
+  constexpr size_t smem = (size_t)2 * (NDIM == 3 ? R * R * R : R * R) * sizeof(T);
+  auto kern = conduction_kernel<T, NDIM, NB>;
+  static bool attr_done = false;
+  if (!attr_done) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr_done = true;
+  }
+  kern<<<L.nblocks, 256, smem, s>>>(L);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_conduction_T(const KernelConfig& kc, const CondLaunch& L, cudaStream_t s, long long* cnt) {
+  if (L.nblocks <= 0) return cudaSuccess;
+  if (cnt) ++*cnt;
+#define CALL_COND(ND, NBV) return launch_conduction_one<T, ND, NBV>(L, s)
+  MAPGB_GEO_DISPATCH(kc, CALL_COND);
+#undef CALL_COND
+}
+
 template <typename T>
 cudaError_t launch_cfl_partial_T(const KernelConfig& kc, const void* u, int nblocks, double gamma, double* partial,
                                  cudaStream_t s) {
@@ -211,6 +236,7 @@ cudaError_t launch_cfl_partial_T(const KernelConfig& kc, const void* u, int nblo
   cudaError_t launch_pack_##SUFFIX(const KernelConfig& k, const PackLaunch& l, cudaStream_t s, long long* c) { return launch_pack_T<T>(k, l, s, c); } \
   cudaError_t launch_regrid_##SUFFIX(const KernelConfig& k, const RegridLaunch& l, cudaStream_t s, long long* c) { return launch_regrid_T<T>(k, l, s, c); } \
   cudaError_t launch_reflux_##SUFFIX(const KernelConfig& k, const RefluxLaunch& l, cudaStream_t s, long long* c) { return launch_reflux_T<T>(k, l, s, c); } \
+  cudaError_t launch_conduction_##SUFFIX(const KernelConfig& k, const CondLaunch& l, cudaStream_t s, long long* c) { return launch_conduction_T<T>(k, l, s, c); } \
   size_t step_smem_##SUFFIX(const KernelConfig& k, int scheme, int res) { return step_smem_T<T>(k, scheme, res); } \
   cudaError_t launch_cfl_partial_##SUFFIX(const KernelConfig& k, const void* u, int n, double g, double* part, cudaStream_t s) { return launch_cfl_partial_T<T>(k, u, n, g, part, s); } \
   }

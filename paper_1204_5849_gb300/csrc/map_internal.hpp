@@ -13,6 +13,7 @@ namespace mapgb {
 
 constexpr int kNV = 9;
 constexpr int kNG = 2;
+constexpr int kEN = 7;      // index of the energy density among the 9 variables
 
 // Per pool block: geometry of one block (leaf or parent).
 struct BlockGeo {
@@ -27,7 +28,9 @@ struct BlockGeo {
 struct ProbDyn {
   double dt, ch, cp, damp, alpha_g, mindx;
   unsigned long long alpha_bits;   // running max of alpha (as ordered bits, alpha >= 0)
-  unsigned long long pad;
+  unsigned long long kmax_bits;    // running max of kappa / rho (thermal conduction), as bits
+  double dtc;                      // thermal-conduction time step (Sec. 3.6), +inf if none
+  double pad;
 };
 
 // One ghost region of a leaf (3^ndim regions, region id = rx + 3 ry + 9 rz with
@@ -153,6 +156,26 @@ struct RefluxLaunch {
   unsigned* err_word;
   double* sums;            // optional: FP64 sums of the corrected cells (fused form)
   ProbDyn* dyn_next;       // optional: alpha max of the corrected cells (fused form)
+  int v0 = 0, v1 = kNV;    // variables corrected: [v0, v1)
+  const double* hsub = nullptr;  // conduction substeps: lam = hsub[p] / dx (else dyn dt)
+  const int* nsub = nullptr;     // with hsub: problems with it >= nsub[p] are skipped
+  int it = 0;
+};
+
+// Thermal conduction (Sec. 3.6): one substep of the energy update over hsub[p] on every
+// leaf of a problem with it < nsub[p], in place (ghosts filled).
+struct CondLaunch {
+  void* u;
+  const int* blocks;       // leaves
+  int nblocks;
+  const BlockGeo* geo;
+  double gamma, tau, kappa0, grad_t_max;
+  int mode;                // 1 isotropic, 2 along B
+  const double* hsub;
+  const int* nsub;
+  int it;
+  void* freg;              // optional face registers (energy slot, as a flux of e along +d)
+  const RefluxLeaf* refl;
 };
 
 struct FillLaunch {
@@ -161,6 +184,7 @@ struct FillLaunch {
   int nblocks;
   const GhostRegion* regions;
   int skip_pushed;         // 1: leave regions the previous step kernel wrote
+  int v0 = 0, v1 = kNV;    // variables filled: [v0, v1)
 };
 
 struct RestrictLaunch {
@@ -177,6 +201,7 @@ struct CflLaunch {
   const BlockGeo* geo;
   ProbDyn* dyn;
   double gamma;
+  double kappa0 = 0.0;     // > 0: also reduce max kappa / rho into dyn.kmax_bits
 };
 
 struct FinalizeLaunch {
@@ -185,6 +210,7 @@ struct FinalizeLaunch {
   int ndim;
   double c_cfl, eta, ch_fixed, cp_fixed, c_d, dt_override;
   int ch_mode, cp_mode;
+  int conduction = 0, subcycle = 1;   // conduction on: dt_c; without the subcycle dt <= dt_c
 };
 
 struct FlagLaunch {
@@ -236,6 +262,7 @@ struct KernelConfig {
   cudaError_t launch_pack_##SUFFIX(const KernelConfig&, const PackLaunch&, cudaStream_t, long long*); \
   cudaError_t launch_regrid_##SUFFIX(const KernelConfig&, const RegridLaunch&, cudaStream_t, long long*); \
   cudaError_t launch_reflux_##SUFFIX(const KernelConfig&, const RefluxLaunch&, cudaStream_t, long long*); \
+  cudaError_t launch_conduction_##SUFFIX(const KernelConfig&, const CondLaunch&, cudaStream_t, long long*); \
   size_t step_smem_##SUFFIX(const KernelConfig&, int scheme, int resistive); \
   cudaError_t launch_cfl_partial_##SUFFIX(const KernelConfig&, const void* u, int nblocks, double gamma, \
                                           double* partial, cudaStream_t);

@@ -363,6 +363,85 @@ def test_hllc_rejected_for_mmc(gpulib):
     assert ei.value.code == -1
 
 
+# --- thermal conduction with subcycle (Sec. 3.6) -------------------------------------------
+
+def _hot_state(mesh):
+    def ic(X, Y, Z, **_):
+        r2 = (X - 0.5) ** 2 + (Y - 0.45) ** 2 + ((Z - 0.5) ** 2 if mesh.ndim == 3 else 0.0)
+        rho = 0.1 * (1.0 - 0.6 * np.exp(-r2 / 0.02))
+        return w.conserved_from_primitive(rho, 0.02, -0.01, 0.0, 1.0, 1.0, 0.3 + 0 * X, 0.1 + 0 * X, 5 / 3)
+    return w.evaluate_on_mesh(mesh, ic)
+
+
+_COND_MESHES = {
+    "2d_uniform": lambda: w.uniform_mesh(2, 16, (2, 3)),
+    "3d_uniform_nb8": lambda: w.uniform_mesh(3, 8, (2, 2, 2)),
+    "2d_amr": lambda: w.radial_amr_mesh(2, 8, (2, 2), 2, radii=(0.16, 0.34), bc=w.mesh.PERIODIC,
+                                        lo=(0, 0, 0), hi=(1, 1, 1), centre=(0.5, 0.5, 0)),
+}
+
+
+@pytest.mark.parametrize("geom", sorted(_COND_MESHES))
+@pytest.mark.parametrize("mode", ["isotropic", "aligned"])
+@pytest.mark.parametrize("subcycle", [1, 0])
+def test_fp64_conduction_matches_oracle(gpulib, geom, mode, subcycle):
+    from paper_1204_5849_gb300 import MAP_FP64
+    mesh = _COND_MESHES[geom]()
+    U0 = _hot_state(mesh)
+    p = P(scheme="lf", conduction=mode, kappa0=5e-3, subcycle=subcycle, grad_t_max=0.0)
+    pool = pool_for(mesh, MAP_FP64, U0)
+    orc = Oracle(mesh, U0)
+    lockstep(pool, orc, p, 3)
+    assert rel_max(pool.read_leaves(), orc.get_state()).max() <= 1e-12
+    assert pool.check() == 0
+
+
+def test_fp64_conduction_clipped_weno_matches_oracle(gpulib):
+    from paper_1204_5849_gb300 import MAP_FP64
+    mesh = _COND_MESHES["2d_amr"]()
+    U0 = _hot_state(mesh)
+    p = P(scheme="weno", conduction="aligned", kappa0=2e-3, grad_t_max=0.5)
+    pool = pool_for(mesh, MAP_FP64, U0)
+    orc = Oracle(mesh, U0)
+    lockstep(pool, orc, p, 2)
+    assert rel_max(pool.read_leaves(), orc.get_state()).max() <= 1e-12
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_conduction_advance_equals_step_sequence(gpulib, prec):
+    mesh = _COND_MESHES["2d_amr"]()
+    U0 = _hot_state(mesh)
+    p = P(scheme="lf", conduction="isotropic", kappa0=2e-3)
+    a = pool_for(mesh, prec, U0)
+    b = pool_for(mesh, prec, U0)
+    a.advance(p, 4)
+    for _ in range(4):
+        b.fill_ghosts(); b.cfl_dt(p); b.step(p)
+    np.testing.assert_array_equal(a.read_leaves(), b.read_leaves())
+
+
+def test_fp32_conduction_l1(gpulib):
+    from paper_1204_5849_gb300 import MAP_FP32_FIX64
+    mesh = _COND_MESHES["2d_uniform"]()
+    U0 = _hot_state(mesh)
+    p = P(scheme="lf", conduction="aligned", kappa0=2e-3)
+    pool = pool_for(mesh, MAP_FP32_FIX64, U0)
+    pool.advance(p, 5)
+    orc = Oracle(mesh, U0)
+    orc.advance(p, 5)
+    assert rel_l1(pool.read_leaves(), orc.get_state()).max() <= 1e-5
+
+
+def test_conduction_needs_kappa0(gpulib):
+    from paper_1204_5849_gb300 import MAP_FP64, MapError
+    mesh = w.uniform_mesh(2, 16, (2, 2))
+    pool = pool_for(mesh, MAP_FP64, _hot_state(mesh))
+    pool.fill_ghosts()
+    with pytest.raises(MapError) as ei:
+        pool.cfl_dt(P(conduction="isotropic", kappa0=0.0))
+    assert ei.value.code == -1
+
+
 # --- several independent problems of uneven sizes -----------------------------------------
 
 def test_fp64_ensemble(gpulib):
