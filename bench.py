@@ -236,6 +236,29 @@ def run_workload(args):
         out[key] = {"value": cell_updates / (ms * 1e-3), "unit": METRIC, "ms_per_step": ms / nsteps,
                     "steps": nsteps, "wall_s": wall, "leaves_end": pool.nleaves,
                     "adapt_ms_total": adapt_ms, "check": pool.check()}
+        if params.get("conduction", "off") != "off":
+            # the conduction share: the same steps without conduction, and the substep count
+            _, nsub = pool.last_conduction()
+            p_off = dict(params, conduction="off")
+            f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            f0.record(stream)
+            for s in range(nsteps):
+                if prec == MAP_FP32_FIX64:
+                    pool.advance(p_off, 1)
+                else:
+                    pool.fill_ghosts(); pool.cfl_dt(p_off); pool.step(p_off)
+            f1.record(stream)
+            torch.cuda.synchronize()
+            ms_off = f0.elapsed_time(f1)
+            n = int(nsub.max())
+            per_sub = (ms - ms_off) / nsteps / max(n, 1)
+            cells = pool.nleaves * mesh0.cells_per_block
+            bpc = 9 * (4 if prec == MAP_FP32_FIX64 else 8)     # read 8 variables + write e
+            out[key]["conduction"] = {"substeps_per_step": n, "ms_per_step_without": ms_off / nsteps,
+                                      "ms_per_substep": per_sub,
+                                      "substep_cells_per_s": cells / (per_sub * 1e-3),
+                                      "algorithmic_gbs": bpc * cells / (per_sub * 1e-3) / 1e9,
+                                      "bytes_per_cell": bpc}
         pool.close()
     if args.workload in ("ot2d", "ensemble") and not args.no_cpu:
         from oracle import Oracle
@@ -267,7 +290,7 @@ def main():
     ap.add_argument("--quick", action="store_true", help="value and kernel timing only (profiling)")
     ap.add_argument("--prec", type=int, default=32, choices=(32, 64), help="pool precision of --quick runs")
     ap.add_argument("--workload", default="alfven3d",
-                    choices=("alfven3d", "ot2d", "rotor_amr", "harris_amr", "ensemble"),
+                    choices=("alfven3d", "ot2d", "rotor_amr", "harris_amr", "ensemble", "conduction"),
                     help="secondary configurations print their own line")
     ap.add_argument("--small", action="store_true", help="small variant of a secondary workload")
     args = ap.parse_args()

@@ -240,6 +240,11 @@ int map_conservation(map_pool* pool, double* sums_out);
  * regrid).  Synchronises. */
 int map_last_sums(map_pool* pool, double* sums_out);
 
+/* Thermal conduction of the last step, per problem: the conduction time step dt_c of the
+ * reduction before it (+inf without conduction) and the number of conduction substeps it
+ * ran (1 without the subcycle).  Synchronises. */
+int map_last_conduction(map_pool* pool, double* dtc_out, int* nsub_out);
+
 /* Per problem: dt, c_h, c_p, psi damping factor, alpha_g of the last CFL reduction
  * (out[n_problems][5]).  Synchronises. */
 int map_get_speeds(map_pool* pool, double* out);

@@ -88,6 +88,7 @@ _SIGS = {
     "map_regrid": (C.c_int, [C.c_void_p, C.POINTER(map_block_desc), C.c_int]),
     "map_conservation": (C.c_int, [C.c_void_p, C.c_void_p]),
     "map_last_sums": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "map_last_conduction": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "map_get_speeds": (C.c_int, [C.c_void_p, C.c_void_p]),
     "map_kernel_launches": (C.c_longlong, [C.c_void_p]),
     "map_last_error": (C.c_char_p, [C.c_void_p]),
@@ -331,6 +332,14 @@ class Pool:
         out = np.zeros((len(self.mesh.problems), 9))
         self._ck(load().map_conservation(self.h, _ptr(out)), "map_conservation")
         return out
+
+    def last_conduction(self):
+        """(dt_c per problem, conduction substeps of the last step per problem)."""
+        dtc = np.zeros(len(self.mesh.problems))
+        n = np.zeros(len(self.mesh.problems), dtype=np.int32)
+        self._ck(load().map_last_conduction(self.h, _ptr(dtc), n.ctypes.data_as(C.c_void_p)),
+                 "map_last_conduction")
+        return dtc, n
 
     def last_sums(self) -> np.ndarray:
         """Conservation sums reduced by the last map_advance step (no extra pass)."""

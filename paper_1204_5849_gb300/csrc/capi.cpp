@@ -890,6 +890,18 @@ int map_conservation(map_pool* pool, double* sums_out) {
   return MAP_OK;
 }
 
+int map_last_conduction(map_pool* pool, double* dtc_out, int* nsub_out) {
+  if (!pool || !dtc_out || !nsub_out) return fail(pool, MAP_EINVAL, "null argument");
+  std::vector<ProbDyn> dyn(pool->nprob);
+  CK(cudaMemcpyAsync(dyn.data(), pool->dyn, sizeof(ProbDyn) * pool->nprob, cudaMemcpyDeviceToHost, pool->stream));
+  CK(cudaStreamSynchronize(pool->stream));
+  for (int q = 0; q < pool->nprob; ++q) {
+    dtc_out[q] = dyn[q].dtc;
+    nsub_out[q] = q < (int)pool->nsub_h.size() ? pool->nsub_h[q] : 0;
+  }
+  return MAP_OK;
+}
+
 int map_last_sums(map_pool* pool, double* sums_out) {
   if (!pool || !sums_out) return fail(pool, MAP_EINVAL, "null argument");
   if (!pool->sums_valid) return fail(pool, MAP_ESTATE, "the state changed since the last map_advance step");

@@ -328,6 +328,23 @@ def config_ensemble(small: bool = False):
                 params=_params(scheme="mmc", limiter="minmod"), steps=100)
 
 
+def conduction_hot_region(X, Y, Z, gamma=5.0 / 3.0, rho0=0.1, rho_hot=0.025, p0=0.1, half=0.1, **_):
+    """The oblique-field conduction test's state (Sec. 5): uniform rho = 0.1, p = 0.1,
+    B = (1, 1, 0), at rest, with a hot square |x|, |y| < 0.1 of rho = rho_hot (T = p/rho)."""
+    hot = (np.abs(X) < half) & (np.abs(Y) < half)
+    rho = np.where(hot, rho_hot, rho0)
+    return conserved_from_primitive(rho, 0.0, 0.0, 0.0, 1.0, 1.0, 0.0, p0 + 0.0 * X, gamma)
+
+
+def config_conduction(small: bool = False):
+    """2D field-aligned thermal conduction with subcycle, WENO + LF, 256^2 as 16x16 blocks
+    of 16^2 on [-0.5, 0.5]^2, periodic, kappa0 = 1e-3 (the Sec. 5 test's parameters)."""
+    n = 4 if small else 16
+    mesh = uniform_mesh(2, 16, (n, n), lo=(-0.5, -0.5, 0.0), hi=(0.5, 0.5, 1.0))
+    return dict(name=f"conduction2d_weno_aligned_{16 * n}", mesh=mesh, ic=conduction_hot_region, ic_kw={},
+                params=_params(scheme="weno", conduction="aligned", kappa0=1e-3, subcycle=1), steps=20)
+
+
 def ensemble_initial(mesh: Mesh, seed0: int = 1204) -> np.ndarray:
     """Per-problem seeded state: problem p uses seed0 + p."""
     nz, ny, nx = mesh.block_shape()
@@ -350,4 +367,5 @@ CONFIGS: Dict[str, Callable] = {
     "rotor_amr": config_rotor_amr,
     "harris_amr": config_harris_amr,
     "ensemble": config_ensemble,
+    "conduction": config_conduction,
 }
