@@ -293,6 +293,7 @@ def main():
                     choices=("alfven3d", "ot2d", "rotor_amr", "harris_amr", "ensemble", "conduction"),
                     help="secondary configurations print their own line")
     ap.add_argument("--small", action="store_true", help="small variant of a secondary workload")
+    ap.add_argument("--no-tune", action="store_true", help="default launch shape (no autotuner)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     if args.impl == "reference":
@@ -330,6 +331,8 @@ def main():
     main_prec = MAP_FP64 if (args.quick and args.prec == 64) else MAP_FP32_FIX64
     pool = Pool(mesh, main_prec, max_blocks=mesh.nleaves, stream=sptr)
     pool.write_leaves(U0)
+    # launch shape of the step kernel picked by the autotuner (untimed; the state is kept)
+    tune = pool.autotune(params, reps=3) if not args.no_tune else None
     for _ in range(args.warmup):
         pool.advance(params, 1)
     clocks = ClockSampler(local)
@@ -381,7 +384,7 @@ def main():
     if args.quick:
         clocks.stop()
         if rank == 0:
-            print(json.dumps({"metric": METRIC, "value": value, "ms_per_step": ms_max / args.steps,
+            print(json.dumps({"metric": METRIC, "value": value, "ms_per_step": ms_max / args.steps, "launch_shape": tune,
                               "kernel_ms": k_ms, "kernel_ms_alone": k_ms_alone, "achieved_gbs": achieved,
                               "achieved_tflops": tflops, "cells": ncells, "gpu_launches": launches}))
         return
@@ -463,6 +466,7 @@ def main():
         "config": {"workload": WORKLOAD, "cells": ncells, "blocks": mesh.nleaves,
                    "block": "16^3 + 2 ghost layers", "form": "fp32+fp64-fix batched, graph-replayed",
                    "l2": "state (1.2 GB) larger than L2; no flush",
+                   "launch_shape": tune,
                    "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
         "roofline": {"bound": "alu", "achieved": tflops, "peak": fp32_peak, "unit": "TFLOP/s",
                      "frac": tflops / fp32_peak, "traffic": traffic,

@@ -240,6 +240,27 @@ int map_conservation(map_pool* pool, double* sums_out);
  * regrid).  Synchronises. */
 int map_last_sums(map_pool* pool, double* sums_out);
 
+/* Launch shape chosen by map_autotune. */
+typedef struct {
+  int grid;           /* step-kernel CTAs: 0 = one per block, else a persistent grid */
+  int w_pred, w_face; /* warp-schedule cost of a predictor unit and of a face unit */
+  double ms_default;  /* step launches with the default shape (one CTA per block, 7:4) */
+  double ms_best;     /* with the chosen shape */
+  int trials;
+} map_tune_result;
+
+/* Autotuner (no counterpart in the paper): times this pool's step launches on its current
+ * tree and state under candidate launch shapes -- one CTA per block or a persistent grid of
+ * 1-16 x the SM count, then warp-schedule weights for the per-plane work list -- and keeps the
+ * fastest for later map_step / map_advance calls (results are bitwise the same under every
+ * shape; the fused FP64 sums may differ in rounding).  The state is not changed: trials
+ * write only the other buffers, and the step constants and sums are restored.  Ghosts are
+ * refilled first.  reps: timed repetitions per candidate (>= 1).  Synchronises. */
+int map_autotune(map_pool* pool, const map_params* p, int reps, map_tune_result* out);
+
+/* Sets the launch shape directly (grid 0 and weights 0 restore the defaults). */
+int map_set_launch(map_pool* pool, int grid, int w_pred, int w_face);
+
 /* Thermal conduction of the last step, per problem: the conduction time step dt_c of the
  * reduction before it (+inf without conduction) and the number of conduction substeps it
  * ran (1 without the subcycle).  Synchronises. */

@@ -7,6 +7,7 @@ and a thin ctypes binding (binding.py).
 
 from .binding import (MAP_FP32_FIX64, MAP_FP64, MapError, Pool, exported_symbols, load,
                       make_params, make_refine)
+from .autotune import choose_block_size
 
 __all__ = ["Pool", "MapError", "MAP_FP64", "MAP_FP32_FIX64", "load", "exported_symbols",
-           "make_params", "make_refine"]
+           "make_params", "make_refine", "choose_block_size"]

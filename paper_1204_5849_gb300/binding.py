@@ -53,6 +53,11 @@ class map_params(C.Structure):
                 ("subcycle", C.c_int), ("grad_t_max", C.c_double)]
 
 
+class map_tune_result(C.Structure):
+    _fields_ = [("grid", C.c_int), ("w_pred", C.c_int), ("w_face", C.c_int),
+                ("ms_default", C.c_double), ("ms_best", C.c_double), ("trials", C.c_int)]
+
+
 class map_refine_params(C.Structure):
     _fields_ = [("var_mask", C.c_int), ("thr", C.c_double), ("coarsen_thr", C.c_double),
                 ("bias", C.c_double), ("filter", C.c_double), ("eps_rho", C.c_double),
@@ -88,6 +93,8 @@ _SIGS = {
     "map_regrid": (C.c_int, [C.c_void_p, C.POINTER(map_block_desc), C.c_int]),
     "map_conservation": (C.c_int, [C.c_void_p, C.c_void_p]),
     "map_last_sums": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "map_autotune": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
+    "map_set_launch": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int]),
     "map_last_conduction": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "map_get_speeds": (C.c_int, [C.c_void_p, C.c_void_p]),
     "map_kernel_launches": (C.c_longlong, [C.c_void_p]),
@@ -346,6 +353,17 @@ class Pool:
         out = np.zeros((len(self.mesh.problems), 9))
         self._ck(load().map_last_sums(self.h, _ptr(out)), "map_last_sums")
         return out
+
+    def autotune(self, params: Dict, reps: int = 3) -> Dict:
+        """Pick the step kernel's launch shape for this pool (see map_autotune)."""
+        r = map_tune_result()
+        self._ck(load().map_autotune(self.h, C.byref(make_params(params)), int(reps), C.byref(r)),
+                 "map_autotune")
+        return {"grid": r.grid, "w_pred": r.w_pred, "w_face": r.w_face, "ms_default": r.ms_default,
+                "ms_best": r.ms_best, "trials": r.trials}
+
+    def set_launch(self, grid: int = 0, w_pred: int = 0, w_face: int = 0):
+        self._ck(load().map_set_launch(self.h, int(grid), int(w_pred), int(w_face)), "map_set_launch")
 
     def speeds(self) -> np.ndarray:
         out = np.zeros((len(self.mesh.problems), 5))

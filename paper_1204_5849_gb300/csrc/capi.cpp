@@ -57,6 +57,9 @@ struct map_pool {
   bool alpha_ready = false;   // dyn.alpha_bits holds alpha_g of the current state
   bool pushed[3] = {false, false, false};  // buffer q: same-level ghosts written by the last step
   bool sums_valid = false;   // sums holds the conservation sums of the current state
+  // launch shape of the step kernel (map_autotune / map_set_launch): CTAs (0 = one per
+  // block) and warp-schedule weights (0 = defaults)
+  int tune_grid = 0, tune_wp = 0, tune_wf = 0;
   long long launches = 0;
   std::string err;
   // graph cache, one per starting buffer parity q and fill kind (2q + 1: residual fill)
@@ -523,6 +526,8 @@ static int step_launches(map_pool* pool, const map_params* p, bool fused) {
   S.scheme = p->scheme;
   S.limiter = p->limiter;
   S.riemann = p->riemann;
+  S.w_pred = pool->tune_wp;
+  S.w_face = pool->tune_wf;
   S.err_word = pool->err_word;
   S.sums = fused ? pool->sums : nullptr;
   S.dyn_next = fused ? pool->dyn : nullptr;
@@ -543,13 +548,13 @@ static int step_launches(map_pool* pool, const map_params* p, bool fused) {
       for (int L = 0; L <= t.maxlev; ++L) {
         S.blocks = pool->dt.level_leaves + pool->dt.leaf_off[L];
         S.nblocks = pool->dt.leaf_off[L + 1] - pool->dt.leaf_off[L];
-        S.grid = 0;
+        S.grid = pool->tune_grid;
         CK(DISPATCH(pool, step, S));
       }
     } else {
       S.blocks = pool->dt.all_leaves;
       S.nblocks = t.nleaves;
-      S.grid = 0;
+      S.grid = pool->tune_grid;
       CK(DISPATCH(pool, step, S));
     }
     return MAP_OK;
@@ -887,6 +892,111 @@ int map_conservation(map_pool* pool, double* sums_out) {
   CK(cudaMemcpyAsync(sums_out, pool->sums, sizeof(double) * kNV * pool->nprob, cudaMemcpyDeviceToHost, pool->stream));
   CK(cudaStreamSynchronize(pool->stream));
   pool->sums_valid = true;
+  return MAP_OK;
+}
+
+int map_set_launch(map_pool* pool, int grid, int w_pred, int w_face) {
+  if (!pool) return MAP_EINVAL;
+  if (grid < 0 || w_pred < 0 || w_face < 0 || w_pred > 64 || w_face > 64)
+    return fail(pool, MAP_EINVAL, "grid, w_pred and w_face must be >= 0 (weights <= 64)");
+  pool->tune_grid = grid;
+  pool->tune_wp = w_pred;
+  pool->tune_wf = w_face;
+  drop_graphs(pool);
+  return MAP_OK;
+}
+
+// Times the step launches (scheme update with its fused reductions, WENO's mid-step fill,
+// reflux) from the current buffer under candidate launch shapes and keeps the fastest: first
+// the grid (one CTA per block, or k = 1, 2, 3, 4, 6, 8, 12, 16 times the SM count as a persistent
+// grid, below the block count) with the
+// default weights, then the warp-schedule weights with that grid.  The trials write only the
+// other buffers; ghosts are refilled and dt recomputed first, and the step constants and sums
+// are restored afterwards, so the state and what later calls see are unchanged.
+int map_autotune(map_pool* pool, const map_params* p, int reps, map_tune_result* out) {
+  if (!pool || !out) return MAP_EINVAL;
+  int rc = check_params(pool, p);
+  if (rc) return rc;
+  if (reps < 1) reps = 1;
+  const int np = pool->nprob;
+  std::vector<ProbDyn> dyn0(np);
+  std::vector<double> sums0((size_t)kNV * np);
+  CK(cudaMemcpyAsync(dyn0.data(), pool->dyn, sizeof(ProbDyn) * np, cudaMemcpyDeviceToHost, pool->stream));
+  CK(cudaMemcpyAsync(sums0.data(), pool->sums, sizeof(double) * kNV * np, cudaMemcpyDeviceToHost, pool->stream));
+  CK(cudaStreamSynchronize(pool->stream));
+  rc = fill_on(pool, pool->cur);
+  if (rc) return rc;
+  rc = cfl_device(pool, p);
+  if (rc) return rc;
+  const int cur0 = pool->cur;
+  const bool pushed0[3] = {pool->pushed[0], pool->pushed[1], pool->pushed[2]};
+  const int g0 = pool->tune_grid, wp0 = pool->tune_wp, wf0 = pool->tune_wf;
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  int trials = 0;
+  auto trial = [&](int grid, int wp, int wf, float* ms) -> int {
+    pool->tune_grid = grid;
+    pool->tune_wp = wp;
+    pool->tune_wf = wf;
+    for (int r = 0; r <= reps; ++r) {
+      if (r == 1) CK(cudaEventRecord(e0, pool->stream));
+      int rc2 = step_launches(pool, p, true);
+      pool->cur = cur0;
+      for (int q = 0; q < 3; ++q) pool->pushed[q] = pushed0[q];
+      if (rc2) return rc2;
+    }
+    CK(cudaEventRecord(e1, pool->stream));
+    CK(cudaEventSynchronize(e1));
+    CK(cudaEventElapsedTime(ms, e0, e1));
+    *ms /= (float)reps;
+    ++trials;
+    return MAP_OK;
+  };
+  int dev = 0, nsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  float best = 0.f, t = 0.f;
+  int bg = 0, bwp = 7, bwf = 4;
+  rc = trial(0, 7, 4, &best);
+  const float base = best;
+  const int K[] = {1, 2, 3, 4, 6, 8, 12, 16};
+  for (int k : K) {
+    if (rc) break;
+    const int grid = k * nsm;
+    if (grid >= pool->tree.nleaves) break;
+    rc = trial(grid, 7, 4, &t);
+    if (rc == MAP_OK && t < best) { best = t; bg = grid; }
+  }
+  const int W[][2] = {{1, 1}, {2, 1}, {5, 4}, {6, 4}, {8, 4}, {9, 4}, {7, 3}, {7, 5}};
+  for (const auto& wgt : W) {
+    if (rc) break;
+    rc = trial(bg, wgt[0], wgt[1], &t);
+    if (rc == MAP_OK && t < best) { best = t; bwp = wgt[0]; bwf = wgt[1]; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  pool->cur = cur0;
+  for (int q = 0; q < 3; ++q) pool->pushed[q] = pushed0[q];
+  CK(cudaMemcpyAsync(pool->dyn, dyn0.data(), sizeof(ProbDyn) * np, cudaMemcpyHostToDevice, pool->stream));
+  CK(cudaMemcpyAsync(pool->sums, sums0.data(), sizeof(double) * kNV * np, cudaMemcpyHostToDevice, pool->stream));
+  CK(cudaStreamSynchronize(pool->stream));
+  if (rc) {
+    pool->tune_grid = g0;
+    pool->tune_wp = wp0;
+    pool->tune_wf = wf0;
+    return rc;
+  }
+  pool->tune_grid = bg;
+  pool->tune_wp = bwp;
+  pool->tune_wf = bwf;
+  drop_graphs(pool);
+  out->grid = bg;
+  out->w_pred = bwp;
+  out->w_face = bwf;
+  out->ms_default = base;
+  out->ms_best = best;
+  out->trials = trials;
   return MAP_OK;
 }
 

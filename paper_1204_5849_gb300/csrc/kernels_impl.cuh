@@ -37,6 +37,8 @@ cudaError_t launch_step_one(const StepLaunch& L, cudaStream_t s) {
   A.pushes = L.pushes;
   A.freg = (T*)L.freg;
   A.refl = L.freg ? L.refl : nullptr;
+  A.w_pred = L.w_pred > 0 ? L.w_pred : 7;
+  A.w_face = L.w_face > 0 ? L.w_face : 4;
   const int grid = L.grid > 0 ? (L.grid < L.nblocks ? L.grid : L.nblocks) : L.nblocks;
   if (grid <= 0) return cudaSuccess;
   kern<<<grid, NB * NB, smem, s>>>(A);

@@ -139,6 +139,7 @@ struct StepLaunch {
   ProbDyn* dyn_next;       // optional: max alpha of the output into dyn_next[p].alpha_bits
   int grid;                // CTAs (0 = one per block)
   int riemann;             // interface flux of LF and WENO: 0 f_m, 1 HLLC
+  int w_pred = 0, w_face = 0;  // warp-schedule weights (0: the defaults 7 and 4)
   const PushEntry* pushes; // optional: write boundary layers into same-level neighbours' ghosts
   void* freg;              // optional: face registers (reflux); with refl
   const RefluxLeaf* refl;  // per block slot and coarse-side mask

@@ -48,6 +48,7 @@ struct StepArgsT {
   const PushEntry* pushes;
   T* freg;
   const RefluxLeaf* refl;
+  int w_pred, w_face;     // warp-schedule cost of a predictor unit and of a face unit
 };
 
 template <int NDIM, int NB>
@@ -404,9 +405,10 @@ step_kernel(StepArgsT<T> A) {
   const int rown = (ty + 1) * RW + (tx + 1);            // own column, ring layout
 
   // Warp schedule of the per-plane work list: warp-sized units of predictor cells (NPU),
-  // x faces and y faces (NXU each), given greedily to the least-loaded warp with a
-  // predictor unit weighted 7 and a face unit 4 (their relative cost), the same on every
-  // block.  sched[w][15] holds the number of units of warp w.
+  // x faces and y faces (NXU each), given greedily to the least-loaded warp that has room,
+  // a predictor unit weighing w_pred and a face unit w_face (their relative cost; 7 and 4
+  // unless tuned), the same on every block.  sched[w][15] holds the number of units of
+  // warp w (NU <= 15 NW, so some warp always has room).
   constexpr int NW = NT / 32;
   constexpr int NPU = (HAS_T || true) ? Pad32<RING>::value / 32 : 0;
   constexpr int NXU = Pad32<NFACE>::value / 32;
@@ -418,12 +420,13 @@ step_kernel(StepArgsT<T> A) {
     fence_mbar_init();
     int load[NW], cnt[NW];
     for (int q = 0; q < NW; ++q) { load[q] = 0; cnt[q] = 0; }
+    static_assert(NU <= 15 * NW, "work units exceed the warp schedule");
     for (int u = 0; u < NU; ++u) {
-      int best = 0;
-      for (int q = 1; q < NW; ++q)
-        if (load[q] < load[best]) best = q;
-      if (cnt[best] < 15) sched[best][cnt[best]++] = u;
-      load[best] += u < NPU ? 7 : 4;
+      int best = -1;
+      for (int q = 0; q < NW; ++q)
+        if (cnt[q] < 15 && (best < 0 || load[q] < load[best])) best = q;
+      sched[best][cnt[best]++] = u;
+      load[best] += u < NPU ? A.w_pred : A.w_face;
     }
     for (int q = 0; q < NW; ++q) sched[q][15] = cnt[q];
   }

@@ -442,6 +442,50 @@ def test_conduction_needs_kappa0(gpulib):
     assert ei.value.code == -1
 
 
+# --- launch-shape autotuner -----------------------------------------------------------------
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("shape", [(0, 1, 1), (7, 9, 4), (64, 2, 1), (300, 7, 5)])
+def test_every_launch_shape_gives_the_same_state(gpulib, prec, shape):
+    mesh = w.uniform_mesh(3, 8, (8, 8, 4))
+    U0 = w.evaluate_on_mesh(mesh, _smooth_3d)
+    p = P(scheme="lf", limiter="vanleer")
+    a = pool_for(mesh, prec, U0)
+    b = pool_for(mesh, prec, U0)
+    a.set_launch(*shape)
+    a.advance(p, 3)
+    b.advance(p, 3)
+    np.testing.assert_array_equal(a.read_leaves(), b.read_leaves())
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_autotune_keeps_the_state_and_the_results(gpulib, prec):
+    mesh = _REFLUX_MESHES["2d_nb8_periodic"]()
+    U0 = _mixed_state(mesh)
+    p = P(scheme="weno")
+    a = pool_for(mesh, prec, U0)
+    b = pool_for(mesh, prec, U0)
+    before = a.read_leaves()
+    r = a.autotune(p, reps=1)
+    assert r["trials"] >= 9 and r["ms_best"] <= r["ms_default"] + 1e-9
+    np.testing.assert_array_equal(a.read_leaves(), before)
+    a.advance(p, 3)
+    b.advance(p, 3)
+    np.testing.assert_array_equal(a.read_leaves(), b.read_leaves())
+    if prec == 0:
+        orc = Oracle(mesh, U0)
+        orc.advance(p, 3)
+        assert rel_max(a.read_leaves(), orc.get_state()).max() <= 1e-12
+
+
+def test_choose_block_size(gpulib):
+    from paper_1204_5849_gb300 import choose_block_size
+    best, rep = choose_block_size(lambda nb: w.uniform_mesh(3, nb, (64 // nb,) * 3),
+                                  lambda m: w.evaluate_on_mesh(m, _smooth_3d), P(scheme="lf"), steps=2)
+    assert best in (8, 16) and set(rep) == {8, 16}
+    assert all(v["ms_per_step"] > 0 for v in rep.values())
+
+
 # --- several independent problems of uneven sizes -----------------------------------------
 
 def test_fp64_ensemble(gpulib):
