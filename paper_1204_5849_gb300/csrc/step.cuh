@@ -414,20 +414,30 @@ step_kernel(StepArgsT<T> A) {
   constexpr int NXU = Pad32<NFACE>::value / 32;
   constexpr int NU = NPU + 2 * NXU;
   __shared__ int sched[NW][16];
+  __shared__ RefluxLeaf srl;               // the block's face-register slot and coarse-side mask
   if (tid == 0) {
     for (int q = 0; q < UPL; ++q) mbar_init(&bars[q], 1);
     *status = 0;
     fence_mbar_init();
-    int load[NW], cnt[NW];
-    for (int q = 0; q < NW; ++q) { load[q] = 0; cnt[q] = 0; }
     static_assert(NU <= 15 * NW, "work units exceed the warp schedule");
+    // register arrays with compile-time indices only (a runtime index would put them in
+    // local memory); ties go to the lowest warp
+    int load[NW], cnt[NW];
+#pragma unroll
+    for (int q = 0; q < NW; ++q) { load[q] = 0; cnt[q] = 0; }
+    const int wp = A.w_pred, wf = A.w_face;
+#pragma unroll 1
     for (int u = 0; u < NU; ++u) {
-      int best = -1;
+      int best = 0, bl = 0x7fffffff;
+#pragma unroll
       for (int q = 0; q < NW; ++q)
-        if (cnt[q] < 15 && (best < 0 || load[q] < load[best])) best = q;
-      sched[best][cnt[best]++] = u;
-      load[best] += u < NPU ? A.w_pred : A.w_face;
+        if (cnt[q] < 15 && load[q] < bl) { best = q; bl = load[q]; }
+      const int wgt = u < NPU ? wp : wf;
+#pragma unroll
+      for (int q = 0; q < NW; ++q)
+        if (q == best) { sched[q][cnt[q]] = u; ++cnt[q]; load[q] += wgt; }
     }
+#pragma unroll
     for (int q = 0; q < NW; ++q) sched[q][15] = cnt[q];
   }
   __syncthreads();
@@ -460,7 +470,7 @@ step_kernel(StepArgsT<T> A) {
       kc[15] = (T)dy.ch;
     }
     if (A.pushes && tid < 27) spush[tid] = A.pushes[(size_t)blk * 27 + tid];   // read after the first barrier
-    const RefluxLeaf rl = A.refl ? A.refl[blk] : RefluxLeaf{-1, 0};
+    if (tid == 0) srl = A.refl ? A.refl[blk] : RefluxLeaf{-1, 0};   // read after the first barrier
     const T* ub = A.u_in + (size_t)blk * NV * S;
     T* ob = A.u_out + (size_t)blk * NV * S;
     const T* bb = (STAGE == 2) ? A.u_base + (size_t)blk * NV * S : nullptr;
@@ -645,6 +655,18 @@ step_kernel(StepArgsT<T> A) {
       }
     };
 
+    // face register (reflux, Sec. 4.2): the flux through a boundary face cell of this block
+    // (side 2d or 2d+1, face cell t0 + NB t1), written where the flux is computed; a WENO
+    // step holds half of each stage's flux
+    auto put_face = [&](int side, int t0, int t1, const T* F) {
+      T* r = A.freg + (size_t)srl.slot * (2 * NDIM * NV * NB * NB) + (size_t)side * NV * NB * NB + t1 * NB + t0;
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        T* rv = r + (size_t)v * NB * NB;
+        *rv = STAGE == 0 ? F[v] : (STAGE == 1 ? T(0.5) * F[v] : *rv + T(0.5) * F[v]);
+      }
+    };
+
     // x face f (fx = f % (NB+1), row = f / (NB+1)) or y face f (col = f % NB, fy = f / NB)
     // of plane z into the face buffer (x faces first, then y faces)
     T* sfx = sf;
@@ -656,6 +678,7 @@ step_kernel(StepArgsT<T> A) {
               (row + 1) * RW + fx, 1, F);
 #pragma unroll
       for (int v = 0; v < NV; ++v) sfx[v * NFACE + f] = F[v];
+      if ((fx == 0 || fx == NB) && srl.slot >= 0) put_face(fx ? 1 : 0, row, NDIM == 3 ? z - NG : 0, F);
     };
     auto do_yface = [&](int z, int f) {
       const int fy = f / NB, col = f % NB;
@@ -664,6 +687,7 @@ step_kernel(StepArgsT<T> A) {
               fy * RW + col + 1, RW, F);
 #pragma unroll
       for (int v = 0; v < NV; ++v) sfy[v * NFACE + f] = F[v];
+      if ((fy == 0 || fy == NB) && srl.slot >= 0) put_face(fy ? 3 : 2, col, NDIM == 3 ? z - NG : 0, F);
     };
 
     // z face of the own column between planes z and z+1; um1 = the column's state at z-1
@@ -776,6 +800,7 @@ step_kernel(StepArgsT<T> A) {
       T Fzhi[NV];
       if (NDIM == 3) {
         if (z >= 1) face_z(z, uprev, Fzhi);                     // face between planes z, z+1
+        if ((z == NG - 1 || z == NB + NG - 1) && srl.slot >= 0) put_face(z == NG - 1 ? 4 : 5, tx, ty, Fzhi);
         if (z < NG) {
 #pragma unroll
           for (int v = 0; v < NV; ++v) Fzlo[v] = Fzhi[v];
@@ -786,27 +811,6 @@ step_kernel(StepArgsT<T> A) {
       }
       const T* P0 = uslot(z);
       const T* T0 = HAS_T ? tslot(z) : nullptr;
-      if (rl.slot >= 0) {
-        // face register (reflux, Sec. 4.2): the flux through this block's boundary face
-        // cells; a WENO step holds half of each stage's flux
-        T* R = A.freg + (size_t)rl.slot * (2 * NDIM * NV * NB * NB);
-        const int tz = NDIM == 3 ? z - NG : 0;
-        auto put = [&](int side, int t0, int t1, const T* f, int stride) {
-          T* r = R + (size_t)side * NV * NB * NB + t1 * NB + t0;
-#pragma unroll
-          for (int v = 0; v < NV; ++v) {
-            const T x = f[v * stride];
-            T* rv = r + (size_t)v * NB * NB;
-            *rv = STAGE == 0 ? x : (STAGE == 1 ? T(0.5) * x : *rv + T(0.5) * x);
-          }
-        };
-        if (tx == 0) put(0, ty, tz, sfx + ty * (NB + 1), NFACE);
-        if (tx == NB - 1) put(1, ty, tz, sfx + ty * (NB + 1) + NB, NFACE);
-        if (ty == 0) put(2, tx, tz, sfy + tx, NFACE);
-        if (ty == NB - 1) put(3, tx, tz, sfy + NB * NB + tx, NFACE);
-        if (NDIM == 3 && z == NG) put(4, tx, ty, Fzlo, 1);
-        if (NDIM == 3 && z == NB + NG - 1) put(5, tx, ty, Fzhi, 1);
-      }
       T acc[NV];
       if (SCHEME == SCH_WENO) {
 #pragma unroll
@@ -914,7 +918,7 @@ step_kernel(StepArgsT<T> A) {
       }
       // cells next to a face where this block is the coarse side change again in the reflux
       // pass, which checks them and adds them to the fused diagnostics itself
-      const int cm = rl.coarse_mask;
+      const int cm = srl.coarse_mask;
       const bool refluxed = cm != 0 && (((cm & 1) && tx == 0) || ((cm & 2) && tx == NB - 1) ||
                                         ((cm & 4) && ty == 0) || ((cm & 8) && ty == NB - 1) ||
                                         (NDIM == 3 && (((cm & 16) && z == NG) || ((cm & 32) && z == NB + NG - 1))));
