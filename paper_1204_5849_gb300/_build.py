@@ -27,6 +27,10 @@ UNITS = {
     "kernels_f32.cu": ["-ftz=true", "-prec-div=false", "-prec-sqrt=false"],
     "kernels_f64_hllc.cu": ["-fmad=false"],
     "kernels_f32_hllc.cu": ["-ftz=true", "-prec-div=false", "-prec-sqrt=false"],
+    "kernels_f64_rfx.cu": ["-fmad=false"],
+    "kernels_f32_rfx.cu": ["-ftz=true", "-prec-div=false", "-prec-sqrt=false"],
+    "kernels_f64_hllc_rfx.cu": ["-fmad=false"],
+    "kernels_f32_hllc_rfx.cu": ["-ftz=true", "-prec-div=false", "-prec-sqrt=false"],
     "common.cu": ["-fmad=false"],
     "noalloc.cu": ["-fmad=false"],
 }

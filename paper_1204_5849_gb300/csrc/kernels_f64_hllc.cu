@@ -1,4 +1,4 @@
 // FP64 step kernels with the HLLC interface flux (LF and WENO), compiled apart from the
-// other FP64 kernels so the two translation units build in parallel.
+// other FP64 kernels so the translation units build in parallel.
 #include "kernels_impl.cuh"
-MAPGB_DEFINE_HLLC_LAUNCHER(double, f64)
+MAPGB_DEFINE_STEP_VARIANT(double, launch_step_hllc_f64, FLX_HLLC, false)

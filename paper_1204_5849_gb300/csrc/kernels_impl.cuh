@@ -6,11 +6,11 @@
 
 namespace mapgb {
 
-template <typename T, int NDIM, int NB, int SCHEME, int LIM, int STAGE, int FLX>
+template <typename T, int NDIM, int NB, int SCHEME, int LIM, int STAGE, int FLX, bool RFX>
 cudaError_t launch_step_one(const StepLaunch& L, cudaStream_t s) {
   const bool res = L.eta > 0.0;
   const size_t smem = step_smem_bytes<T, NDIM, NB, SCHEME>(res);
-  auto kern = step_kernel<T, NDIM, NB, SCHEME, LIM, STAGE, FLX>;
+  auto kern = step_kernel<T, NDIM, NB, SCHEME, LIM, STAGE, FLX, RFX>;
   static bool attr_done[2] = {false, false};
   if (!attr_done[res]) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -35,33 +35,33 @@ cudaError_t launch_step_one(const StepLaunch& L, cudaStream_t s) {
   A.sums = L.sums;
   A.dyn_next = L.dyn_next;
   A.pushes = L.pushes;
-  A.freg = (T*)L.freg;
-  A.refl = L.freg ? L.refl : nullptr;
-  A.w_pred = L.w_pred > 0 ? L.w_pred : 7;
-  A.w_face = L.w_face > 0 ? L.w_face : 4;
+  A.freg = RFX ? (T*)L.freg : nullptr;
+  A.refl = RFX ? L.refl : nullptr;
+  build_schedule<NDIM, NB>(L.w_pred > 0 ? L.w_pred : 7, L.w_face > 0 ? L.w_face : 4, A.sched);
   const int grid = L.grid > 0 ? (L.grid < L.nblocks ? L.grid : L.nblocks) : L.nblocks;
   if (grid <= 0) return cudaSuccess;
   kern<<<grid, NB * NB, smem, s>>>(A);
   return cudaGetLastError();
 }
 
-// FLX = FLX_HLLC is instantiated in its own translation units (kernels_*_hllc.cu) and
-// covers LF and WENO only (MMC has no interface Riemann problem).
-template <typename T, int NDIM, int NB, int FLX>
+// Each (FLX, RFX) pair is instantiated in its own translation unit (kernels_<prec>.cu,
+// _hllc.cu, _rfx.cu, _hllc_rfx.cu).  FLX = FLX_HLLC covers LF and WENO only (MMC has no
+// interface Riemann problem).
+template <typename T, int NDIM, int NB, int FLX, bool RFX>
 cudaError_t launch_step_geo(const StepLaunch& L, cudaStream_t s) {
   const int lim = L.limiter ? 1 : 0;
   if (L.scheme == SCH_MMC) {
     if constexpr (FLX == FLX_LF)
-      return lim ? launch_step_one<T, NDIM, NB, SCH_MMC, 1, 0, 0>(L, s)
-                 : launch_step_one<T, NDIM, NB, SCH_MMC, 0, 0, 0>(L, s);
+      return lim ? launch_step_one<T, NDIM, NB, SCH_MMC, 1, 0, 0, RFX>(L, s)
+                 : launch_step_one<T, NDIM, NB, SCH_MMC, 0, 0, 0, RFX>(L, s);
     else
       return cudaErrorInvalidValue;
   }
   if (L.scheme == SCH_LF)
-    return lim ? launch_step_one<T, NDIM, NB, SCH_LF, 1, 0, FLX>(L, s)
-               : launch_step_one<T, NDIM, NB, SCH_LF, 0, 0, FLX>(L, s);
-  if (L.stage == 1) return launch_step_one<T, NDIM, NB, SCH_WENO, 0, 1, FLX>(L, s);
-  return launch_step_one<T, NDIM, NB, SCH_WENO, 0, 2, FLX>(L, s);
+    return lim ? launch_step_one<T, NDIM, NB, SCH_LF, 1, 0, FLX, RFX>(L, s)
+               : launch_step_one<T, NDIM, NB, SCH_LF, 0, 0, FLX, RFX>(L, s);
+  if (L.stage == 1) return launch_step_one<T, NDIM, NB, SCH_WENO, 0, 1, FLX, RFX>(L, s);
+  return launch_step_one<T, NDIM, NB, SCH_WENO, 0, 2, FLX, RFX>(L, s);
 }
 
 #define MAPGB_GEO_DISPATCH(KC, CALL)                              \
@@ -75,11 +75,11 @@ cudaError_t launch_step_geo(const StepLaunch& L, cudaStream_t s) {
 
 inline int grid_for(int n) { return n < 1 ? 0 : n; }
 
-template <typename T, int FLX>
+template <typename T, int FLX, bool RFX>
 cudaError_t launch_step_T(const KernelConfig& kc, const StepLaunch& L, cudaStream_t s, long long* cnt) {
   if (L.nblocks <= 0) return cudaSuccess;
   if (cnt) ++*cnt;
-#define CALL_STEP(ND, NBV) return launch_step_geo<T, ND, NBV, FLX>(L, s)
+#define CALL_STEP(ND, NBV) return launch_step_geo<T, ND, NBV, FLX, RFX>(L, s)
   MAPGB_GEO_DISPATCH(kc, CALL_STEP);
 #undef CALL_STEP
 }
@@ -229,7 +229,9 @@ cudaError_t launch_cfl_partial_T(const KernelConfig& kc, const void* u, int nblo
 #define MAPGB_DEFINE_LAUNCHERS(T, SUFFIX)                                                          \
   namespace mapgb {                                                                                \
   cudaError_t launch_step_##SUFFIX(const KernelConfig& k, const StepLaunch& l, cudaStream_t s, long long* c) { \
-    return l.riemann ? launch_step_hllc_##SUFFIX(k, l, s, c) : launch_step_T<T, FLX_LF>(k, l, s, c); } \
+    const bool rfx = l.freg != nullptr;                                                          \
+    if (l.riemann) return rfx ? launch_step_hllc_rfx_##SUFFIX(k, l, s, c) : launch_step_hllc_##SUFFIX(k, l, s, c); \
+    return rfx ? launch_step_rfx_##SUFFIX(k, l, s, c) : launch_step_T<T, FLX_LF, false>(k, l, s, c); } \
   cudaError_t launch_fill_##SUFFIX(const KernelConfig& k, const FillLaunch& l, cudaStream_t s, long long* c) { return launch_fill_T<T>(k, l, s, c); } \
   cudaError_t launch_restrict_##SUFFIX(const KernelConfig& k, const RestrictLaunch& l, cudaStream_t s, long long* c) { return launch_restrict_T<T>(k, l, s, c); } \
   cudaError_t launch_cfl_##SUFFIX(const KernelConfig& k, const CflLaunch& l, cudaStream_t s, long long* c) { return launch_cfl_T<T>(k, l, s, c); } \
@@ -243,8 +245,9 @@ cudaError_t launch_cfl_partial_T(const KernelConfig& kc, const void* u, int nblo
   cudaError_t launch_cfl_partial_##SUFFIX(const KernelConfig& k, const void* u, int n, double g, double* part, cudaStream_t s) { return launch_cfl_partial_T<T>(k, u, n, g, part, s); } \
   }
 
-#define MAPGB_DEFINE_HLLC_LAUNCHER(T, SUFFIX)                                                      \
+// The step kernels of one (flux, reflux) variant, for their own translation unit.
+#define MAPGB_DEFINE_STEP_VARIANT(T, NAME, FLXV, RFXV)                                             \
   namespace mapgb {                                                                                \
-  cudaError_t launch_step_hllc_##SUFFIX(const KernelConfig& k, const StepLaunch& l, cudaStream_t s, long long* c) { \
-    return launch_step_T<T, FLX_HLLC>(k, l, s, c); }                                               \
+  cudaError_t NAME(const KernelConfig& k, const StepLaunch& l, cudaStream_t s, long long* c) {     \
+    return launch_step_T<T, FLXV, RFXV>(k, l, s, c); }                                             \
   }

@@ -270,8 +270,13 @@ struct KernelConfig {
 
 MAPGB_DECLARE_LAUNCHERS(f64)
 MAPGB_DECLARE_LAUNCHERS(f32)
+// step-kernel variants in their own translation units: HLLC flux, reflux bookkeeping, both
 cudaError_t launch_step_hllc_f64(const KernelConfig&, const StepLaunch&, cudaStream_t, long long*);
 cudaError_t launch_step_hllc_f32(const KernelConfig&, const StepLaunch&, cudaStream_t, long long*);
+cudaError_t launch_step_rfx_f64(const KernelConfig&, const StepLaunch&, cudaStream_t, long long*);
+cudaError_t launch_step_rfx_f32(const KernelConfig&, const StepLaunch&, cudaStream_t, long long*);
+cudaError_t launch_step_hllc_rfx_f64(const KernelConfig&, const StepLaunch&, cudaStream_t, long long*);
+cudaError_t launch_step_hllc_rfx_f32(const KernelConfig&, const StepLaunch&, cudaStream_t, long long*);
 
 cudaError_t launch_finalize(const FinalizeLaunch&, cudaStream_t, long long*);
 cudaError_t launch_zero_alpha(ProbDyn* dyn, int nprob, cudaStream_t, long long*);

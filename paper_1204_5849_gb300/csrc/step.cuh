@@ -48,7 +48,7 @@ struct StepArgsT {
   const PushEntry* pushes;
   T* freg;
   const RefluxLeaf* refl;
-  int w_pred, w_face;     // warp-schedule cost of a predictor unit and of a face unit
+  unsigned char sched[8][16];   // warp schedule of the per-plane work list (build_schedule)
 };
 
 template <int NDIM, int NB>
@@ -370,6 +370,38 @@ __device__ __forceinline__ void resist_src_col(const T* jc, int cj, const T* jzm
 template <int N>
 struct Pad32 { static constexpr int value = (N + 31) / 32 * 32; };
 
+// The per-plane work list of the step kernel: warp-sized units of predictor ring cells (NPU),
+// then x faces and y faces (NXU each), over NW warps.
+template <int NDIM, int NB>
+struct WorkList {
+  using G = Geo<NDIM, NB>;
+  static constexpr int NW = G::NT / 32;
+  static constexpr int NPU = Pad32<G::RING>::value / 32;
+  static constexpr int NXU = Pad32<G::NFACE>::value / 32;
+  static constexpr int NU = NPU + 2 * NXU;
+  static_assert(NW <= 8 && NU <= 15 * NW, "work list exceeds the schedule table");
+};
+
+// Warp schedule, built on the host once per launch: each unit goes, in order, to the
+// least-loaded warp that has room (ties to the lowest warp), a predictor unit weighing w_pred
+// and a face unit w_face (their relative cost; 7 and 4 unless tuned).  s[w][15] holds the
+// number of units of warp w, s[w][0..] the units.
+template <int NDIM, int NB>
+inline void build_schedule(int w_pred, int w_face, unsigned char (&s)[8][16]) {
+  using W = WorkList<NDIM, NB>;
+  int load[8] = {0}, cnt[8] = {0};
+  for (int q = 0; q < 8; ++q)
+    for (int k = 0; k < 16; ++k) s[q][k] = 0;
+  for (int u = 0; u < W::NU; ++u) {
+    int best = -1;
+    for (int q = 0; q < W::NW; ++q)
+      if (cnt[q] < 15 && (best < 0 || load[q] < load[best])) best = q;
+    s[best][cnt[best]++] = (unsigned char)u;
+    load[best] += u < W::NPU ? w_pred : w_face;
+  }
+  for (int q = 0; q < W::NW; ++q) s[q][15] = (unsigned char)cnt[q];
+}
+
 // a + b as an unevaluated pair (hi, lo) (TwoSum, Knuth)
 template <typename T>
 __device__ __forceinline__ void two_sum_acc(T& hi, T& lo, T h2, T l2) {
@@ -380,7 +412,10 @@ __device__ __forceinline__ void two_sum_acc(T& hi, T& lo, T h2, T l2) {
   hi = s;
 }
 
-template <typename T, int NDIM, int NB, int SCHEME, int LIM, int STAGE, int FLX>
+// RFX: the mesh has coarse/fine faces with reflux on -- the kernel then records its boundary
+// face fluxes and leaves the cells the reflux pass corrects out of the fused reductions.
+// Without it none of that code exists in the kernel.
+template <typename T, int NDIM, int NB, int SCHEME, int LIM, int STAGE, int FLX, bool RFX>
 __global__ void __launch_bounds__(NB * NB, sizeof(T) == 4 ? (NB == 16 ? 2 : 8) : 1)
 step_kernel(StepArgsT<T> A) {
   using G = Geo<NDIM, NB>;
@@ -404,41 +439,21 @@ step_kernel(StepArgsT<T> A) {
   const int cown = (ty + NG) * NP + (tx + NG);          // own column, full plane layout
   const int rown = (ty + 1) * RW + (tx + 1);            // own column, ring layout
 
-  // Warp schedule of the per-plane work list: warp-sized units of predictor cells (NPU),
-  // x faces and y faces (NXU each), given greedily to the least-loaded warp that has room,
-  // a predictor unit weighing w_pred and a face unit w_face (their relative cost; 7 and 4
-  // unless tuned), the same on every block.  sched[w][15] holds the number of units of
-  // warp w (NU <= 15 NW, so some warp always has room).
-  constexpr int NW = NT / 32;
-  constexpr int NPU = (HAS_T || true) ? Pad32<RING>::value / 32 : 0;
-  constexpr int NXU = Pad32<NFACE>::value / 32;
-  constexpr int NU = NPU + 2 * NXU;
+  // warp schedule of the per-plane work list (WorkList, build_schedule), the same on every
+  // block; thread 0 copies it from the arguments with constant indices
+  constexpr int NW = WorkList<NDIM, NB>::NW;
+  constexpr int NPU = WorkList<NDIM, NB>::NPU;
+  constexpr int NXU = WorkList<NDIM, NB>::NXU;
   __shared__ int sched[NW][16];
   __shared__ RefluxLeaf srl;               // the block's face-register slot and coarse-side mask
   if (tid == 0) {
     for (int q = 0; q < UPL; ++q) mbar_init(&bars[q], 1);
     *status = 0;
     fence_mbar_init();
-    static_assert(NU <= 15 * NW, "work units exceed the warp schedule");
-    // register arrays with compile-time indices only (a runtime index would put them in
-    // local memory); ties go to the lowest warp
-    int load[NW], cnt[NW];
 #pragma unroll
-    for (int q = 0; q < NW; ++q) { load[q] = 0; cnt[q] = 0; }
-    const int wp = A.w_pred, wf = A.w_face;
-#pragma unroll 1
-    for (int u = 0; u < NU; ++u) {
-      int best = 0, bl = 0x7fffffff;
+    for (int q = 0; q < NW; ++q)
 #pragma unroll
-      for (int q = 0; q < NW; ++q)
-        if (cnt[q] < 15 && load[q] < bl) { best = q; bl = load[q]; }
-      const int wgt = u < NPU ? wp : wf;
-#pragma unroll
-      for (int q = 0; q < NW; ++q)
-        if (q == best) { sched[q][cnt[q]] = u; ++cnt[q]; load[q] += wgt; }
-    }
-#pragma unroll
-    for (int q = 0; q < NW; ++q) sched[q][15] = cnt[q];
+      for (int k = 0; k < 16; ++k) sched[q][k] = A.sched[q][k];
   }
   __syncthreads();
   unsigned phase = 0;                                   // parity bit per u slot
@@ -470,7 +485,7 @@ step_kernel(StepArgsT<T> A) {
       kc[15] = (T)dy.ch;
     }
     if (A.pushes && tid < 27) spush[tid] = A.pushes[(size_t)blk * 27 + tid];   // read after the first barrier
-    if (tid == 0) srl = A.refl ? A.refl[blk] : RefluxLeaf{-1, 0};   // read after the first barrier
+    if (RFX && tid == 0) srl = A.refl[blk];             // read after the first barrier
     const T* ub = A.u_in + (size_t)blk * NV * S;
     T* ob = A.u_out + (size_t)blk * NV * S;
     const T* bb = (STAGE == 2) ? A.u_base + (size_t)blk * NV * S : nullptr;
@@ -678,7 +693,8 @@ step_kernel(StepArgsT<T> A) {
               (row + 1) * RW + fx, 1, F);
 #pragma unroll
       for (int v = 0; v < NV; ++v) sfx[v * NFACE + f] = F[v];
-      if ((fx == 0 || fx == NB) && srl.slot >= 0) put_face(fx ? 1 : 0, row, NDIM == 3 ? z - NG : 0, F);
+      if (RFX && SCHEME == SCH_LF && (fx == 0 || fx == NB) && srl.slot >= 0)
+        put_face(fx ? 1 : 0, row, NDIM == 3 ? z - NG : 0, F);
     };
     auto do_yface = [&](int z, int f) {
       const int fy = f / NB, col = f % NB;
@@ -687,7 +703,8 @@ step_kernel(StepArgsT<T> A) {
               fy * RW + col + 1, RW, F);
 #pragma unroll
       for (int v = 0; v < NV; ++v) sfy[v * NFACE + f] = F[v];
-      if ((fy == 0 || fy == NB) && srl.slot >= 0) put_face(fy ? 3 : 2, col, NDIM == 3 ? z - NG : 0, F);
+      if (RFX && SCHEME == SCH_LF && (fy == 0 || fy == NB) && srl.slot >= 0)
+        put_face(fy ? 3 : 2, col, NDIM == 3 ? z - NG : 0, F);
     };
 
     // z face of the own column between planes z and z+1; um1 = the column's state at z-1
@@ -800,7 +817,7 @@ step_kernel(StepArgsT<T> A) {
       T Fzhi[NV];
       if (NDIM == 3) {
         if (z >= 1) face_z(z, uprev, Fzhi);                     // face between planes z, z+1
-        if ((z == NG - 1 || z == NB + NG - 1) && srl.slot >= 0) put_face(z == NG - 1 ? 4 : 5, tx, ty, Fzhi);
+        if (RFX && (z == NG - 1 || z == NB + NG - 1) && srl.slot >= 0) put_face(z == NG - 1 ? 4 : 5, tx, ty, Fzhi);
         if (z < NG) {
 #pragma unroll
           for (int v = 0; v < NV; ++v) Fzlo[v] = Fzhi[v];
@@ -918,8 +935,8 @@ step_kernel(StepArgsT<T> A) {
       }
       // cells next to a face where this block is the coarse side change again in the reflux
       // pass, which checks them and adds them to the fused diagnostics itself
-      const int cm = srl.coarse_mask;
-      const bool refluxed = cm != 0 && (((cm & 1) && tx == 0) || ((cm & 2) && tx == NB - 1) ||
+      const int cm = RFX ? srl.coarse_mask : 0;
+      const bool refluxed = RFX && cm != 0 && (((cm & 1) && tx == 0) || ((cm & 2) && tx == NB - 1) ||
                                         ((cm & 4) && ty == 0) || ((cm & 8) && ty == NB - 1) ||
                                         (NDIM == 3 && (((cm & 16) && z == NG) || ((cm & 32) && z == NB + NG - 1))));
       if (STAGE != 1 && !refluxed) {
@@ -950,6 +967,17 @@ step_kernel(StepArgsT<T> A) {
         }
       }
       if (NDIM == 3) ldw<T, P2>(P0, cown, uprev);
+      if (RFX && SCHEME != SCH_LF && srl.slot >= 0 && tid < 4 * NB) {
+        // this plane's x and y boundary faces (still in the face buffer) into the face
+        // register (LF writes them where it computes them: either place suits one scheme's
+        // register allocation better)
+        const int side = tid / NB, t0 = tid % NB;
+        const T* src = side < 2 ? sfx + t0 * (NB + 1) + (side ? NB : 0) : sfy + (side == 3 ? NB * NB : 0) + t0;
+        T F[NV];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) F[v] = src[v * NFACE];
+        put_face(side, t0, NDIM == 3 ? z - NG : 0, F);
+      }
       __syncthreads();
     }
     if (!ok) break;
