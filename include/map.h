@@ -266,6 +266,18 @@ int map_set_launch(map_pool* pool, int grid, int w_pred, int w_face);
  * ran (1 without the subcycle).  Synchronises. */
 int map_last_conduction(map_pool* pool, double* dtc_out, int* nsub_out);
 
+/* Asynchronous form of map_write_leaves (no counterpart in the paper): the copy runs on the
+ * pool's own copy stream into one of two device staging buffers, so it overlaps steps still
+ * running on the pool stream; the pool stream waits for it before unpacking.  The host
+ * buffer (pinned, for a truly asynchronous copy) must stay unchanged until the pool stream
+ * has passed this call (map_check, or any synchronising call).  Allocates the two buffers
+ * (n_leaves * 9 * nb^ndim doubles each) on first use. */
+int map_write_leaves_async(map_pool* pool, const double* u);
+
+/* Asynchronous map_get_speeds: out[n_problems][5] is written when the pool stream reaches
+ * this point (pinned memory for a truly asynchronous copy); no synchronisation. */
+int map_get_speeds_async(map_pool* pool, double* out);
+
 /* Per problem: dt, c_h, c_p, psi damping factor, alpha_g of the last CFL reduction
  * (out[n_problems][5]).  Synchronises. */
 int map_get_speeds(map_pool* pool, double* out);

@@ -93,6 +93,8 @@ _SIGS = {
     "map_regrid": (C.c_int, [C.c_void_p, C.POINTER(map_block_desc), C.c_int]),
     "map_conservation": (C.c_int, [C.c_void_p, C.c_void_p]),
     "map_last_sums": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "map_write_leaves_async": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "map_get_speeds_async": (C.c_int, [C.c_void_p, C.c_void_p]),
     "map_autotune": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
     "map_set_launch": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int]),
     "map_last_conduction": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
@@ -265,6 +267,14 @@ class Pool:
 
     def write_leaves_ptr(self, host_ptr: int):
         self._ck(load().map_write_leaves(self.h, C.c_void_p(host_ptr)), "map_write_leaves")
+
+    def write_leaves_async_ptr(self, host_ptr: int):
+        """Asynchronous write from host memory (see map_write_leaves_async)."""
+        self._ck(load().map_write_leaves_async(self.h, C.c_void_p(host_ptr)), "map_write_leaves_async")
+
+    def speeds_async_ptr(self, host_ptr: int):
+        """Asynchronous read of [n_problems][5] speeds into host memory at host_ptr."""
+        self._ck(load().map_get_speeds_async(self.h, C.c_void_p(host_ptr)), "map_get_speeds_async")
 
     def read_leaves(self, out: Optional[np.ndarray] = None) -> np.ndarray:
         if out is None:

@@ -47,6 +47,13 @@ struct map_pool {
   std::vector<double> hsub_h;
   std::vector<int> nsub_h;
   double* staging = nullptr;
+  // asynchronous host writes: two staging buffers filled on their own copy stream, so the
+  // copy of the next state overlaps the steps running on the pool stream
+  double* astaging[2] = {nullptr, nullptr};
+  size_t astaging_elems = 0;
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t copied[2] = {nullptr, nullptr}, consumed[2] = {nullptr, nullptr};
+  int wslot = 0;
   size_t staging_elems = 0;
   int8_t* flags = nullptr;
   double* est = nullptr;
@@ -201,6 +208,15 @@ int map_destroy_pool(map_pool* pool) {
   cudaFree(pool->err_word);
   cudaFree(pool->sums);
   cudaFree(pool->staging);
+  if (pool->copy_stream) {
+    cudaStreamSynchronize(pool->copy_stream);
+    for (int k = 0; k < 2; ++k) {
+      cudaFree(pool->astaging[k]);
+      cudaEventDestroy(pool->copied[k]);
+      cudaEventDestroy(pool->consumed[k]);
+    }
+    cudaStreamDestroy(pool->copy_stream);
+  }
   cudaFree(pool->flags);
   cudaFree(pool->est);
   cudaFree(pool->tasks);
@@ -300,10 +316,10 @@ static size_t interior_elems(const map_pool* p) {
   return (size_t)p->nb * p->nb * (p->ndim == 3 ? p->nb : 1) * kNV;
 }
 
-static int pack(map_pool* pool, const int* dev_ids, int n, int to_pool) {
+static int pack(map_pool* pool, const int* dev_ids, int n, int to_pool, double* staging = nullptr) {
   PackLaunch L;
   L.u = pool->buf[pool->cur];
-  L.host_layout = pool->staging;
+  L.host_layout = staging ? staging : pool->staging;
   L.blocks = dev_ids;
   L.nblocks = n;
   L.to_pool = to_pool;
@@ -345,6 +361,46 @@ int map_write_leaves(map_pool* pool, const double* u) {
   pool->pushed[pool->cur] = false;
   pool->sums_valid = false;
   return pack(pool, pool->dt.leaf_ids, n, 1);
+}
+
+int map_write_leaves_async(map_pool* pool, const double* u) {
+  if (!pool || !u) return fail(pool, MAP_EINVAL, "null argument");
+  if (!pool->have_tree) return fail(pool, MAP_ESTATE, "no tree");
+  const int n = pool->tree.nleaves;
+  const size_t need = (size_t)n * interior_elems(pool);
+  if (!pool->copy_stream) {
+    CK(cudaStreamCreateWithFlags(&pool->copy_stream, cudaStreamNonBlocking));
+    for (int k = 0; k < 2; ++k) {
+      CK(cudaEventCreateWithFlags(&pool->copied[k], cudaEventDisableTiming));
+      CK(cudaEventCreateWithFlags(&pool->consumed[k], cudaEventDisableTiming));
+      CK(cudaEventRecord(pool->consumed[k], pool->stream));
+    }
+  }
+  if (need > pool->astaging_elems) {
+    CK(cudaStreamSynchronize(pool->copy_stream));
+    CK(cudaStreamSynchronize(pool->stream));
+    for (int k = 0; k < 2; ++k) {
+      cudaFree(pool->astaging[k]);
+      pool->astaging[k] = nullptr;
+      CK(cudaMalloc(&pool->astaging[k], need * sizeof(double)));
+    }
+    pool->astaging_elems = need;
+  }
+  const int k = pool->wslot;
+  pool->wslot ^= 1;
+  // the copy into buffer k waits for the pack that last read it; the pack waits for the copy
+  CK(cudaStreamWaitEvent(pool->copy_stream, pool->consumed[k], 0));
+  CK(cudaMemcpyAsync(pool->astaging[k], u, need * sizeof(double), cudaMemcpyHostToDevice, pool->copy_stream));
+  CK(cudaEventRecord(pool->copied[k], pool->copy_stream));
+  CK(cudaStreamWaitEvent(pool->stream, pool->copied[k], 0));
+  pool->have_dt = false;
+  pool->alpha_ready = false;
+  pool->pushed[pool->cur] = false;
+  pool->sums_valid = false;
+  int rc = pack(pool, pool->dt.leaf_ids, n, 1, pool->astaging[k]);
+  if (rc) return rc;
+  CK(cudaEventRecord(pool->consumed[k], pool->stream));
+  return MAP_OK;
 }
 
 int map_read_leaves(map_pool* pool, double* u) {
@@ -1017,6 +1073,16 @@ int map_last_sums(map_pool* pool, double* sums_out) {
   if (!pool->sums_valid) return fail(pool, MAP_ESTATE, "the state changed since the last map_advance step");
   CK(cudaMemcpyAsync(sums_out, pool->sums, sizeof(double) * kNV * pool->nprob, cudaMemcpyDeviceToHost, pool->stream));
   CK(cudaStreamSynchronize(pool->stream));
+  return MAP_OK;
+}
+
+int map_get_speeds_async(map_pool* pool, double* out) {
+  if (!pool || !out) return fail(pool, MAP_EINVAL, "null argument");
+  static_assert(offsetof(ProbDyn, dt) == 0 && offsetof(ProbDyn, ch) == 8 && offsetof(ProbDyn, cp) == 16 &&
+                offsetof(ProbDyn, damp) == 24 && offsetof(ProbDyn, alpha_g) == 32,
+                "dt, c_h, c_p, damping, alpha_g lead ProbDyn");
+  CK(cudaMemcpy2DAsync(out, 5 * sizeof(double), pool->dyn, sizeof(ProbDyn), 5 * sizeof(double), pool->nprob,
+                       cudaMemcpyDeviceToHost, pool->stream));
   return MAP_OK;
 }
 

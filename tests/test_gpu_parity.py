@@ -486,6 +486,35 @@ def test_choose_block_size(gpulib):
     assert all(v["ms_per_step"] > 0 for v in rep.values())
 
 
+# --- asynchronous host writes and reads -------------------------------------------------------
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_async_writes_and_reads_match_the_synchronous_calls(gpulib, prec):
+    import torch
+    mesh = w.uniform_mesh(3, 8, (2, 2, 2))
+    p = P(scheme="lf", limiter="vanleer")
+    states = [w.evaluate_on_mesh(mesh, _smooth_3d) * (1.0 + 0.01 * k) for k in range(5)]
+    pinned = []
+    for U in states:
+        t = torch.empty(U.shape, dtype=torch.float64, pin_memory=True)
+        t.numpy()[...] = U
+        pinned.append(t)
+    outs = torch.zeros((5, len(mesh.problems), 5), dtype=torch.float64, pin_memory=True)
+    a = pool_for(mesh, prec, states[0])
+    b = pool_for(mesh, prec, states[0])
+    finals = []
+    for k in range(5):                        # both staging buffers, each reused
+        a.write_leaves_async_ptr(pinned[k].data_ptr())
+        a.advance(p, 2)
+        a.speeds_async_ptr(outs[k].data_ptr())
+    assert a.check() == 0                     # synchronises
+    for k in range(5):
+        b.write_leaves(states[k])
+        b.advance(p, 2)
+        np.testing.assert_array_equal(outs[k].numpy(), b.speeds())
+    np.testing.assert_array_equal(a.read_leaves(), b.read_leaves())
+
+
 # --- several independent problems of uneven sizes -----------------------------------------
 
 def test_fp64_ensemble(gpulib):
