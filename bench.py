@@ -62,6 +62,28 @@ def error_table(A, B):
     return {"l1_rel": l1, "linf_rel": li}
 
 
+def max_over_ranks(ms: float, dist=None, device: str = "cuda") -> float:
+    """The job's time: the slowest rank's (every rank times the same number of steps).
+    dist is torch.distributed (initialised) or None for one process."""
+    if dist is None:
+        return float(ms)
+    import torch
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(world: int, cells: int, steps: int, ms: float) -> float:
+    """Whole-job cell-updates/s: every rank runs its own replica of the workload (weak
+    scaling, no collective on the data path), so the job updates world x cells per step."""
+    return world * cells * steps / (ms * 1e-3)
+
+
+def prints_line(rank: int) -> bool:
+    """Only rank 0 prints the JSON line."""
+    return rank == 0
+
+
 def peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -166,8 +188,8 @@ def cpu_baseline(params, seconds: float = 10.0):
 def run_reference(args):
     """Reference arm: the FP64 CPU oracle, timed on this host, bounded sample per step."""
     rank = int(os.environ.get("RANK", "0"))
-    if rank != 0:
-        return
+    if not prints_line(rank):
+        return                                        # the other ranks exit without work
     from workloads.problems import config_alfven3d
     import workloads as w
     from oracle import Oracle
@@ -364,11 +386,8 @@ def main():
     ms = evs[0].elapsed_time(evs[-1])
     step_ms = [evs[i].elapsed_time(evs[i + 1]) for i in range(args.steps)]
     launches = pool.kernel_launches() - l0
-    t = torch.tensor([ms], device="cuda")
-    if dist is not None:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
-    value = world * ncells * args.steps / (ms_max * 1e-3)
+    ms_max = max_over_ranks(ms, dist)
+    value = job_value(world, ncells, args.steps, ms_max)
     assert pool.check() == 0, "device error word set during the benchmark"
 
     # -------- step kernel alone (map_step, without the fused reductions) ----------------
@@ -397,7 +416,7 @@ def main():
 
     if args.quick:
         clocks.stop()
-        if rank == 0:
+        if prints_line(rank):
             print(json.dumps({"metric": METRIC, "value": value, "ms_per_step": ms_max / args.steps, "launch_shape": tune,
                               "kernel_ms": k_ms, "kernel_ms_alone": k_ms_alone, "achieved_gbs": achieved,
                               "achieved_tflops": tflops, "cells": ncells, "gpu_launches": launches}))
@@ -482,7 +501,7 @@ def main():
     wave_inf = {nm: float(np.abs(G32[:, v] - G64[:, v]).max() / amp) for v, nm in enumerate(NAMES)
                 if nm in ("my", "mz", "by", "bz")}
 
-    if rank != 0:
+    if not prints_line(rank):
         if dist is not None:
             dist.destroy_process_group()
         return
