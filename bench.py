@@ -448,6 +448,23 @@ def main():
     barrier()
     e2e_ms = max(e0.elapsed_time(e1), 1e3 * (time.perf_counter() - t0))
     assert np.all(res.numpy()[:, :, 0] > 0), "a step's result was not read back"
+    # the same with the FP32 host layout (an FP32 pool stores FP32: the device state is
+    # bitwise the same as with the FP64 copy), half the bytes copied
+    pinned32 = torch.empty(U0.shape, dtype=torch.float32, pin_memory=True)
+    pinned32.numpy()[...] = U0.astype(np.float32)
+    barrier()
+    f0 = torch.cuda.Event(enable_timing=True)
+    f1 = torch.cuda.Event(enable_timing=True)
+    t0 = time.perf_counter()
+    f0.record(stream)
+    for i in range(ne):
+        pool.write_leaves_async_f32_ptr(pinned32.data_ptr())
+        pool.advance(params, 1)
+        pool.speeds_async_ptr(res[i].data_ptr())
+    f1.record(stream)
+    barrier()
+    e2e32_ms = max(f0.elapsed_time(f1), 1e3 * (time.perf_counter() - t0))
+    e2e32 = world * ncells * ne / (e2e32_ms * 1e-3)
     b0 = torch.cuda.Event(enable_timing=True)
     b1 = torch.cuda.Event(enable_timing=True)
     nb_ = min(ne, 20)
@@ -529,7 +546,9 @@ def main():
         "e2e": {"value": e2e_val, "unit": METRIC, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "steps": ne, "copies": "FP64 host state in (pinned, async copy stream, double-buffered staging), "
                                        "the step's speeds out (pinned, async); one sync at the end",
-                "blocking_value": e2e_blocking},
+                "blocking_value": e2e_blocking,
+                "fp32_host": {"value": e2e32, "h2d_bytes_per_step": U0.nbytes // 2,
+                              "copies": "FP32 host state in (map_write_leaves_async_f32), speeds out"}},
         "gpu_launches": launches,
         "clocks": clk,
         "fp64_plain": {"value": f64_val, "unit": METRIC, "ms_per_step": f64_ms / n64, "steps": n64},

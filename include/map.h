@@ -274,6 +274,11 @@ int map_last_conduction(map_pool* pool, double* dtc_out, int* nsub_out);
  * (n_leaves * 9 * nb^ndim doubles each) on first use. */
 int map_write_leaves_async(map_pool* pool, const double* u);
 
+/* map_write_leaves_async with an FP32 host layout (same shape): half the bytes to copy.  An
+ * MAP_FP32_FIX64 pool ends up bitwise as with the FP64 call on the same values rounded to
+ * nearest; an FP64 pool takes the FP32 values exactly. */
+int map_write_leaves_async_f32(map_pool* pool, const float* u);
+
 /* Asynchronous map_get_speeds: out[n_problems][5] is written when the pool stream reaches
  * this point (pinned memory for a truly asynchronous copy); no synchronisation. */
 int map_get_speeds_async(map_pool* pool, double* out);

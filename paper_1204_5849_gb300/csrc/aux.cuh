@@ -378,11 +378,12 @@ __global__ void __launch_bounds__(256) pack_kernel(PackLaunch L) {
     const int blk = L.blocks[bi];
     T* ub = u + (size_t)blk * NV * S;
     double* hb = L.host_layout + (size_t)bi * NV * NI;
+    const float* hf = reinterpret_cast<const float*>(L.host_layout) + (size_t)bi * NV * NI;
     for (int q = threadIdx.x; q < NV * NI; q += blockDim.x) {
       const int v = q / NI, c = q % NI;
       const int i = c % NB, j = (c / NB) % NB, k = NDIM == 3 ? c / (NB * NB) : 0;
       const int cc = ((NDIM == 3 ? k + NG : 0) * NP + j + NG) * NP + i + NG;
-      if (L.to_pool) ub[(size_t)v * S + cc] = (T)hb[q];
+      if (L.to_pool) ub[(size_t)v * S + cc] = L.staging_f32 ? (T)hf[q] : (T)hb[q];
       else hb[q] = (double)ub[(size_t)v * S + cc];
     }
   }

@@ -316,10 +316,11 @@ static size_t interior_elems(const map_pool* p) {
   return (size_t)p->nb * p->nb * (p->ndim == 3 ? p->nb : 1) * kNV;
 }
 
-static int pack(map_pool* pool, const int* dev_ids, int n, int to_pool, double* staging = nullptr) {
+static int pack(map_pool* pool, const int* dev_ids, int n, int to_pool, double* staging = nullptr, int f32 = 0) {
   PackLaunch L;
   L.u = pool->buf[pool->cur];
   L.host_layout = staging ? staging : pool->staging;
+  L.staging_f32 = f32;
   L.blocks = dev_ids;
   L.nblocks = n;
   L.to_pool = to_pool;
@@ -363,7 +364,7 @@ int map_write_leaves(map_pool* pool, const double* u) {
   return pack(pool, pool->dt.leaf_ids, n, 1);
 }
 
-int map_write_leaves_async(map_pool* pool, const double* u) {
+static int write_leaves_async(map_pool* pool, const void* u, int f32) {
   if (!pool || !u) return fail(pool, MAP_EINVAL, "null argument");
   if (!pool->have_tree) return fail(pool, MAP_ESTATE, "no tree");
   const int n = pool->tree.nleaves;
@@ -390,18 +391,23 @@ int map_write_leaves_async(map_pool* pool, const double* u) {
   pool->wslot ^= 1;
   // the copy into buffer k waits for the pack that last read it; the pack waits for the copy
   CK(cudaStreamWaitEvent(pool->copy_stream, pool->consumed[k], 0));
-  CK(cudaMemcpyAsync(pool->astaging[k], u, need * sizeof(double), cudaMemcpyHostToDevice, pool->copy_stream));
+  CK(cudaMemcpyAsync(pool->astaging[k], u, need * (f32 ? sizeof(float) : sizeof(double)), cudaMemcpyHostToDevice,
+                     pool->copy_stream));
   CK(cudaEventRecord(pool->copied[k], pool->copy_stream));
   CK(cudaStreamWaitEvent(pool->stream, pool->copied[k], 0));
   pool->have_dt = false;
   pool->alpha_ready = false;
   pool->pushed[pool->cur] = false;
   pool->sums_valid = false;
-  int rc = pack(pool, pool->dt.leaf_ids, n, 1, pool->astaging[k]);
+  int rc = pack(pool, pool->dt.leaf_ids, n, 1, pool->astaging[k], f32);
   if (rc) return rc;
   CK(cudaEventRecord(pool->consumed[k], pool->stream));
   return MAP_OK;
 }
+
+int map_write_leaves_async(map_pool* pool, const double* u) { return write_leaves_async(pool, u, 0); }
+
+int map_write_leaves_async_f32(map_pool* pool, const float* u) { return write_leaves_async(pool, u, 1); }
 
 int map_read_leaves(map_pool* pool, double* u) {
   if (!pool || !u) return fail(pool, MAP_EINVAL, "null argument");

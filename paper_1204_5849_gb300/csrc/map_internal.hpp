@@ -239,6 +239,7 @@ struct PackLaunch {
   const int* blocks;       // pool ids in caller leaf order
   int nblocks;
   int to_pool;             // 1: staging -> pool, 0: pool -> staging
+  int staging_f32 = 0;     // 1: the staging holds floats (FP32 host layout), to_pool only
 };
 
 struct RegridLaunch {

@@ -515,6 +515,24 @@ def test_async_writes_and_reads_match_the_synchronous_calls(gpulib, prec):
     np.testing.assert_array_equal(a.read_leaves(), b.read_leaves())
 
 
+@pytest.mark.parametrize("prec", [0, 1])
+def test_async_fp32_write_equals_rounded_fp64_write(gpulib, prec):
+    import torch
+    mesh = w.uniform_mesh(2, 16, (2, 3))
+    U = w.evaluate_on_mesh(mesh, _smooth_2d)
+    U32 = U.astype(np.float32)
+    t = torch.empty(U32.shape, dtype=torch.float32, pin_memory=True)
+    t.numpy()[...] = U32
+    a = pool_for(mesh, prec, U)
+    b = pool_for(mesh, prec, U32.astype(np.float64))
+    a.write_leaves_async_f32_ptr(t.data_ptr())
+    assert a.check() == 0
+    np.testing.assert_array_equal(a.read_leaves(), b.read_leaves())
+    if prec == 1:                                           # FP32 pool: as the FP64 write of U
+        c = pool_for(mesh, prec, U)
+        np.testing.assert_array_equal(a.read_leaves(), c.read_leaves())
+
+
 # --- several independent problems of uneven sizes -----------------------------------------
 
 def test_fp64_ensemble(gpulib):
