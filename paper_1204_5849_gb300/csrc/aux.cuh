@@ -255,19 +255,24 @@ __global__ void __launch_bounds__(256) cfl_partial_kernel(const T* __restrict__ 
 // interior and the first ghost ring; block maximum -> flag.
 template <typename T, int NDIM, int NB>
 __global__ void __launch_bounds__(256) flags_kernel(FlagLaunch L) {
+  // the estimator runs in the pool's precision: FP64 pools bitwise as the FP64 formula, FP32
+  // pools in FP32 (decisions then differ from FP64 only within float rounding of a threshold)
+  using R = T;
   using G = Geo<NDIM, NB>;
   constexpr int NP = G::NP, P2 = G::P2, S = G::S;
   constexpr int NR = NDIM == 3 ? (NB + 2) * (NB + 2) * (NB + 2) : (NB + 2) * (NB + 2);
   __shared__ double red[32];
   const T* u = (const T*)L.u;
-  const double gm1 = L.gamma - 1.0;
-  auto pres = [&](const T* ub, int c) -> double {
-    double w[NV];
+  const R gm1 = (R)(L.gamma - 1.0);
+  const R bias = (R)L.r.bias, filt = (R)L.r.filter;
+  const R half_sqrt3 = (R)(1.7320508075688772 / 2.0);
+  auto pres = [&](const T* ub, int c) -> R {
+    R w[NV];
 #pragma unroll
-    for (int v = 0; v < NV; ++v) w[v] = (double)ub[(size_t)v * S + c];
-    double m2 = w[MX] * w[MX] + w[MY] * w[MY] + w[MZ] * w[MZ];
-    double b2 = w[BX] * w[BX] + w[BY] * w[BY] + w[BZ] * w[BZ];
-    return gm1 * (w[EN] - 0.5 * m2 / w[RHO] - 0.5 * b2);
+    for (int v = 0; v < NV; ++v) w[v] = (R)ub[(size_t)v * S + c];
+    R m2 = w[MX] * w[MX] + w[MY] * w[MY] + w[MZ] * w[MZ];
+    R b2 = w[BX] * w[BX] + w[BY] * w[BY] + w[BZ] * w[BZ];
+    return gm1 * (w[EN] - R(0.5) * m2 / w[RHO] - R(0.5) * b2);
   };
   const int offs[3] = {1, NP, P2};
   for (int bi = blockIdx.x; bi < L.nblocks; bi += gridDim.x) {
@@ -276,46 +281,47 @@ __global__ void __launch_bounds__(256) flags_kernel(FlagLaunch L) {
     const T* ub = u + (size_t)blk * NV * S;
     double mindx = gg.dx[0];
     for (int d = 1; d < NDIM; ++d) mindx = fmin(mindx, gg.dx[d]);
-    const double lvf = pow(L.r.ratio, L.r.xi * (double)(gg.level + 1 - 1));
-    double emax = 0.0;
+    const R lvf = (R)pow(L.r.ratio, L.r.xi * (double)(gg.level + 1 - 1));
+    const R two_dx[3] = {(R)(2.0 * gg.dx[0]), (R)(2.0 * gg.dx[1]), (R)(NDIM == 3 ? 2.0 * gg.dx[2] : 1.0)};
+    R emax = R(0);
     for (int q = threadIdx.x; q < NR; q += blockDim.x) {
       const int i = 1 + q % (NB + 2), j = 1 + (q / (NB + 2)) % (NB + 2);
       const int k = NDIM == 3 ? 1 + q / ((NB + 2) * (NB + 2)) : 0;
       const int c = (k * NP + j) * NP + i;
-      auto est = [&](auto field, double eps) -> double {
-        double s1 = 0.0, s2 = 0.0;
-        const double f0 = field(c);
+      auto est = [&](auto field, R eps) -> R {
+        R s1 = R(0), s2 = R(0);
+        const R f0 = field(c);
         for (int d = 0; d < NDIM; ++d) {
-          const double fp = field(c + offs[d]), fm = field(c - offs[d]);
-          const double d1 = fp - fm;
-          const double d2 = fp - 2.0 * f0 + fm;
+          const R fp = field(c + offs[d]), fm = field(c - offs[d]);
+          const R d1 = fp - fm;
+          const R d2 = fp - R(2) * f0 + fm;
           s1 += d1 * d1;
           s2 += d2 * d2;
         }
-        const double du = sqrt(3.0) / 2.0 * sqrt(s1);
-        const double d2u = sqrt(s2);
-        const double au = fabs(f0) + eps;
-        const double e = L.r.bias * du / au + (1.0 - L.r.bias) * d2u / (du + L.r.filter * au);
+        const R du = half_sqrt3 * sqrt(s1);
+        const R d2u = sqrt(s2);
+        const R au = fabs(f0) + eps;
+        const R e = bias * du / au + (R(1) - bias) * d2u / (du + filt * au);
         return e * lvf;
       };
-      if (L.r.var_mask & 1) emax = fmax(emax, est([&](int cc) { return (double)ub[RHO * (size_t)S + cc]; }, L.r.eps_rho));
-      if (L.r.var_mask & 2) emax = fmax(emax, est([&](int cc) { return pres(ub, cc); }, L.r.eps_p));
+      if (L.r.var_mask & 1) emax = fmax(emax, est([&](int cc) { return (R)ub[RHO * (size_t)S + cc]; }, (R)L.r.eps_rho));
+      if (L.r.var_mask & 2) emax = fmax(emax, est([&](int cc) { return pres(ub, cc); }, (R)L.r.eps_p));
       if (L.r.var_mask & 4) {
-        auto cd = [&](int comp, int d) -> double {
-          if (d >= NDIM) return 0.0;
-          return ((double)ub[(size_t)comp * S + c + offs[d]] - (double)ub[(size_t)comp * S + c - offs[d]]) /
-                 (2.0 * gg.dx[d]);
+        auto cd = [&](int comp, int d) -> R {
+          if (d >= NDIM) return R(0);
+          return ((R)ub[(size_t)comp * S + c + offs[d]] - (R)ub[(size_t)comp * S + c - offs[d]]) / two_dx[d];
         };
-        const double jx = cd(BZ, 1) - cd(BY, 2);
-        const double jy = cd(BX, 2) - cd(BZ, 0);
-        const double jz = cd(BY, 0) - cd(BX, 1);
-        const double bx = ub[(size_t)BX * S + c], by = ub[(size_t)BY * S + c], bz = ub[(size_t)BZ * S + c];
-        const double e = sqrt(jx * jx + jy * jy + jz * jz) * mindx / (sqrt(bx * bx + by * by + bz * bz) + L.r.eps_b);
+        const R jx = cd(BZ, 1) - cd(BY, 2);
+        const R jy = cd(BX, 2) - cd(BZ, 0);
+        const R jz = cd(BY, 0) - cd(BX, 1);
+        const R bx = ub[(size_t)BX * S + c], by = ub[(size_t)BY * S + c], bz = ub[(size_t)BZ * S + c];
+        const R e = sqrt(jx * jx + jy * jy + jz * jz) * (R)mindx / (sqrt(bx * bx + by * by + bz * bz) + (R)L.r.eps_b);
         emax = fmax(emax, e);
       }
     }
-    for (int o = 16; o > 0; o >>= 1) emax = fmax(emax, __shfl_xor_sync(0xffffffffu, emax, o));
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = emax;
+    double em = (double)emax;
+    for (int o = 16; o > 0; o >>= 1) em = fmax(em, __shfl_xor_sync(0xffffffffu, em, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = em;
     __syncthreads();
     if (threadIdx.x == 0) {
       double e = 0.0;
