@@ -106,6 +106,11 @@ struct HostTree {
   // lookup (problem, level, i, j, k) -> pool id
   int find(int p, int L, int i, int j, int k) const;
   std::vector<std::pair<unsigned long long, int>> keys;  // sorted packed keys -> id
+  // open-addressing hash index over the same keys (linear probing, power-of-two table)
+  std::vector<unsigned long long> hkeys;
+  std::vector<int> hvals;
+  unsigned long long hmask = 0;
+  void build_index();
 };
 
 // Build the tree; returns an empty string on success, else the reason.

@@ -55,11 +55,46 @@ std::string fmt(const char* what, int p, int L, const int* ijk) {
 
 }  // namespace
 
+namespace {
+constexpr unsigned long long kEmpty = ~0ull;   // no packed key reaches all ones (p <= 4000)
+
+// SplitMix64's output mix, as the hash of a packed key
+unsigned long long mix64(unsigned long long x) {
+  x ^= x >> 30;
+  x *= 0xbf58476d1ce4e5b9ull;
+  x ^= x >> 27;
+  x *= 0x94d049bb133111ebull;
+  x ^= x >> 31;
+  return x;
+}
+}  // namespace
+
+void HostTree::build_index() {
+  size_t cap = 16;
+  while (cap < 2 * keys.size()) cap <<= 1;
+  hkeys.assign(cap, kEmpty);
+  hvals.assign(cap, -1);
+  hmask = cap - 1;
+  for (const auto& kv : keys) {
+    unsigned long long h = mix64(kv.first) & hmask;
+    while (hkeys[h] != kEmpty) h = (h + 1) & hmask;
+    hkeys[h] = kv.first;
+    hvals[h] = kv.second;
+  }
+}
+
 int HostTree::find(int p, int L, int i, int j, int k) const {
   if (i < 0 || j < 0 || k < 0 || i >= (1 << 15) || j >= (1 << 15) || k >= (1 << 15)) return -1;
-  unsigned long long key = pack_key(p, L, i, j, k);
-  auto it = std::lower_bound(keys.begin(), keys.end(), std::make_pair(key, -1));
-  if (it != keys.end() && it->first == key) return it->second;
+  const unsigned long long key = pack_key(p, L, i, j, k);
+  if (hkeys.empty()) {
+    auto it = std::lower_bound(keys.begin(), keys.end(), std::make_pair(key, -1));
+    return (it != keys.end() && it->first == key) ? it->second : -1;
+  }
+  unsigned long long h = mix64(key) & hmask;
+  while (hkeys[h] != kEmpty) {
+    if (hkeys[h] == key) return hvals[h];
+    h = (h + 1) & hmask;
+  }
   return -1;
 }
 
@@ -138,18 +173,19 @@ std::string build_tree(int ndim, int nb, const std::vector<map_problem_desc>& pr
   std::vector<int> order(nodes.size());
   for (size_t q = 0; q < nodes.size(); ++q) order[q] = (int)q;
   const int ML = t.maxlev;
-  auto mkey = [&](const Node& a) {
-    int s = ML - a.L;
-    return morton(ndim, a.ijk[0] << s, a.ijk[1] << s, a.ijk[2] << s);
-  };
+  std::vector<unsigned long long> mk(nodes.size());      // Morton key at the finest level
+  for (size_t q = 0; q < nodes.size(); ++q) {
+    const Node& a = nodes[q];
+    const int s = ML - a.L;
+    mk[q] = morton(ndim, a.ijk[0] << s, a.ijk[1] << s, a.ijk[2] << s);
+  }
   std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
     const Node& a = nodes[x];
     const Node& b = nodes[y];
     if (a.leaf != b.leaf) return a.leaf;
     if (a.p != b.p) return a.p < b.p;
     if (!a.leaf && a.L != b.L) return a.L > b.L;
-    unsigned long long ma = mkey(a), mb = mkey(b);
-    if (ma != mb) return ma < mb;
+    if (mk[x] != mk[y]) return mk[x] < mk[y];
     return a.L < b.L;
   });
   const int NB = (int)nodes.size();
@@ -182,6 +218,7 @@ std::string build_tree(int ndim, int nb, const std::vector<map_problem_desc>& pr
     t.keys.push_back({pack_key(a.p, a.L, a.ijk[0], a.ijk[1], a.ijk[2]), id});
   }
   std::sort(t.keys.begin(), t.keys.end());
+  t.build_index();
   // parent/child links and completeness
   for (int id = 0; id < NB; ++id) {
     int L = t.blk_level[id];
