@@ -234,8 +234,8 @@ int map_get_leaves(map_pool* pool, map_block_desc* out, int cap, int* n_out);
  * volume.  Synchronises. */
 int map_conservation(map_pool* pool, double* sums_out);
 
-/* The FP64 conservation sums (same layout as map_conservation) that the last map_advance
- * step reduced inside its kernels for the state it produced, without another pass over
+/* (No counterpart in the paper.)  The FP64 conservation sums (same layout as
+ * map_conservation) that the last map_advance step reduced inside its kernels for the state it produced, without another pass over
  * the pool.  MAP_ESTATE when the state changed otherwise since (a write, map_step, a
  * regrid).  Synchronises. */
 int map_last_sums(map_pool* pool, double* sums_out);
@@ -258,10 +258,12 @@ typedef struct {
  * refilled first.  reps: timed repetitions per candidate (>= 1).  Synchronises. */
 int map_autotune(map_pool* pool, const map_params* p, int reps, map_tune_result* out);
 
-/* Sets the launch shape directly (grid 0 and weights 0 restore the defaults). */
+/* (No counterpart in the paper.)  Sets the launch shape directly (grid 0 and weights 0
+ * restore the defaults). */
 int map_set_launch(map_pool* pool, int grid, int w_pred, int w_face);
 
-/* Thermal conduction of the last step, per problem: the conduction time step dt_c of the
+/* (No counterpart in the paper.)  Thermal conduction of the last step, per problem: the
+ * conduction time step dt_c of the
  * reduction before it (+inf without conduction) and the number of conduction substeps it
  * ran (1 without the subcycle).  Synchronises. */
 int map_last_conduction(map_pool* pool, double* dtc_out, int* nsub_out);
@@ -274,12 +276,14 @@ int map_last_conduction(map_pool* pool, double* dtc_out, int* nsub_out);
  * (n_leaves * 9 * nb^ndim doubles each) on first use. */
 int map_write_leaves_async(map_pool* pool, const double* u);
 
-/* map_write_leaves_async with an FP32 host layout (same shape): half the bytes to copy.  An
+/* (No counterpart in the paper.)  map_write_leaves_async with an FP32 host layout (same
+ * shape): half the bytes to copy.  An
  * MAP_FP32_FIX64 pool ends up bitwise as with the FP64 call on the same values rounded to
  * nearest; an FP64 pool takes the FP32 values exactly. */
 int map_write_leaves_async_f32(map_pool* pool, const float* u);
 
-/* Asynchronous map_get_speeds: out[n_problems][5] is written when the pool stream reaches
+/* (No counterpart in the paper.)  Asynchronous map_get_speeds: out[n_problems][5] is
+ * written when the pool stream reaches
  * this point (pinned memory for a truly asynchronous copy); no synchronisation. */
 int map_get_speeds_async(map_pool* pool, double* out);
 
@@ -287,8 +291,8 @@ int map_get_speeds_async(map_pool* pool, double* out);
  * (out[n_problems][5]).  Synchronises. */
 int map_get_speeds(map_pool* pool, double* out);
 
-/* Number of kernels the library launched since the pool was created (graph replays
- * count each kernel in the graph). */
+/* (No counterpart in the paper.)  Number of kernels the library launched since the pool
+ * was created (graph replays count each kernel in the graph). */
 long long map_kernel_launches(const map_pool* pool);
 
 /* Last error text of the pool (or of the last failed create when pool is NULL). */
