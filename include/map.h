@@ -258,6 +258,14 @@ typedef struct {
  * refilled first.  reps: timed repetitions per candidate (>= 1).  Synchronises. */
 int map_autotune(map_pool* pool, const map_params* p, int reps, map_tune_result* out);
 
+/* (No counterpart in the paper.)  Test hook for the bounded-wait path: with on = 1 every
+ * wait of the step kernel for a plane copy gives up at once, as a wait that ran out of its
+ * bound (about a second) would: the kernel records the timeout, still waits (bounded) for
+ * the copies in flight so none lands after the block has left, and leaves; map_check then
+ * returns MAP_ETIMEOUT.  The step's output is not valid afterwards: write the state again.
+ * 0 restores normal waits. */
+int map_test_fail_waits(map_pool* pool, int on);
+
 /* (No counterpart in the paper.)  Sets the launch shape directly (grid 0 and weights 0
  * restore the defaults). */
 int map_set_launch(map_pool* pool, int grid, int w_pred, int w_face);

@@ -67,6 +67,7 @@ struct map_pool {
   // launch shape of the step kernel (map_autotune / map_set_launch): CTAs (0 = one per
   // block) and warp-schedule weights (0 = defaults)
   int tune_grid = 0, tune_wp = 0, tune_wf = 0;
+  int fail_waits = 0;        // test hook: the step kernel's plane waits give up at once
   long long launches = 0;
   std::string err;
   // graph cache, one per starting buffer parity q and fill kind (2q + 1: residual fill)
@@ -590,6 +591,7 @@ static int step_launches(map_pool* pool, const map_params* p, bool fused) {
   S.riemann = p->riemann;
   S.w_pred = pool->tune_wp;
   S.w_face = pool->tune_wf;
+  S.fail_waits = pool->fail_waits;
   S.err_word = pool->err_word;
   S.sums = fused ? pool->sums : nullptr;
   S.dyn_next = fused ? pool->dyn : nullptr;
@@ -954,6 +956,13 @@ int map_conservation(map_pool* pool, double* sums_out) {
   CK(cudaMemcpyAsync(sums_out, pool->sums, sizeof(double) * kNV * pool->nprob, cudaMemcpyDeviceToHost, pool->stream));
   CK(cudaStreamSynchronize(pool->stream));
   pool->sums_valid = true;
+  return MAP_OK;
+}
+
+int map_test_fail_waits(map_pool* pool, int on) {
+  if (!pool) return MAP_EINVAL;
+  pool->fail_waits = on ? 1 : 0;
+  drop_graphs(pool);
   return MAP_OK;
 }
 

@@ -38,6 +38,7 @@ cudaError_t launch_step_one(const StepLaunch& L, cudaStream_t s) {
   A.freg = RFX ? (T*)L.freg : nullptr;
   A.refl = RFX ? L.refl : nullptr;
   build_schedule<NDIM, NB>(L.w_pred > 0 ? L.w_pred : 7, L.w_face > 0 ? L.w_face : 4, A.sched);
+  A.fail_waits = L.fail_waits;
   const int grid = L.grid > 0 ? (L.grid < L.nblocks ? L.grid : L.nblocks) : L.nblocks;
   if (grid <= 0) return cudaSuccess;
   kern<<<grid, NB * NB, smem, s>>>(A);

@@ -145,6 +145,7 @@ struct StepLaunch {
   int grid;                // CTAs (0 = one per block)
   int riemann;             // interface flux of LF and WENO: 0 f_m, 1 HLLC
   int w_pred = 0, w_face = 0;  // warp-schedule weights (0: the defaults 7 and 4)
+  int fail_waits = 0;          // test hook (map_test_fail_waits)
   const PushEntry* pushes; // optional: write boundary layers into same-level neighbours' ghosts
   void* freg;              // optional: face registers (reflux); with refl
   const RefluxLeaf* refl;  // per block slot and coarse-side mask

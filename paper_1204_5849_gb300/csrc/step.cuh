@@ -49,6 +49,7 @@ struct StepArgsT {
   T* freg;
   const RefluxLeaf* refl;
   unsigned char sched[8][16];   // warp schedule of the per-plane work list (build_schedule)
+  int fail_waits;               // test hook: 1 = the plane waits give up at once
 };
 
 template <int NDIM, int NB>
@@ -511,7 +512,8 @@ step_kernel(StepArgsT<T> A) {
     auto wait_plane = [&](int z) -> bool {
       const int q = NDIM == 3 ? (z & 3) : 0;
       if (tid == 0) {
-        if (mbar_wait_bounded(&bars[q], (phase >> q) & 1u)) inflight &= ~(1u << q);
+        // (the test hook gives up without waiting; the copies are still drained below)
+        if (!A.fail_waits && mbar_wait_bounded(&bars[q], (phase >> q) & 1u)) inflight &= ~(1u << q);
         else *status = 1;
       }
       __syncthreads();

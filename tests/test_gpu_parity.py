@@ -633,6 +633,30 @@ def test_error_word_negative_pressure(gpulib):
     assert pool.check() == 0    # cleared
 
 
+@pytest.mark.parametrize("geom", [(2, 16, (2, 2)), (3, 16, (2, 1, 1)), (3, 8, (2, 2, 2))])
+def test_bounded_wait_timeout_is_reported_and_the_pool_recovers(gpulib, geom):
+    """A plane-copy wait that gives up makes the kernel drain its copies and leave; map_check
+    reports MAP_ETIMEOUT, and after the state is written again the pool steps normally."""
+    from paper_1204_5849_gb300 import MAP_FP32_FIX64
+    from paper_1204_5849_gb300.binding import STATUS
+    ndim, nb, nbase = geom
+    mesh = w.uniform_mesh(ndim, nb, nbase)
+    U0 = w.evaluate_on_mesh(mesh, _smooth_2d if ndim == 2 else _smooth_3d)
+    p = P(scheme="lf")
+    pool = pool_for(mesh, MAP_FP32_FIX64, U0)
+    pool.test_fail_waits(True)
+    pool.fill_ghosts(); pool.cfl_dt(p); pool.step(p)
+    code = pool.check()
+    assert STATUS.get(code) == "MAP_ETIMEOUT", code
+    pool.test_fail_waits(False)
+    pool.write_leaves(U0)
+    pool.advance(p, 2)
+    ref = pool_for(mesh, MAP_FP32_FIX64, U0)
+    ref.advance(p, 2)
+    np.testing.assert_array_equal(pool.read_leaves(), ref.read_leaves())
+    assert pool.check() == 0
+
+
 def test_bad_tree_rejected(gpulib):
     from paper_1204_5849_gb300 import MAP_FP64, MapError, Pool
     leaves = [(0, 0, 1, 0, 0), (0, 0, 0, 1, 0), (0, 0, 1, 1, 0)]
