@@ -546,6 +546,33 @@ def test_fp64_ensemble(gpulib):
     assert rel_max(pool.read_leaves(), orc.get_state()).max() <= 1e-12
 
 
+# --- full-size configurations against the oracle ----------------------------------------
+
+@pytest.mark.parametrize("name", ["rotor_amr", "harris_amr", "ensemble"])
+def test_full_size_config_against_oracle(gpulib, name):
+    """At the benchmark sizes (3028-leaf WENO rotor, 9472-leaf resistive Harris octree with
+    reflux, 96-problem ensemble): the plain FP64 form in lockstep with the oracle for two
+    steps (dt bitwise), and the batched FP32 form as bench.py times it (graph-replayed
+    map_advance) against the same oracle state."""
+    from workloads.problems import CONFIGS, initial_state
+    from paper_1204_5849_gb300 import MAP_FP32_FIX64, MAP_FP64
+    cfg = CONFIGS[name]()
+    mesh = cfg["mesh"]
+    U0 = initial_state(cfg)
+    p = dict(cfg["params"])
+    orc = Oracle(mesh, U0)
+    pool = pool_for(mesh, MAP_FP64, U0)
+    lockstep(pool, orc, p, 2)
+    R = orc.get_state()
+    assert rel_max(pool.read_leaves(), R).max() <= 1e-12
+    assert pool.check() == 0
+    pool.close()
+    b = pool_for(mesh, MAP_FP32_FIX64, U0)
+    b.advance(dict(p, fp64_fix_tau=1e-2), 2)
+    assert rel_l1(b.read_leaves(), R).max() <= 1e-5
+    assert b.check() == 0
+
+
 # --- diagnostics: conservation sums, speeds, flags, regrid, error word --------------------
 
 def test_conservation_and_speeds(gpulib):

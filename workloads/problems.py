@@ -346,12 +346,19 @@ def config_conduction(small: bool = False):
 
 
 def ensemble_initial(mesh: Mesh, seed0: int = 1204) -> np.ndarray:
-    """Per-problem seeded state: problem p uses seed0 + p."""
+    """Per-problem seeded state: problem p uses seed0 + p (all blocks of a problem are
+    evaluated in one call; the values do not depend on the batching)."""
     nz, ny, nx = mesh.block_shape()
     out = np.empty((mesh.nleaves, NVAR, nz, ny, nx), dtype=np.float64)
-    for b in range(mesh.nleaves):
-        X, Y, Z = cell_centres(mesh, b)
-        out[b] = ensemble_problem(X, Y, Z, seed=seed0 + int(mesh.leaves[b, 0]))
+    probs = mesh.leaves[:, 0].astype(np.int64)
+    for p in np.unique(probs):
+        idx = np.nonzero(probs == p)[0]
+        cc = [cell_centres(mesh, int(b)) for b in idx]
+        X = np.stack([c[0] for c in cc])
+        Y = np.stack([c[1] for c in cc])
+        Z = np.stack([c[2] for c in cc])
+        U = ensemble_problem(X, Y, Z, seed=seed0 + int(p))      # (9, nblocks, nz, ny, nx)
+        out[idx] = np.moveaxis(U, 0, 1)
     return out
 
 
