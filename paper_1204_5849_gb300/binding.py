@@ -44,6 +44,9 @@ class map_block_desc(C.Structure):
     _fields_ = [("problem", C.c_int), ("level", C.c_int), ("ijk", C.c_int * 3)]
 
 
+assert C.sizeof(map_block_desc) == 20
+
+
 class map_params(C.Structure):
     _fields_ = [("gamma", C.c_double), ("c_cfl", C.c_double), ("ch_mode", C.c_int),
                 ("ch", C.c_double), ("cp_mode", C.c_int), ("c_d", C.c_double), ("cp", C.c_double),
@@ -175,21 +178,15 @@ def make_refine(r: Dict) -> map_refine_params:
 
 
 def _leaves(mesh) -> "C.Array":
+    # map_block_desc is five packed int32 (problem, level, i, j, k): one memory copy
+    a = np.ascontiguousarray(np.asarray(mesh.leaves)[:, :5], dtype=np.int32)
     arr = (map_block_desc * mesh.nleaves)()
-    for q, (p, lv, i, j, k) in enumerate(mesh.leaves):
-        arr[q].problem = int(p)
-        arr[q].level = int(lv)
-        arr[q].ijk[0] = int(i)
-        arr[q].ijk[1] = int(j)
-        arr[q].ijk[2] = int(k)
+    C.memmove(arr, a.ctypes.data, a.nbytes)
     return arr
 
 
 def _leaves_to_array(arr, n: int) -> np.ndarray:
-    out = np.zeros((n, 5), dtype=np.int32)
-    for q in range(n):
-        out[q] = (arr[q].problem, arr[q].level, arr[q].ijk[0], arr[q].ijk[1], arr[q].ijk[2])
-    return out
+    return np.frombuffer(arr, dtype=np.int32, count=5 * n).reshape(n, 5).copy()
 
 
 class Pool:

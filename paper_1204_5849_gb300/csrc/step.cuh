@@ -416,8 +416,16 @@ __device__ __forceinline__ void two_sum_acc(T& hi, T& lo, T h2, T l2) {
 // RFX: the mesh has coarse/fine faces with reflux on -- the kernel then records its boundary
 // face fluxes and leaves the cells the reflux pass corrects out of the fused reductions.
 // Without it none of that code exists in the kernel.
+// Resident CTAs per SM the register budget is sized for: the 3D 8^3 window (about 41 KB of
+// shared memory) lets at most 5 CTAs reside, so asking for 8 would only cap the registers
+// at 128 and spill the column state.
+template <typename T, int NDIM, int NB>
+constexpr int step_min_ctas() {
+  return sizeof(T) != 4 ? 1 : NB == 16 ? 2 : NDIM == 3 ? 5 : 8;
+}
+
 template <typename T, int NDIM, int NB, int SCHEME, int LIM, int STAGE, int FLX, bool RFX>
-__global__ void __launch_bounds__(NB * NB, sizeof(T) == 4 ? (NB == 16 ? 2 : 8) : 1)
+__global__ void __launch_bounds__(NB * NB, step_min_ctas<T, NDIM, NB>())
 step_kernel(StepArgsT<T> A) {
   using G = Geo<NDIM, NB>;
   constexpr int NP = G::NP, P2 = G::P2, NZ = G::NZ, S = G::S, NT = G::NT;
