@@ -163,35 +163,39 @@ __global__ void __launch_bounds__(256) cfl_kernel(const T* __restrict__ u, const
   for (int bi = blockIdx.x; bi < n; bi += gridDim.x) {
     const int blk = blocks[bi];
     const T* ub = u + (size_t)blk * NV * S;
-    double am = 0.0, km = 0.0;
+    // maxima in T within each warp (a maximum is exact in any precision, and widening to
+    // FP64 is exact and monotone), then FP64 across warps
+    const bool cond = kappa0 > 0.0;
+    const T kap0 = (T)kappa0;
+    T am = T(0), km = T(0);
     for (int c = threadIdx.x; c < NI; c += blockDim.x) {
       const int i = c % NB, j = (c / NB) % NB, k = NDIM == 3 ? c / (NB * NB) : 0;
       const int cc = ((NDIM == 3 ? k + NG : 0) * NP + j + NG) * NP + i + NG;
       T w[NV];
       load_global<T>(ub, S, cc, w);
       const T p = pressure<T>(w, P);
-      double a = (double)alpha_p<T, 0>(w, p, P);
-      a = fmax(a, (double)alpha_p<T, 1>(w, p, P));
-      if (NDIM == 3) a = fmax(a, (double)alpha_p<T, 2>(w, p, P));
+      T a = alpha_p<T, 0>(w, p, P);
+      a = fmax(a, alpha_p<T, 1>(w, p, P));
+      if (NDIM == 3) a = fmax(a, alpha_p<T, 2>(w, p, P));
       if (a != a) am = a;            // NaN wins
       else if (!(am != am)) am = fmax(am, a);
-      if (kappa0 > 0.0) {
+      if (cond) {
         // kappa T / p read as kappa / rho, kappa = kappa0 T^(5/2), T = max(p, 0) / rho
         const T tt = (p < T(0) ? T(0) : p) / w[RHO];
-        const double kr = (double)((T)kappa0 * (tt * tt * sqrt(tt)) / w[RHO]);
+        const T kr = kap0 * (tt * tt * sqrt(tt)) / w[RHO];
         if (kr != kr) km = kr;
         else if (!(km != km)) km = fmax(km, kr);
       }
     }
     for (int o = 16; o > 0; o >>= 1) {
-      double t = __shfl_xor_sync(0xffffffffu, am, o);
+      const T t = __shfl_xor_sync(0xffffffffu, am, o);
       am = (t != t) ? t : fmax(am, t);
-      double t2 = __shfl_xor_sync(0xffffffffu, km, o);
+      const T t2 = __shfl_xor_sync(0xffffffffu, km, o);
       km = (t2 != t2) ? t2 : fmax(km, t2);
     }
     if ((threadIdx.x & 31) == 0) {
-      red[threadIdx.x >> 5] = am;
-      redk[threadIdx.x >> 5] = km;
+      red[threadIdx.x >> 5] = (double)am;
+      redk[threadIdx.x >> 5] = (double)km;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -223,21 +227,21 @@ __global__ void __launch_bounds__(256) cfl_partial_kernel(const T* __restrict__ 
   P.tau = T(0);
   for (int blk = blockIdx.x; blk < nblocks; blk += gridDim.x) {
     const T* ub = u + (size_t)blk * NV * S;
-    double am = 0.0;
+    T am = T(0);                     // in T within each warp, as in cfl_kernel
     for (int c = threadIdx.x; c < NI; c += blockDim.x) {
       const int i = c % NB, j = (c / NB) % NB, k = NDIM == 3 ? c / (NB * NB) : 0;
       const int cc = ((NDIM == 3 ? k + NG : 0) * NP + j + NG) * NP + i + NG;
       T w[NV];
       load_global<T>(ub, S, cc, w);
       const T p = pressure<T>(w, P);
-      double a = (double)alpha_p<T, 0>(w, p, P);
-      a = fmax(a, (double)alpha_p<T, 1>(w, p, P));
-      if (NDIM == 3) a = fmax(a, (double)alpha_p<T, 2>(w, p, P));
+      T a = alpha_p<T, 0>(w, p, P);
+      a = fmax(a, alpha_p<T, 1>(w, p, P));
+      if (NDIM == 3) a = fmax(a, alpha_p<T, 2>(w, p, P));
       if (a != a) am = a;
       else if (!(am != am)) am = fmax(am, a);
     }
     for (int o = 16; o > 0; o >>= 1) {
-      const double t = __shfl_xor_sync(0xffffffffu, am, o);
+      const T t = __shfl_xor_sync(0xffffffffu, am, o);
       am = (t != t) ? t : ((am != am) ? am : fmax(am, t));
     }
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = am;
@@ -281,7 +285,7 @@ __global__ void __launch_bounds__(256) flags_kernel(FlagLaunch L) {
     const T* ub = u + (size_t)blk * NV * S;
     double mindx = gg.dx[0];
     for (int d = 1; d < NDIM; ++d) mindx = fmin(mindx, gg.dx[d]);
-    const R lvf = (R)pow(L.r.ratio, L.r.xi * (double)(gg.level + 1 - 1));
+    const R lvf = (R)L.level_factor[gg.level < 16 ? gg.level : 15];
     const R two_dx[3] = {(R)(2.0 * gg.dx[0]), (R)(2.0 * gg.dx[1]), (R)(NDIM == 3 ? 2.0 * gg.dx[2] : 1.0)};
     R emax = R(0);
     for (int q = threadIdx.x; q < NR; q += blockDim.x) {

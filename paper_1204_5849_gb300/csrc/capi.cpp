@@ -855,6 +855,7 @@ int map_flag_refine(map_pool* pool, const map_params* p, const map_refine_params
   F.r = *r;
   F.flags = pool->flags;
   F.est = pool->est;
+  for (int L = 0; L < 16; ++L) F.level_factor[L] = pow(r->ratio, r->xi * (double)(L + 1 - 1));
   CK(DISPATCH(pool, flags, F));
   CK(cudaMemcpyAsync(flags_out, pool->flags, pool->tree.nleaves, cudaMemcpyDeviceToHost, pool->stream));
   if (est_out)

@@ -229,6 +229,7 @@ struct FlagLaunch {
   map_refine_params r;
   int8_t* flags;
   double* est;
+  double level_factor[16];   // R^(xi (L+1-1)) for levels L = 0..15, computed on the host
 };
 
 struct SumLaunch {
