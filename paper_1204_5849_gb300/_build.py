@@ -78,7 +78,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         jobs.append((obj, cmd))
     for src in CPP_UNITS:
         obj = os.path.join(BUILD, src.replace(".cpp", ".o"))
-        cmd = ["g++", "-O2", "-std=c++17", "-fPIC", "-I", INCLUDE, "-I", os.path.join(home, "include"),
+        cmd = ["g++", "-O2", "-std=c++17", "-fPIC", "-pthread", "-I", INCLUDE, "-I", os.path.join(home, "include"),
                "-c", os.path.join(CSRC, src), "-o", obj]
         jobs.append((obj, cmd))
 
@@ -94,7 +94,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     with cf.ThreadPoolExecutor(max_workers=max(2, min(8, os.cpu_count() or 2))) as ex:
         objs = list(ex.map(run, jobs))
     tmp = LIB + f".tmp{os.getpid()}"
-    link = [nvcc, *ARCH, "-shared", "-o", tmp, *objs]
+    link = [nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lpthread"]
     r = subprocess.run(link, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed: {' '.join(link)}\n{r.stdout}\n{r.stderr}")

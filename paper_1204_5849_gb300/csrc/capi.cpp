@@ -37,6 +37,7 @@ struct map_pool {
   bool ext = false;
   int cur = 0;
   HostTree tree;
+  HostTree spare;              // the next tree is built here; the two swap on install
   bool have_tree = false;
   DevTree dt;
   ProbDyn* dyn = nullptr;
@@ -295,7 +296,7 @@ static int install_tree(map_pool* pool, HostTree& t) {
     pool->flags_cap = t.nleaves;
   }
   CK(cudaStreamSynchronize(pool->stream));
-  pool->tree = std::move(t);
+  std::swap(pool->tree, t);    // t (the spare) keeps the old tree's storage for reuse
   pool->have_tree = true;
   pool->have_dt = false;
   pool->alpha_ready = false;
@@ -306,7 +307,7 @@ static int install_tree(map_pool* pool, HostTree& t) {
 
 int map_set_tree(map_pool* pool, const map_block_desc* leaves, int n) {
   if (!pool || !leaves || n <= 0) return fail(pool, MAP_EINVAL, "null or empty leaf list");
-  HostTree t;
+  HostTree& t = pool->spare;
   std::string why = build_tree(pool->ndim, pool->nb, pool->probs, leaves, n, t);
   if (!why.empty()) return fail(pool, MAP_EINVAL, why);
   if (t.nblocks > pool->max_blocks) return fail(pool, MAP_ENOMEM, "tree has more blocks than max_blocks");
@@ -867,7 +868,7 @@ int map_flag_refine(map_pool* pool, const map_params* p, const map_refine_params
 int map_regrid(map_pool* pool, const map_block_desc* leaves, int n) {
   if (!pool || !leaves || n <= 0) return fail(pool, MAP_EINVAL, "null or empty leaf list");
   if (!pool->have_tree) return fail(pool, MAP_ESTATE, "no tree");
-  HostTree t;
+  HostTree& t = pool->spare;
   std::string why = build_tree(pool->ndim, pool->nb, pool->probs, leaves, n, t);
   if (!why.empty()) return fail(pool, MAP_EINVAL, why);
   if (t.nblocks > pool->max_blocks) return fail(pool, MAP_ENOMEM, "tree has more blocks than max_blocks");

@@ -111,6 +111,8 @@ struct HostTree {
   std::vector<int> hvals;
   unsigned long long hmask = 0;
   void build_index();
+  // empty the tree but keep the vectors' storage for the next build_tree into it
+  void reset();
 };
 
 // Build the tree; returns an empty string on success, else the reason.

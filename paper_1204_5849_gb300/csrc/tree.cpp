@@ -7,8 +7,10 @@
 // finest level), then parents.  For each leaf the 3^ndim ghost regions are resolved once
 // into a source block and an affine index map, so the device fill is a pure gather.
 #include <algorithm>
+#include <climits>
 #include <cstdio>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "map_internal.hpp"
@@ -53,6 +55,49 @@ std::string fmt(const char* what, int p, int L, const int* ijk) {
   return buf;
 }
 
+// Runs body(id) for id in [0, n): on up to 16 host threads when n is large, each over a
+// contiguous range in increasing id.  body only reads the tree and writes slots of its own
+// id.  Returns the message of the lowest id whose body failed (what a serial loop returns
+// first), else an empty string.
+template <typename F>
+std::string for_each_leaf(int n, const F& body) {
+  auto serial = [&](int lo, int hi, int* at) -> std::string {
+    for (int id = lo; id < hi; ++id) {
+      std::string e = body(id);
+      if (!e.empty()) {
+        *at = id;
+        return e;
+      }
+    }
+    return std::string();
+  };
+  int nt = 1;
+  if (n >= 2048) {
+    const unsigned hw = std::thread::hardware_concurrency();
+    nt = std::min(std::min((int)(hw ? hw : 1u), 16), n / 512);
+  }
+  int at = INT_MAX;
+  if (nt <= 1) return serial(0, n, &at);
+  std::vector<std::string> err(nt);
+  std::vector<int> err_at(nt, INT_MAX);
+  std::vector<std::thread> th;
+  bool spawned = true;
+  try {
+    for (int k = 1; k < nt; ++k)
+      th.emplace_back([&, k] {
+        err[k] = serial((int)((long long)n * k / nt), (int)((long long)n * (k + 1) / nt), &err_at[k]);
+      });
+  } catch (...) {
+    spawned = false;
+  }
+  if (spawned) err[0] = serial(0, (int)((long long)n / nt), &err_at[0]);
+  for (auto& x : th) x.join();
+  if (!spawned) return serial(0, n, &at);     // no threads to be had: the plain loop
+  for (int k = 0; k < nt; ++k)
+    if (!err[k].empty()) return err[k];      // ranges ascend with k
+  return std::string();
+}
+
 }  // namespace
 
 namespace {
@@ -68,6 +113,25 @@ unsigned long long mix64(unsigned long long x) {
   return x;
 }
 }  // namespace
+
+void HostTree::reset() {
+  ndim = nb = nblocks = nleaves = maxlev = nslots = 0;
+  hmask = 0;
+  for (auto* v : {&leaf_to_block, &blk_problem, &blk_level, &blk_ijk, &children, &all_leaves, &leaves_per_problem,
+                  &hvals})
+    v->clear();
+  geo.clear();
+  regions.clear();
+  pushes.clear();
+  level_has_residual.clear();
+  refl.clear();
+  reflux_tasks.clear();
+  leaves_by_level.clear();
+  parents_by_level.clear();
+  mindx.clear();
+  keys.clear();
+  hkeys.clear();
+}
 
 void HostTree::build_index() {
   size_t cap = 16;
@@ -100,7 +164,7 @@ int HostTree::find(int p, int L, int i, int j, int k) const {
 
 std::string build_tree(int ndim, int nb, const std::vector<map_problem_desc>& probs,
                        const map_block_desc* leaves, int n, HostTree& t) {
-  t = HostTree();
+  t.reset();
   t.ndim = ndim;
   t.nb = nb;
   const int np = (int)probs.size();
@@ -244,7 +308,7 @@ std::string build_tree(int ndim, int nb, const std::vector<map_problem_desc>& pr
           }
   }
   // 2:1 balance over faces, edges and corners
-  for (int id = 0; id < n; ++id) {
+  std::string err = for_each_leaf(n, [&](int id) -> std::string {
     int p = t.blk_problem[id], L = t.blk_level[id];
     const int* c = &t.blk_ijk[3 * id];
     for (int oz = (ndim == 3 ? -1 : 0); oz <= (ndim == 3 ? 1 : 0); ++oz)
@@ -280,10 +344,12 @@ std::string build_tree(int ndim, int nb, const std::vector<map_problem_desc>& pr
             if (cq < 0 || cq >= n) return fmt("2:1 balance violated (coarser by two levels)", p, L, c);
           }
         }
-  }
+    return std::string();
+  });
+  if (!err.empty()) return err;
   // ghost regions of every leaf
   t.regions.assign((size_t)NB * 27, GhostRegion{});
-  for (int id = 0; id < n; ++id) {
+  err = for_each_leaf(n, [&](int id) -> std::string {
     int p = t.blk_problem[id], L = t.blk_level[id];
     const int* c = &t.blk_ijk[3 * id];
     for (int rz = 0; rz < 3; ++rz)
@@ -336,7 +402,9 @@ std::string build_tree(int ndim, int nb, const std::vector<map_problem_desc>& pr
           }
           t.regions[(size_t)id * 27 + rx + 3 * ry + 9 * rz] = g;
         }
-  }
+    return std::string();
+  });
+  if (!err.empty()) return err;
   // pushes: a same-level leaf copy with an affine map in every dimension is written by the
   // source block's step kernel into the destination's ghost region
   t.pushes.assign((size_t)NB * 27, PushEntry{-1, {0, 0, 0}});
