@@ -244,14 +244,16 @@ int map_last_sums(map_pool* pool, double* sums_out);
 typedef struct {
   int grid;           /* step-kernel CTAs: 0 = one per block, else a persistent grid */
   int w_pred, w_face; /* warp-schedule cost of a predictor unit and of a face unit */
-  double ms_default;  /* step launches with the default shape (one CTA per block, 7:4) */
+  double ms_default;  /* step launches with the default shape (one CTA per block, default
+                         weights: 1:1 in 2D, 3:1 for 3D 16^3 LF/MMC, 3:2 for 3D 8^3) */
   double ms_best;     /* with the chosen shape */
   int trials;
 } map_tune_result;
 
 /* Autotuner (no counterpart in the paper): times this pool's step launches on its current
  * tree and state under candidate launch shapes -- one CTA per block or a persistent grid of
- * 1-16 x the SM count, then warp-schedule weights for the per-plane work list -- and keeps the
+ * 1-16 x the SM count, then warp-schedule weight ratios from 1:1 to 6:1 for the per-plane
+ * work list -- and keeps the
  * fastest for later map_step / map_advance calls (results are bitwise the same under every
  * shape; the fused FP64 sums may differ in rounding).  The state is not changed: trials
  * write only the other buffers, and the step constants and sums are restored.  Ghosts are

@@ -1030,20 +1030,24 @@ int map_autotune(map_pool* pool, const map_params* p, int reps, map_tune_result*
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   float best = 0.f, t = 0.f;
-  int bg = 0, bwp = 7, bwf = 4;
-  rc = trial(0, 7, 4, &best);
+  int dwp = 1, dwf = 1;
+  default_schedule_weights(pool->ndim, pool->nb, p->scheme, &dwp, &dwf);
+  int bg = 0, bwp = dwp, bwf = dwf;
+  rc = trial(0, dwp, dwf, &best);
   const float base = best;
   const int K[] = {1, 2, 3, 4, 6, 8, 12, 16};
   for (int k : K) {
     if (rc) break;
     const int grid = k * nsm;
     if (grid >= pool->tree.nleaves) break;
-    rc = trial(grid, 7, 4, &t);
+    rc = trial(grid, dwp, dwf, &t);
     if (rc == MAP_OK && t < best) { best = t; bg = grid; }
   }
-  const int W[][2] = {{1, 1}, {2, 1}, {5, 4}, {6, 4}, {8, 4}, {9, 4}, {7, 3}, {7, 5}};
+  // weight ratios from 1:1 to 6:1 (only the ratio shapes the schedule); the default's is skipped
+  const int W[][2] = {{1, 1}, {5, 4}, {3, 2}, {2, 1}, {9, 4}, {3, 1}, {4, 1}, {6, 1}};
   for (const auto& wgt : W) {
     if (rc) break;
+    if (wgt[0] * dwf == wgt[1] * dwp) continue;
     rc = trial(bg, wgt[0], wgt[1], &t);
     if (rc == MAP_OK && t < best) { best = t; bwp = wgt[0]; bwf = wgt[1]; }
   }

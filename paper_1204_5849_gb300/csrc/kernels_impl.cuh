@@ -37,7 +37,9 @@ cudaError_t launch_step_one(const StepLaunch& L, cudaStream_t s) {
   A.pushes = L.pushes;
   A.freg = RFX ? (T*)L.freg : nullptr;
   A.refl = RFX ? L.refl : nullptr;
-  build_schedule<NDIM, NB>(L.w_pred > 0 ? L.w_pred : 7, L.w_face > 0 ? L.w_face : 4, A.sched);
+  int wp = L.w_pred, wf = L.w_face;
+  if (wp <= 0 || wf <= 0) default_schedule_weights(NDIM, NB, SCHEME, &wp, &wf);
+  build_schedule<NDIM, NB>(wp, wf, SCHEME != SCH_WENO || res, A.sched);
   A.fail_waits = L.fail_waits;
   const int grid = L.grid > 0 ? (L.grid < L.nblocks ? L.grid : L.nblocks) : L.nblocks;
   if (grid <= 0) return cudaSuccess;

@@ -131,6 +131,21 @@ std::string build_regrid(const HostTree& old_t, const HostTree& new_t,
 // ---------------------------------------------------------------------------------------
 // Kernel launchers (kernels_f64.cu / kernels_f32.cu).
 
+// Default warp-schedule weights (predictor unit : face unit) of the step kernel's per-plane
+// work list, from step times measured on GB300 over the weight ratio (map_autotune searches
+// around them).  In 2D the predictor and the faces run in separate barrier intervals, so each
+// kind is best spread evenly (1:1); in 3D one interval holds both and the weights follow the
+// two units' costs (an LF predictor unit costs about three face units, MMC alike; with the
+// resistive current of the 8^3 Harris-sheet kernel, 3:2 measured best).
+inline void default_schedule_weights(int ndim, int nb, int scheme, int* w_pred, int* w_face) {
+  *w_pred = 1;
+  *w_face = 1;
+  if (ndim == 3 && (scheme == MAP_LF || scheme == MAP_MMC)) {
+    *w_pred = 3;
+    *w_face = nb == 8 ? 2 : 1;
+  }
+}
+
 struct StepLaunch {
   const void* u_in;        // state with ghosts
   void* u_out;             // output state (interior written)
@@ -146,7 +161,7 @@ struct StepLaunch {
   ProbDyn* dyn_next;       // optional: max alpha of the output into dyn_next[p].alpha_bits
   int grid;                // CTAs (0 = one per block)
   int riemann;             // interface flux of LF and WENO: 0 f_m, 1 HLLC
-  int w_pred = 0, w_face = 0;  // warp-schedule weights (0: the defaults 7 and 4)
+  int w_pred = 0, w_face = 0;  // warp-schedule weights (0: default_schedule_weights)
   int fail_waits = 0;          // test hook (map_test_fail_waits)
   const PushEntry* pushes; // optional: write boundary layers into same-level neighbours' ghosts
   void* freg;              // optional: face registers (reflux); with refl

@@ -27,6 +27,7 @@
 namespace mapgb {
 
 enum { SCH_MMC = 0, SCH_LF = 1, SCH_WENO = 2 };
+static_assert(SCH_MMC == MAP_MMC && SCH_LF == MAP_LF && SCH_WENO == MAP_WENO, "scheme codes follow map.h");
 enum { FLX_LF = 0, FLX_HLLC = 1 };   // interface flux of LF and WENO: f_m or HLLC
 
 template <typename T>
@@ -63,6 +64,9 @@ struct Geo {
   static constexpr int WPL = NDIM == 3 ? 3 : 1;   // u~ and J planes z-1..z+1
   static constexpr int RW = NB + 2;               // ring row width (padded 1..NB+2)
   static constexpr int RING = RW * RW;
+  // ring cells the predictor fills: all but the four corners, which no stencil reads (the
+  // faces read u~ across one axis; the sources read u~ and J along the axes)
+  static constexpr int NPC = RING - 4;
   static constexpr int NFACE = NB * (NB + 1);
 };
 
@@ -371,13 +375,14 @@ __device__ __forceinline__ void resist_src_col(const T* jc, int cj, const T* jzm
 template <int N>
 struct Pad32 { static constexpr int value = (N + 31) / 32 * 32; };
 
-// The per-plane work list of the step kernel: warp-sized units of predictor ring cells (NPU),
+// The per-plane work list of the step kernel: warp-sized units of predictor ring cells (NPU,
+// corners left out),
 // then x faces and y faces (NXU each), over NW warps.
 template <int NDIM, int NB>
 struct WorkList {
   using G = Geo<NDIM, NB>;
   static constexpr int NW = G::NT / 32;
-  static constexpr int NPU = Pad32<G::RING>::value / 32;
+  static constexpr int NPU = Pad32<G::NPC>::value / 32;
   static constexpr int NXU = Pad32<G::NFACE>::value / 32;
   static constexpr int NU = NPU + 2 * NXU;
   static_assert(NW <= 8 && NU <= 15 * NW, "work list exceeds the schedule table");
@@ -385,15 +390,16 @@ struct WorkList {
 
 // Warp schedule, built on the host once per launch: each unit goes, in order, to the
 // least-loaded warp that has room (ties to the lowest warp), a predictor unit weighing w_pred
-// and a face unit w_face (their relative cost; 7 and 4 unless tuned).  s[w][15] holds the
-// number of units of warp w, s[w][0..] the units.
+// and a face unit w_face (their relative cost; default_schedule_weights unless tuned).  s[w][15] holds the
+// number of units of warp w, s[w][0..] the units.  Without a predictor (WENO without
+// resistivity) its units are left out, so they do not displace face units.
 template <int NDIM, int NB>
-inline void build_schedule(int w_pred, int w_face, unsigned char (&s)[8][16]) {
+inline void build_schedule(int w_pred, int w_face, bool pred, unsigned char (&s)[8][16]) {
   using W = WorkList<NDIM, NB>;
   int load[8] = {0}, cnt[8] = {0};
   for (int q = 0; q < 8; ++q)
     for (int k = 0; k < 16; ++k) s[q][k] = 0;
-  for (int u = 0; u < W::NU; ++u) {
+  for (int u = pred ? 0 : W::NPU; u < W::NU; ++u) {
     int best = -1;
     for (int q = 0; q < W::NW; ++q)
       if (cnt[q] < 15 && (best < 0 || load[q] < load[best])) best = q;
@@ -774,8 +780,10 @@ step_kernel(StepArgsT<T> A) {
       for (int k = 0; k < cnt; ++k) {
         const int u = sched[wq][k];
         if (u < NPU) {
-          const int r = u * 32 + lane;
-          if (do_pred && r < RING) predict_cell(zp, r);
+          // q-th ring cell in row order, the corners 0, RW-1, RING-RW and RING-1 skipped
+          const int q = u * 32 + lane;
+          const int r = q + 1 + (q >= RW - 2) + (q >= RING - RW - 2);
+          if (do_pred && q < G::NPC) predict_cell(zp, r);
         } else if (u < NPU + NXU) {
           const int f = (u - NPU) * 32 + lane;
           if (do_faces && f < NFACE) do_xface(zf, f);
