@@ -485,20 +485,6 @@ step_kernel(StepArgsT<T> A) {
   for (int bi = blockIdx.x; bi < A.nblocks; bi += gridDim.x) {
     const int blk = A.blocks[bi];
     const BlockGeo gg = A.geo[blk];
-    if (tid == 0) {
-      // per-block constants, computed once in FP64 and rounded to T
-      const ProbDyn dy = A.dyn[gg.problem];
-      for (int d = 0; d < 3; ++d) {
-        kc[d] = (T)(dy.dt / gg.dx[d]);
-        kc[3 + d] = (T)((0.5 * dy.dt) / gg.dx[d]);
-        kc[6 + d] = (T)(2.0 * gg.dx[d]);
-        kc[9 + d] = (T)gg.dx[d];
-      }
-      kc[12] = (T)dy.dt;
-      kc[13] = (T)(0.5 * dy.dt);
-      kc[14] = (T)dy.damp;
-      kc[15] = (T)dy.ch;
-    }
     if (A.pushes && tid < 27) spush[tid] = A.pushes[(size_t)blk * 27 + tid];   // read after the first barrier
     if (RFX && tid == 0) srl = A.refl[blk];             // read after the first barrier
     const T* ub = A.u_in + (size_t)blk * NV * S;
@@ -804,6 +790,19 @@ step_kernel(StepArgsT<T> A) {
         issue_plane(2);
         issue_plane(3);
       }
+      // per-block constants, computed in FP64 and rounded to T while the first planes are
+      // in flight
+      const ProbDyn dy = A.dyn[gg.problem];
+      for (int d = 0; d < 3; ++d) {
+        kc[d] = (T)(dy.dt / gg.dx[d]);
+        kc[3 + d] = (T)((0.5 * dy.dt) / gg.dx[d]);
+        kc[6 + d] = (T)(2.0 * gg.dx[d]);
+        kc[9 + d] = (T)gg.dx[d];
+      }
+      kc[12] = (T)dy.dt;
+      kc[13] = (T)(0.5 * dy.dt);
+      kc[14] = (T)dy.damp;
+      kc[15] = (T)dy.ch;
     }
     // 3D: iteration z predicts plane z+1 and updates plane z (z >= NG); one call site per
     // work-item kind keeps the kernel's code small.  2D: a single plane.
@@ -1009,41 +1008,38 @@ step_kernel(StepArgsT<T> A) {
         const T t = __shfl_xor_sync(0xffffffffu, am, o);
         am = (t != t || am != am) ? (T)NAN : dmax<T>(am, t);
       }
-      T hi[NV], lo[NV];
+      // after the butterflies every lane holds the warp's (hi, lo) of variable v; lane v
+      // keeps it as one FP64 value and stores it, lane NV stores the alpha maximum
+      double mine = (double)am;
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
-        hi[v] = csum[v];
-        lo[v] = -ccmp[v];
+        T hi = csum[v], lo = -ccmp[v];
         for (int o = 16; o > 0; o >>= 1) {
-          const T h2 = __shfl_xor_sync(0xffffffffu, hi[v], o);
-          const T l2 = __shfl_xor_sync(0xffffffffu, lo[v], o);
-          two_sum_acc<T>(hi[v], lo[v], h2, l2);
+          const T h2 = __shfl_xor_sync(0xffffffffu, hi, o);
+          const T l2 = __shfl_xor_sync(0xffffffffu, lo, o);
+          two_sum_acc<T>(hi, lo, h2, l2);
         }
+        if (lane == v) mine = (double)hi + (double)lo;
       }
-      if (lane == 0) {
-        red[NV * 32 + wid] = (double)am;
-#pragma unroll
-        for (int v = 0; v < NV; ++v) red[v * 32 + wid] = (double)hi[v] + (double)lo[v];
-      }
+      if (lane <= NV) red[lane * 32 + wid] = mine;
       __syncthreads();
-      if (tid == 0) {
+      if (tid <= NV) {
+        // warp 0: lane v adds variable v over the warps (in warp order), lane NV takes the
+        // alpha maximum
         const int nw = (NT + 31) / 32;
-        double a2 = 0.0;
-        for (int q = 0; q < nw; ++q) {
-          const double t = red[NV * 32 + q];
-          a2 = (t != t || a2 != a2) ? __longlong_as_double(0x7ff8000000000000ll) : fmax(a2, t);
-        }
-        if (A.dyn_next) {
-          // alpha >= 0: its IEEE bit pattern orders like the value (NaN above everything)
-          atomicMax(&A.dyn_next[gg.problem].alpha_bits, (unsigned long long)__double_as_longlong(a2));
-        }
-        if (A.sums) {
-          const double vol = gg.dx[0] * gg.dx[1] * (NDIM == 3 ? gg.dx[2] : 1.0);
-          for (int v = 0; v < NV; ++v) {
-            double t = 0.0;
-            for (int q = 0; q < nw; ++q) t += red[v * 32 + q];
-            atomicAdd(&A.sums[gg.problem * NV + v], t * vol);
+        if (tid == NV) {
+          double a2 = 0.0;
+          for (int q = 0; q < nw; ++q) {
+            const double t = red[NV * 32 + q];
+            a2 = (t != t || a2 != a2) ? __longlong_as_double(0x7ff8000000000000ll) : fmax(a2, t);
           }
+          // alpha >= 0: its IEEE bit pattern orders like the value (NaN above everything)
+          if (A.dyn_next) atomicMax(&A.dyn_next[gg.problem].alpha_bits, (unsigned long long)__double_as_longlong(a2));
+        } else if (A.sums) {
+          const double vol = gg.dx[0] * gg.dx[1] * (NDIM == 3 ? gg.dx[2] : 1.0);
+          double t = 0.0;
+          for (int q = 0; q < nw; ++q) t += red[tid * 32 + q];
+          atomicAdd(&A.sums[gg.problem * NV + tid], t * vol);
         }
       }
       __syncthreads();
