@@ -277,6 +277,11 @@ static int install_tree(map_pool* pool, HostTree& t) {
   for (int p = 0; p < pool->nprob; ++p) {
     dyn[p].mindx = t.mindx[p];
     dyn[p].alpha_bits = 0ull;
+    // level-0 spacing, the same expression as the tree's per-block spacing at level 0
+    for (int d = 0; d < 3; ++d) {
+      const int ncell = d < pool->ndim ? pool->probs[p].nbase[d] * pool->nb : 1;
+      dyn[p].dx0[d] = (pool->probs[p].hi[d] - pool->probs[p].lo[d]) / (double)ncell;
+    }
   }
   CK(cudaMemcpyAsync(pool->dyn, dyn.data(), sizeof(ProbDyn) * pool->nprob, cudaMemcpyHostToDevice, pool->stream));
   // staging for host-layout copies

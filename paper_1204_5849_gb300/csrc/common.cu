@@ -41,6 +41,9 @@ __global__ void finalize_kernel(FinalizeLaunch L) {
   d.alpha_bits = 0ull;
   d.kmax_bits = 0ull;
   d.dtc = dtc;
+  // per-dimension dt/dx at level 0; a level-L block takes 2^L of it, which is dt/dx_L
+  // exactly (dx_L = dx0 / 2^L as the host computes it), so blocks divide nothing
+  for (int k = 0; k < 3; ++k) d.lam0[k] = dt / d.dx0[k];
   L.dyn[p] = d;
 }
 

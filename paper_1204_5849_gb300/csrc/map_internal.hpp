@@ -30,7 +30,8 @@ struct ProbDyn {
   unsigned long long alpha_bits;   // running max of alpha (as ordered bits, alpha >= 0)
   unsigned long long kmax_bits;    // running max of kappa / rho (thermal conduction), as bits
   double dtc;                      // thermal-conduction time step (Sec. 3.6), +inf if none
-  double pad;
+  double dx0[3];                   // the problem's level-0 cell spacing (host, per tree)
+  double lam0[3];                  // dt / dx0 (finalisation); dt/dx at level L = 2^L dt/dx0
 };
 
 // One ghost region of a leaf (3^ndim regions, region id = rx + 3 ry + 9 rz with

@@ -790,17 +790,23 @@ step_kernel(StepArgsT<T> A) {
         issue_plane(2);
         issue_plane(3);
       }
-      // per-block constants, computed in FP64 and rounded to T while the first planes are
-      // in flight
+      // per-block constants, rounded to T while the first planes are in flight.  dt/dx at
+      // level L is 2^L dt/dx0 exactly, and rounding to T commutes with scaling by powers of
+      // two, so these equal the FP64 dt/dx, (dt/2)/dx, 2 dx, dx, dt, dt/2 rounded to T
+      // without an FP64 division per block (the FP64 pipe runs at 1/64 of the FP32 rate)
       const ProbDyn dy = A.dyn[gg.problem];
+      const T scale = (T)(1 << gg.level);
       for (int d = 0; d < 3; ++d) {
-        kc[d] = (T)(dy.dt / gg.dx[d]);
-        kc[3 + d] = (T)((0.5 * dy.dt) / gg.dx[d]);
-        kc[6 + d] = (T)(2.0 * gg.dx[d]);
-        kc[9 + d] = (T)gg.dx[d];
+        const T lam_d = (T)dy.lam0[d] * (d < NDIM ? scale : T(1));
+        const T dx_d = (T)gg.dx[d];
+        kc[d] = lam_d;
+        kc[3 + d] = T(0.5) * lam_d;
+        kc[6 + d] = T(2) * dx_d;
+        kc[9 + d] = dx_d;
       }
-      kc[12] = (T)dy.dt;
-      kc[13] = (T)(0.5 * dy.dt);
+      const T dt_T = (T)dy.dt;
+      kc[12] = dt_T;
+      kc[13] = T(0.5) * dt_T;
       kc[14] = (T)dy.damp;
       kc[15] = (T)dy.ch;
     }
@@ -1009,8 +1015,9 @@ step_kernel(StepArgsT<T> A) {
         am = (t != t || am != am) ? (T)NAN : dmax<T>(am, t);
       }
       // after the butterflies every lane holds the warp's (hi, lo) of variable v; lane v
-      // keeps it as one FP64 value and stores it, lane NV stores the alpha maximum
-      double mine = (double)am;
+      // keeps variable v's pair and widens it to one FP64 value (one conversion per warp:
+      // the FP64 pipe runs at 1/64 of the FP32 rate), lane NV the alpha maximum
+      T hsel = am, lsel = T(0);
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
         T hi = csum[v], lo = -ccmp[v];
@@ -1019,9 +1026,10 @@ step_kernel(StepArgsT<T> A) {
           const T l2 = __shfl_xor_sync(0xffffffffu, lo, o);
           two_sum_acc<T>(hi, lo, h2, l2);
         }
-        if (lane == v) mine = (double)hi + (double)lo;
+        if (lane == v) { hsel = hi; lsel = lo; }
       }
-      if (lane <= NV) red[lane * 32 + wid] = mine;
+      if (lane < NV) red[lane * 32 + wid] = (double)hsel + (double)lsel;
+      if (lane == NV) red[NV * 32 + wid] = (double)hsel;
       __syncthreads();
       if (tid <= NV) {
         // warp 0: lane v adds variable v over the warps (in warp order), lane NV takes the
