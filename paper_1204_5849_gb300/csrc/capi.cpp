@@ -19,12 +19,13 @@ struct DevTree {
   int* all_leaves = nullptr;   // pool ids 0..n-1 (Morton order)
   int* level_leaves = nullptr; // concatenated by level
   int* level_parents = nullptr;
+  int* level_residual = nullptr;  // per level: leaves with ghost regions the pushes leave over
   PushEntry* pushes = nullptr;
   RefluxLeaf* refl = nullptr;
   RefluxTask* rtasks = nullptr;
   int nrtasks = 0;
   void* freg = nullptr;        // face registers, tree.nslots slots
-  std::vector<int> leaf_off, parent_off;  // offsets per level (host)
+  std::vector<int> leaf_off, parent_off, residual_off;  // offsets per level (host)
 };
 
 struct map_pool {
@@ -113,6 +114,7 @@ static void free_tree(map_pool* pool) {
   cudaFree(pool->dt.all_leaves);
   cudaFree(pool->dt.level_leaves);
   cudaFree(pool->dt.level_parents);
+  cudaFree(pool->dt.level_residual);
   cudaFree(pool->dt.pushes);
   cudaFree(pool->dt.refl);
   cudaFree(pool->dt.rtasks);
@@ -257,19 +259,24 @@ static int install_tree(map_pool* pool, HostTree& t) {
     D.nrtasks = (int)t.reflux_tasks.size();
     CK(cudaMalloc(&D.freg, (size_t)t.nslots * 2 * pool->ndim * kNV * pool->nb * pool->nb * pool->elem));
   }
-  std::vector<int> ll, pl;
+  std::vector<int> ll, pl, rl;
   D.leaf_off.assign(t.maxlev + 2, 0);
   D.parent_off.assign(t.maxlev + 2, 0);
+  D.residual_off.assign(t.maxlev + 2, 0);
   for (int L = 0; L <= t.maxlev; ++L) {
     D.leaf_off[L] = (int)ll.size();
     ll.insert(ll.end(), t.leaves_by_level[L].begin(), t.leaves_by_level[L].end());
     D.parent_off[L] = (int)pl.size();
     pl.insert(pl.end(), t.parents_by_level[L].begin(), t.parents_by_level[L].end());
+    D.residual_off[L] = (int)rl.size();
+    rl.insert(rl.end(), t.residual_by_level[L].begin(), t.residual_by_level[L].end());
   }
   D.leaf_off[t.maxlev + 1] = (int)ll.size();
   D.parent_off[t.maxlev + 1] = (int)pl.size();
+  D.residual_off[t.maxlev + 1] = (int)rl.size();
   CK(upload(&D.level_leaves, ll, pool->stream));
   CK(upload(&D.level_parents, pl, pool->stream));
+  CK(upload(&D.level_residual, rl, pool->stream));
   // per-problem minimum spacing (dt uses the finest leaf, Sec. 4.5 / Sec. 3.7)
   std::vector<ProbDyn> dyn(pool->nprob);
   CK(cudaMemcpyAsync(dyn.data(), pool->dyn, sizeof(ProbDyn) * pool->nprob, cudaMemcpyDeviceToHost, pool->stream));
@@ -447,8 +454,9 @@ static int fill_on(map_pool* pool, int q) {
     if (residual && !t.level_has_residual[L]) continue;
     FillLaunch F;
     F.u = pool->buf[q];
-    F.blocks = D.level_leaves + D.leaf_off[L];
-    F.nblocks = D.leaf_off[L + 1] - D.leaf_off[L];
+    // after a step only the leaves with regions that no push wrote take part
+    F.blocks = residual ? D.level_residual + D.residual_off[L] : D.level_leaves + D.leaf_off[L];
+    F.nblocks = residual ? D.residual_off[L + 1] - D.residual_off[L] : D.leaf_off[L + 1] - D.leaf_off[L];
     F.regions = D.regions;
     F.skip_pushed = residual ? 1 : 0;
     CK(DISPATCH(pool, fill, F));

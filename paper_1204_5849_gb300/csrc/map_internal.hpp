@@ -101,6 +101,7 @@ struct HostTree {
   int nslots = 0;                           // face-register slots
   std::vector<std::vector<int>> leaves_by_level;   // pool ids
   std::vector<std::vector<int>> parents_by_level;  // pool ids
+  std::vector<std::vector<int>> residual_by_level; // leaves with a ghost region no step pushes
   std::vector<int> all_leaves;              // pool ids, Morton order
   std::vector<double> mindx;                // per problem
   std::vector<int> leaves_per_problem;

@@ -128,6 +128,7 @@ void HostTree::reset() {
   reflux_tasks.clear();
   leaves_by_level.clear();
   parents_by_level.clear();
+  residual_by_level.clear();
   mindx.clear();
   keys.clear();
   hkeys.clear();
@@ -409,7 +410,9 @@ std::string build_tree(int ndim, int nb, const std::vector<map_problem_desc>& pr
   // source block's step kernel into the destination's ghost region
   t.pushes.assign((size_t)NB * 27, PushEntry{-1, {0, 0, 0}});
   t.level_has_residual.assign(t.maxlev + 1, 0);
+  t.residual_by_level.assign(t.maxlev + 1, {});
   for (int id = 0; id < n; ++id) {
+    bool residual = false;
     for (int rz = 0; rz < 3; ++rz)
       for (int ry = 0; ry < 3; ++ry)
         for (int rx = 0; rx < 3; ++rx) {
@@ -429,8 +432,12 @@ std::string build_tree(int ndim, int nb, const std::vector<map_problem_desc>& pr
               g.pushed = 1;
             }
           }
-          if (!g.pushed) t.level_has_residual[t.blk_level[id]] = 1;
+          if (!g.pushed) residual = true;
         }
+    if (residual) {
+      t.level_has_residual[t.blk_level[id]] = 1;
+      t.residual_by_level[t.blk_level[id]].push_back(id);
+    }
   }
   // reflux: the coarse leaf of every coarse/fine face gets a task naming the fine leaves
   // covering that face; both sides get a face-register slot
