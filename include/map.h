@@ -245,7 +245,7 @@ typedef struct {
   int grid;           /* step-kernel CTAs: 0 = one per block, else a persistent grid */
   int w_pred, w_face; /* warp-schedule cost of a predictor unit and of a face unit */
   double ms_default;  /* step launches with the default shape (one CTA per block, default
-                         weights: 1:1 in 2D, 3:1 for 3D 16^3 LF/MMC, 3:2 for 3D 8^3) */
+                         weights: 3:1 for 3D LF, 3:2 for 3D MMC, 7:4 in 2D, 1:1 for WENO) */
   double ms_best;     /* with the chosen shape */
   int trials;
 } map_tune_result;

@@ -135,16 +135,23 @@ std::string build_regrid(const HostTree& old_t, const HostTree& new_t,
 
 // Default warp-schedule weights (predictor unit : face unit) of the step kernel's per-plane
 // work list, from step times measured on GB300 over the weight ratio (map_autotune searches
-// around them).  In 2D the predictor and the faces run in separate barrier intervals, so each
-// kind is best spread evenly (1:1); in 3D one interval holds both and the weights follow the
-// two units' costs (an LF predictor unit costs about three face units, MMC alike; with the
-// resistive current of the 8^3 Harris-sheet kernel, 3:2 measured best).
+// around them): 3:1 for 3D LF (16^3 and the resistive 8^3), 3:2 for 3D MMC, 7:4 for 2D LF and
+// MMC (the predictor and the faces run in separate barrier intervals there), 1:1 for WENO,
+// whose only predictor work is the resistive current.
 inline void default_schedule_weights(int ndim, int nb, int scheme, int* w_pred, int* w_face) {
+  (void)nb;
   *w_pred = 1;
   *w_face = 1;
-  if (ndim == 3 && (scheme == MAP_LF || scheme == MAP_MMC)) {
+  if (scheme == MAP_WENO) return;
+  if (ndim == 2) {
+    *w_pred = 7;
+    *w_face = 4;
+  } else if (scheme == MAP_LF) {
     *w_pred = 3;
-    *w_face = nb == 8 ? 2 : 1;
+    *w_face = 1;
+  } else {
+    *w_pred = 3;
+    *w_face = 2;
   }
 }
 

@@ -362,6 +362,16 @@ __device__ __forceinline__ void resist_src_col(const T* jc, int cj, const T* jzm
   s[EN] += re;
 }
 
+// Exchange of the x and y components of m and B when yd (the map P with F_y(U) = P F_x(P U)).
+template <typename V>
+__device__ __forceinline__ void exch_xy(bool yd, V* w) {
+  const V mx = w[MX], my = w[MY], bx = w[BX], by = w[BY];
+  w[MX] = yd ? my : mx;
+  w[MY] = yd ? mx : my;
+  w[BX] = yd ? by : bx;
+  w[BY] = yd ? bx : by;
+}
+
 // ---- the kernel --------------------------------------------------------------------------
 //
 // 3D z-march with a window of three resident u planes (z..z+2) plus one plane in flight:
@@ -377,14 +387,14 @@ struct Pad32 { static constexpr int value = (N + 31) / 32 * 32; };
 
 // The per-plane work list of the step kernel: warp-sized units of predictor ring cells (NPU,
 // corners left out),
-// then x faces and y faces (NXU each), over NW warps.
+// then the x faces and y faces in one numbering (NFU), over NW warps.
 template <int NDIM, int NB>
 struct WorkList {
   using G = Geo<NDIM, NB>;
   static constexpr int NW = G::NT / 32;
   static constexpr int NPU = Pad32<G::NPC>::value / 32;
-  static constexpr int NXU = Pad32<G::NFACE>::value / 32;
-  static constexpr int NU = NPU + 2 * NXU;
+  static constexpr int NFU = Pad32<2 * G::NFACE>::value / 32;   // x faces, then y faces
+  static constexpr int NU = NPU + NFU;
   static_assert(NW <= 8 && NU <= 15 * NW, "work list exceeds the schedule table");
 };
 
@@ -458,7 +468,6 @@ step_kernel(StepArgsT<T> A) {
   // block; thread 0 copies it from the arguments with constant indices
   constexpr int NW = WorkList<NDIM, NB>::NW;
   constexpr int NPU = WorkList<NDIM, NB>::NPU;
-  constexpr int NXU = WorkList<NDIM, NB>::NXU;
   __shared__ int sched[NW][16];
   __shared__ RefluxLeaf srl;               // the block's face-register slot and coarse-side mask
   if (tid == 0) {
@@ -628,8 +637,12 @@ step_kernel(StepArgsT<T> A) {
 
     // x (D=0) or y (D=1) face flux between in-plane cells cl and cl+st (full layout), with
     // the u~ ring cells rl and rl+rs
-    auto face_xy = [&](auto Dc, const T* up, const T* tp, int cl, int st, int rl, int rs, T* F) {
-      constexpr int D = decltype(Dc)::value;
+    // x face (yd false) or y face (yd true) flux between in-plane cells cl and cl+st (full
+    // layout), with the u~ ring cells rl and rl+rs.  A y face is the x-face flux of the states
+    // with the x and y components of m and B exchanged, exchanged back: F_y(U) = P F_x(P U)
+    // with the same operations on the same operands, so both directions share one instance
+    // of the flux code (and a warp may hold faces of both)
+    auto face_xy = [&](bool yd, const T* up, const T* tp, int cl, int st, int rl, int rs, T* F) {
       if (SCHEME == SCH_MMC) {
         T w0[NV], w1[NV], w2[NV], w3[NV], t0[NV], t1[NV];
         ldw<T, P2>(up, cl - st, w0);
@@ -638,7 +651,13 @@ step_kernel(StepArgsT<T> A) {
         ldw<T, P2>(up, cl + 2 * st, w3);
         ldw<T, RING>(tp, rl, t0);
         ldw<T, RING>(tp, rl + rs, t1);
-        mmc_face<T, D, LIM>(w0, w1, w2, w3, t0, t1, P, F);
+        exch_xy(yd, w0);
+        exch_xy(yd, w1);
+        exch_xy(yd, w2);
+        exch_xy(yd, w3);
+        exch_xy(yd, t0);
+        exch_xy(yd, t1);
+        mmc_face<T, 0, LIM>(w0, w1, w2, w3, t0, t1, P, F);
       } else if (std::is_same<T, float>::value && SCHEME == SCH_LF && FLX == FLX_LF) {
         float2 ab[NV];
 #pragma unroll
@@ -650,7 +669,8 @@ step_kernel(StepArgsT<T> A) {
           const float2 tt = make_float2(tp[v * RING + rl], tp[v * RING + rl + rs]);
           ab[v] = pair::fma(ph, make_float2(0.5f, -0.5f), tt);
         }
-        pair::lf_flux2<D>(ab, *reinterpret_cast<const Phys<float>*>(&P), reinterpret_cast<float*>(F));
+        exch_xy(yd, ab);
+        pair::lf_flux2<0>(ab, *reinterpret_cast<const Phys<float>*>(&P), reinterpret_cast<float*>(F));
       } else {
         T a[NV], b[NV];
 #pragma unroll
@@ -667,9 +687,12 @@ step_kernel(StepArgsT<T> A) {
             b[v] = weno_plus_left<T>(u1, u2, u3);
           }
         }
-        if (FLX == FLX_HLLC) hllc_flux<T, D>(a, b, P, F);
-        else lf_flux<T, D>(a, b, P, F);
+        exch_xy(yd, a);
+        exch_xy(yd, b);
+        if (FLX == FLX_HLLC) hllc_flux<T, 0>(a, b, P, F);
+        else lf_flux<T, 0>(a, b, P, F);
       }
+      exch_xy(yd, F);
     };
 
     // face register (reflux, Sec. 4.2): the flux through a boundary face cell of this block
@@ -688,25 +711,22 @@ step_kernel(StepArgsT<T> A) {
     // of plane z into the face buffer (x faces first, then y faces)
     T* sfx = sf;
     T* sfy = sf + (size_t)NV * NFACE;
-    auto do_xface = [&](int z, int f) {
-      const int row = f / (NB + 1), fx = f % (NB + 1);
+    // face k of plane z: x faces k < NFACE (f = row (NB+1) + fx), then y faces (f = fy NB + col)
+    auto do_face = [&](int z, int k) {
+      const bool yd = k >= NFACE;
+      const int f = yd ? k - NFACE : k;
+      const int row = f / (NB + 1), fx = f % (NB + 1);       // x face
+      const int fy = f / NB, col = f % NB;                   // y face
       T F[NV];
-      face_xy(std::integral_constant<int, 0>(), uslot(z), HAS_T ? tslot(z) : nullptr, (row + NG) * NP + fx + 1, 1,
-              (row + 1) * RW + fx, 1, F);
+      face_xy(yd, uslot(z), HAS_T ? tslot(z) : nullptr, yd ? (fy + 1) * NP + col + NG : (row + NG) * NP + fx + 1,
+              yd ? NP : 1, yd ? fy * RW + col + 1 : (row + 1) * RW + fx, yd ? RW : 1, F);
+      T* dst = (yd ? sfy : sfx) + f;
 #pragma unroll
-      for (int v = 0; v < NV; ++v) sfx[v * NFACE + f] = F[v];
-      if (RFX && SCHEME == SCH_LF && (fx == 0 || fx == NB) && srl.slot >= 0)
-        put_face(fx ? 1 : 0, row, NDIM == 3 ? z - NG : 0, F);
-    };
-    auto do_yface = [&](int z, int f) {
-      const int fy = f / NB, col = f % NB;
-      T F[NV];
-      face_xy(std::integral_constant<int, 1>(), uslot(z), HAS_T ? tslot(z) : nullptr, (fy + 1) * NP + col + NG, NP,
-              fy * RW + col + 1, RW, F);
-#pragma unroll
-      for (int v = 0; v < NV; ++v) sfy[v * NFACE + f] = F[v];
-      if (RFX && SCHEME == SCH_LF && (fy == 0 || fy == NB) && srl.slot >= 0)
-        put_face(fy ? 3 : 2, col, NDIM == 3 ? z - NG : 0, F);
+      for (int v = 0; v < NV; ++v) dst[v * NFACE] = F[v];
+      if (RFX && SCHEME == SCH_LF && srl.slot >= 0) {
+        const int pos = yd ? fy : fx, t0 = yd ? col : row;
+        if (pos == 0 || pos == NB) put_face((yd ? 2 : 0) + (pos ? 1 : 0), t0, NDIM == 3 ? z - NG : 0, F);
+      }
     };
 
     // z face of the own column between planes z and z+1; um1 = the column's state at z-1
@@ -757,7 +777,7 @@ step_kernel(StepArgsT<T> A) {
     };
 
     // work list of one barrier interval: [predictor ring cells of plane zp (if any)] then
-    // [x faces of plane zf] then [y faces of plane zf], each padded to whole warps
+    // [x faces, then y faces, of plane zf], each kind padded to whole warps
     // each warp walks its own list of warp-sized units (see the schedule above); units of a
     // kind that this interval does not run are skipped
     auto work = [&](int zp, bool do_pred, int zf, bool do_faces) {
@@ -770,12 +790,9 @@ step_kernel(StepArgsT<T> A) {
           const int q = u * 32 + lane;
           const int r = q + 1 + (q >= RW - 2) + (q >= RING - RW - 2);
           if (do_pred && q < G::NPC) predict_cell(zp, r);
-        } else if (u < NPU + NXU) {
-          const int f = (u - NPU) * 32 + lane;
-          if (do_faces && f < NFACE) do_xface(zf, f);
         } else {
-          const int f = (u - NPU - NXU) * 32 + lane;
-          if (do_faces && f < NFACE) do_yface(zf, f);
+          const int k = (u - NPU) * 32 + lane;
+          if (do_faces && k < 2 * NFACE) do_face(zf, k);
         }
       }
     };
