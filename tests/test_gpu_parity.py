@@ -756,8 +756,10 @@ def test_fp64_pressure_fix_at_low_beta(gpulib):
     """Where e_int << e (here beta = 2e-4, e_int / e = 3e-4) the FP32 pressure loses digits to
     cancellation; the fix recomputes it in FP64 from the same stored values.  It removes the
     arithmetic's share of the error but not the FP32 storage error of e itself, which
-    dominates: the FP32 form's pressure is no further from the FP64 form's with the fix than
-    without (measured 7.29e-4 vs 7.54e-4 L1 after 10 steps), and the run stays clean."""
+    dominates both: with and without the fix the FP32 form's pressure is about 7-9e-4 (L1)
+    from the FP64 form's after 10 steps, the two within the rounding noise of the kernel's
+    FP32 code (their order changed with a different FMA contraction), and the run stays
+    clean."""
     from paper_1204_5849_gb300 import MAP_FP32_FIX64, MAP_FP64
     mesh = w.uniform_mesh(3, 8, (2, 2, 2))
     U0 = w.evaluate_on_mesh(mesh, alfven_wave, ndim=3, amp=1e-3, p0=1e-4)
@@ -777,7 +779,8 @@ def test_fp64_pressure_fix_at_low_beta(gpulib):
         a.advance(dict(p, fp64_fix_tau=tau), 10)
         assert a.check() == 0
         err[tau] = float(np.abs(pres(a.read_leaves()) - P64).mean() / np.abs(P64).mean())
-    assert err[1e-2] <= err[0.0] and err[1e-2] < 2e-3, err
+    assert err[1e-2] < 2e-3 and err[0.0] < 2e-3, err
+    assert err[1e-2] <= 1.25 * err[0.0], err            # not worse than without, up to noise
 
 
 def test_fp32_alfven3d_small(gpulib):
