@@ -14,10 +14,12 @@
 // Layout: a pool block is [9][NZ][NP][NP] with NP = NB + 4 (two ghost layers); NZ = NP in
 // 3D and 1 in 2D.  One CTA owns one block at a time (grid-stride over the block list) and
 // has NB*NB threads, thread (tx,ty) owning interior column (tx+2, ty+2).  In 3D the CTA
-// marches in z keeping a rolling window in shared memory: four u planes (z-1..z+2), three
-// u~ planes (z-1..z+1) and, with resistivity, three planes of J; x- and y-face fluxes of
-// the current plane go through one shared buffer, the z-face flux of the column is carried
-// in registers from one plane to the next.  In 2D the window is the single plane.
+// marches in z keeping a rolling window in shared memory: four u planes (z..z+3, one in
+// flight), the u~ planes and, with resistivity, the J planes (z-1..z+1 for 16^3 blocks; z,
+// z+1 for 8^3, whose update carries its own column's plane z-1 values in registers); x- and
+// y-face fluxes of the current plane go through one shared buffer, the z-face flux of the
+// column is carried in registers from one plane to the next.  In 2D the window is the single
+// plane.
 #pragma once
 #include <type_traits>
 
@@ -61,7 +63,13 @@ struct Geo {
   static constexpr int S = NZ * P2;
   static constexpr int NT = NB * NB;
   static constexpr int UPL = NDIM == 3 ? 4 : 1;   // u planes z..z+2 and one in flight
-  static constexpr int WPL = NDIM == 3 ? 3 : 1;   // u~ and J planes z-1..z+1
+  // u~ and J ring planes.  3D 8^3: planes z and z+1 -- the update of plane z reads plane
+  // z-1 only at its own column, and only u~ B_z, psi and J, which are carried in registers
+  // from the previous plane; the smaller window lets 6 CTAs reside instead of 5.  3D 16^3:
+  // planes z-1..z+1 (two CTAs reside either way, and carried values would only add
+  // registers at the 128-register cap).
+  static constexpr int WPL = NDIM == 3 ? (NB == 8 ? 2 : 3) : 1;
+  static constexpr bool CARRY = NDIM == 3 && WPL == 2;
   static constexpr int RW = NB + 2;               // ring row width (padded 1..NB+2)
   static constexpr int RING = RW * RW;
   // ring cells the predictor fills: all but the four corners, which no stencil reads (the
@@ -378,7 +386,9 @@ __device__ __forceinline__ void exch_xy(bool yd, V* w) {
 // plane z+3 is fetched by bulk copies (cp.async.bulk, completion on an mbarrier) while
 // plane z is computed.  Every z-direction stencil (z faces, z derivatives of the sources)
 // runs along a thread's own column, so the column's state at z-1 is carried in registers
-// and no fourth resident plane is needed.  u~ and J live in ring layout (padded 1..NB+2).
+// and no fourth resident plane is needed.  u~ and J live in ring layout (padded 1..NB+2); for
+// 8^3 blocks two planes each, the few values of plane z-1 that the update of plane z needs
+// (its own column's u~ B_z and psi, and J) being read while plane z-1 is current and carried.
 // Per plane, the predictor of plane z+1 and the x and y faces of plane z form one
 // warp-aligned work list (they touch different slots), so a plane costs three barriers.
 
@@ -432,12 +442,12 @@ __device__ __forceinline__ void two_sum_acc(T& hi, T& lo, T h2, T l2) {
 // RFX: the mesh has coarse/fine faces with reflux on -- the kernel then records its boundary
 // face fluxes and leaves the cells the reflux pass corrects out of the fused reductions.
 // Without it none of that code exists in the kernel.
-// Resident CTAs per SM the register budget is sized for: the 3D 8^3 window (about 41 KB of
-// shared memory) lets at most 5 CTAs reside, so asking for 8 would only cap the registers
-// at 128 and spill the column state.
+// Resident CTAs per SM the register budget is sized for: the 3D 8^3 window (at most 36 KB of
+// shared memory) lets 6 CTAs reside, so asking for 8 would only cap the registers at 128 and
+// spill the column state.
 template <typename T, int NDIM, int NB>
 constexpr int step_min_ctas() {
-  return sizeof(T) != 4 ? 1 : NB == 16 ? 2 : NDIM == 3 ? 5 : 8;
+  return sizeof(T) != 4 ? 1 : NB == 16 ? 2 : NDIM == 3 ? 6 : 8;
 }
 
 template <typename T, int NDIM, int NB, int SCHEME, int LIM, int STAGE, int FLX, bool RFX>
@@ -503,8 +513,8 @@ step_kernel(StepArgsT<T> A) {
     const T eta = (T)A.eta;
 
     auto uslot = [&](int z) -> T* { return su + (size_t)(NDIM == 3 ? (z & 3) : 0) * NV * P2; };
-    auto tslot = [&](int z) -> T* { return sut + (size_t)(NDIM == 3 ? (z % 3) : 0) * NV * RING; };
-    auto jslot = [&](int z) -> T* { return sj + (size_t)(NDIM == 3 ? (z % 3) : 0) * 3 * RING; };
+    auto tslot = [&](int z) -> T* { return sut + (size_t)(NDIM == 3 ? (z % WPL) : 0) * NV * RING; };
+    auto jslot = [&](int z) -> T* { return sj + (size_t)(NDIM == 3 ? (z % WPL) : 0) * 3 * RING; };
 
     // issue the bulk copies of u plane z into its slot (thread 0 only)
     auto issue_plane = [&](int z) {
@@ -798,6 +808,8 @@ step_kernel(StepArgsT<T> A) {
     };
 
     T Fzlo[NV], uprev[NV];
+    // the own column's u~ B_z, psi and J of the previous plane (its ring slot is reused)
+    T car_bz = T(0), car_psi = T(0), car_j[3] = {T(0), T(0), T(0)};
     bool ok = true;
     const bool PRED = HAS_T || RES;
     if (tid == 0) {
@@ -854,6 +866,20 @@ step_kernel(StepArgsT<T> A) {
         work(0, false, 0, true);
       }
       __syncthreads();
+      // plane z-1's values for this plane's sources; plane z's are kept for the next, as the
+      // predictor of plane z+2 overwrites plane z's ring slot in the next interval
+      const T zm_bz = car_bz, zm_psi = car_psi;
+      const T zm_j[3] = {car_j[0], car_j[1], car_j[2]};
+      if (G::CARRY) {
+        if (HAS_T) {
+          car_bz = tslot(z)[BZ * RING + rown];
+          car_psi = tslot(z)[PSI * RING + rown];
+        }
+        if (RES) {
+#pragma unroll
+          for (int q = 0; q < 3; ++q) car_j[q] = jslot(z)[q * RING + rown];
+        }
+      }
       T Fzhi[NV];
       if (NDIM == 3) {
         if (z >= 1) face_z(z, uprev, Fzhi);                     // face between planes z, z+1
@@ -907,8 +933,15 @@ step_kernel(StepArgsT<T> A) {
       if (A.eglm) {
         if (SCHEME == SCH_LF) {
           T tm[NV], tq[NV];
+#pragma unroll
+          for (int v = 0; v < NV; ++v) tm[v] = T(0);
           if (NDIM == 3) {
-            ldw<T, RING>(tslot(z - 1), rown, tm);
+            if (G::CARRY) {
+              tm[BZ] = zm_bz;                                   // the z-1 values the sources read
+              tm[PSI] = zm_psi;
+            } else {
+              ldw<T, RING>(tslot(z - 1), rown, tm);
+            }
             ldw<T, RING>(tslot(z + 1), rown, tq);
           }
           eglm_src_col<T, NDIM>(T0, RING, RW, rown, tm, tq, dx2, s);
@@ -919,11 +952,10 @@ step_kernel(StepArgsT<T> A) {
       if (RES) {
         T jm[3] = {T(0), T(0), T(0)}, jq[3] = {T(0), T(0), T(0)};
         if (NDIM == 3) {
-          const T* j0 = jslot(z - 1);
           const T* j2 = jslot(z + 1);
 #pragma unroll
           for (int q = 0; q < 3; ++q) {
-            jm[q] = j0[q * RING + rown];
+            jm[q] = G::CARRY ? zm_j[q] : jslot(z - 1)[q * RING + rown];
             jq[q] = j2[q * RING + rown];
           }
         }
