@@ -408,10 +408,14 @@ std::string build_tree(int ndim, int nb, const std::vector<map_problem_desc>& pr
   if (!err.empty()) return err;
   // pushes: a same-level leaf copy with an affine map in every dimension is written by the
   // source block's step kernel into the destination's ghost region
+  // For a fixed region, the same-level neighbour is a translation (with periodic wrap), a
+  // bijection: each (source, direction) slot belongs to one (destination, region), so the
+  // leaves fill their slots independently, on host threads.
   t.pushes.assign((size_t)NB * 27, PushEntry{-1, {0, 0, 0}});
   t.level_has_residual.assign(t.maxlev + 1, 0);
   t.residual_by_level.assign(t.maxlev + 1, {});
-  for (int id = 0; id < n; ++id) {
+  std::vector<char> has_residual(n, 0);
+  err = for_each_leaf(n, [&](int id) -> std::string {
     bool residual = false;
     for (int rz = 0; rz < 3; ++rz)
       for (int ry = 0; ry < 3; ++ry)
@@ -426,19 +430,23 @@ std::string build_tree(int ndim, int nb, const std::vector<map_problem_desc>& pr
             // seen from the source, this block lies in direction -(r - 1)
             const int dir = (1 - (rx - 1)) + 3 * (1 - (ry - 1)) + 9 * (ndim == 3 ? 1 - (rz - 1) : 1);
             PushEntry& pe = t.pushes[(size_t)g.src * 27 + dir];
-            if (pe.dst < 0) {
-              pe.dst = id;
-              for (int d = 0; d < 3; ++d) pe.off[d] = d < ndim ? -g.a[d] : 0;
-              g.pushed = 1;
-            }
+            if (pe.dst >= 0) return fmt("internal error: two ghost regions push from one slot", t.blk_problem[id],
+                                        t.blk_level[id], &t.blk_ijk[3 * id]);
+            pe.dst = id;
+            for (int d = 0; d < 3; ++d) pe.off[d] = d < ndim ? -g.a[d] : 0;
+            g.pushed = 1;
           }
           if (!g.pushed) residual = true;
         }
-    if (residual) {
+    has_residual[id] = residual ? 1 : 0;
+    return std::string();
+  });
+  if (!err.empty()) return err;
+  for (int id = 0; id < n; ++id)
+    if (has_residual[id]) {
       t.level_has_residual[t.blk_level[id]] = 1;
       t.residual_by_level[t.blk_level[id]].push_back(id);
     }
-  }
   // reflux: the coarse leaf of every coarse/fine face gets a task naming the fine leaves
   // covering that face; both sides get a face-register slot
   t.refl.assign((size_t)NB, RefluxLeaf{-1, 0});
