@@ -446,10 +446,18 @@ def test_conduction_needs_kappa0(gpulib):
 
 @pytest.mark.parametrize("prec", [0, 1])
 @pytest.mark.parametrize("shape", [(0, 1, 1), (7, 9, 4), (64, 2, 1), (300, 7, 5)])
-def test_every_launch_shape_gives_the_same_state(gpulib, prec, shape):
-    mesh = w.uniform_mesh(3, 8, (8, 8, 4))
-    U0 = w.evaluate_on_mesh(mesh, _smooth_3d)
-    p = P(scheme="lf", limiter="vanleer")
+@pytest.mark.parametrize("geom", ["3d", "2d_mmc", "2d_weno"])
+def test_every_launch_shape_gives_the_same_state(gpulib, prec, shape, geom):
+    """Persistent grids (a CTA steps several blocks in turn) give the state of one CTA per
+    block, bitwise, in 3D and 2D."""
+    if geom == "3d":
+        mesh = w.uniform_mesh(3, 8, (8, 8, 4))
+        U0 = w.evaluate_on_mesh(mesh, _smooth_3d)
+        p = P(scheme="lf", limiter="vanleer")
+    else:
+        mesh = w.uniform_mesh(2, 16, (16, 16))
+        U0 = w.evaluate_on_mesh(mesh, _smooth_2d)
+        p = P(scheme="mmc" if geom == "2d_mmc" else "weno", limiter="minmod")
     a = pool_for(mesh, prec, U0)
     b = pool_for(mesh, prec, U0)
     a.set_launch(*shape)
