@@ -308,6 +308,22 @@ long long map_kernel_launches(const map_pool* pool);
 /* Last error text of the pool (or of the last failed create when pool is NULL). */
 const char* map_last_error(const map_pool* pool);
 
+/* (No counterpart in the paper.)  Host-only forms of the block-tree logic, without a pool
+ * or a GPU, for checking a leaf list before it reaches one.  ndim, nb and problems[n_problems]
+ * as in map_pool_desc; leaves[n] as in map_set_tree; msg[msg_cap] receives the reason of a
+ * rejection (empty on success; NULL allowed).
+ * map_check_leaves: the validation map_set_tree performs (leaves inside their domains, no
+ *   duplicates or nested leaves, every domain covered, complete parents, 2:1 over faces,
+ *   edges and corners; Sec. 4.1).  MAP_OK or MAP_EINVAL.
+ * map_plan_leaves: the regrid decision of map_plan_regrid (Sec. 4.5) for flags[n] on that
+ *   leaf list.  out[cap] receives the new list, *n_out its length (MAP_ENOMEM when cap is too
+ *   small); MAP_EINVAL if the list itself is invalid. */
+int map_check_leaves(int ndim, int nb, const map_problem_desc* problems, int n_problems,
+                     const map_block_desc* leaves, int n, char* msg, int msg_cap);
+int map_plan_leaves(int ndim, int nb, const map_problem_desc* problems, int n_problems,
+                    const map_block_desc* leaves, int n, const int8_t* flags, int max_level,
+                    map_block_desc* out, int cap, int* n_out, char* msg, int msg_cap);
+
 /* Allocation-free CFL reduction (no counterpart in the paper; an interface addition).
  *
  * For callers that cannot allocate device memory: code that runs inside a CUDA-graph

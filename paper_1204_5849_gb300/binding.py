@@ -113,6 +113,11 @@ _SIGS = {
     "map_get_leaves": (C.c_int, [C.c_void_p, C.POINTER(map_block_desc), C.c_int, C.POINTER(C.c_int)]),
     "map_cfl_dt_noalloc": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p,
                                      C.POINTER(map_params), C.c_void_p, C.c_void_p]),
+    "map_check_leaves": (C.c_int, [C.c_int, C.c_int, C.c_void_p, C.c_int, C.POINTER(map_block_desc), C.c_int,
+                                   C.c_char_p, C.c_int]),
+    "map_plan_leaves": (C.c_int, [C.c_int, C.c_int, C.c_void_p, C.c_int, C.POINTER(map_block_desc), C.c_int,
+                                  C.c_void_p, C.c_int, C.POINTER(map_block_desc), C.c_int, C.POINTER(C.c_int),
+                                  C.c_char_p, C.c_int]),
 }
 
 NOALLOC_MAX_BLOCKS = 65536
@@ -129,6 +134,40 @@ def cfl_dt_noalloc(u_dev_ptr: int, precision: int, ndim: int, nb: int, nblocks: 
     if rc != MAP_OK:
         raise MapError(rc, "map_cfl_dt_noalloc", L.map_last_error(None).decode())
     return out
+
+
+def _problems(mesh) -> "C.Array":
+    probs = (map_problem_desc * len(mesh.problems))()
+    for q, pr in enumerate(mesh.problems):
+        for d in range(3):
+            probs[q].nbase[d] = int(pr.nbase[d])
+            probs[q].lo[d] = float(pr.lo[d])
+            probs[q].hi[d] = float(pr.hi[d])
+            probs[q].bc[d][0] = int(pr.bc[d][0])
+            probs[q].bc[d][1] = int(pr.bc[d][1])
+    return probs
+
+
+def check_leaves(mesh) -> str:
+    """map_check_leaves (host only, no GPU): '' if the leaf list is a valid tree, else why not."""
+    msg = C.create_string_buffer(256)
+    load().map_check_leaves(mesh.ndim, mesh.nb, _problems(mesh), len(mesh.problems), _leaves(mesh),
+                            mesh.nleaves, msg, 256)
+    return msg.value.decode()
+
+
+def plan_leaves(mesh, flags: np.ndarray, max_level: int) -> np.ndarray:
+    """map_plan_leaves (host only, no GPU): the new leaf list (n, 5) of map_plan_regrid."""
+    f = np.ascontiguousarray(flags, dtype=np.int8)
+    cap = int(mesh.nleaves * (8 if mesh.ndim == 3 else 4))
+    arr = (map_block_desc * cap)()
+    n = C.c_int(0)
+    msg = C.create_string_buffer(256)
+    rc = load().map_plan_leaves(mesh.ndim, mesh.nb, _problems(mesh), len(mesh.problems), _leaves(mesh),
+                                mesh.nleaves, _ptr(f), int(max_level), arr, cap, C.byref(n), msg, 256)
+    if rc != MAP_OK:
+        raise MapError(rc, "map_plan_leaves", msg.value.decode())
+    return _leaves_to_array(arr, n.value)
 
 
 def load(path: str = LIB_PATH):
@@ -199,14 +238,7 @@ class Pool:
         self.precision = precision
         n_par_est = mesh.nleaves // (3 if mesh.ndim == 2 else 7) + 4 * len(mesh.problems) + 64
         self.max_blocks = int(max_blocks or (2 * (mesh.nleaves + n_par_est)))
-        probs = (map_problem_desc * len(mesh.problems))()
-        for q, pr in enumerate(mesh.problems):
-            for d in range(3):
-                probs[q].nbase[d] = int(pr.nbase[d])
-                probs[q].lo[d] = float(pr.lo[d])
-                probs[q].hi[d] = float(pr.hi[d])
-                probs[q].bc[d][0] = int(pr.bc[d][0])
-                probs[q].bc[d][1] = int(pr.bc[d][1])
+        probs = _problems(mesh)
         self._probs = probs
         desc = map_pool_desc(mesh.ndim, mesh.nb, 2, precision, self.max_blocks, len(mesh.problems),
                              probs, C.c_void_p(ext_buffer or 0), ext_bytes)

@@ -1135,6 +1135,58 @@ int map_get_speeds(map_pool* pool, double* out) {
   return MAP_OK;
 }
 
+static void put_msg(char* msg, int cap, const std::string& why) {
+  if (!msg || cap <= 0) return;
+  const size_t k = why.size() < (size_t)(cap - 1) ? why.size() : (size_t)(cap - 1);
+  memcpy(msg, why.data(), k);
+  msg[k] = 0;
+}
+
+static std::string host_tree(int ndim, int nb, const map_problem_desc* problems, int np,
+                             const map_block_desc* leaves, int n, HostTree& t, std::vector<map_problem_desc>& probs) {
+  if (ndim != 2 && ndim != 3) return "ndim must be 2 or 3";
+  if (nb != 8 && nb != 16) return "nb must be 8 or 16";
+  if (!problems || np <= 0) return "no problems";
+  if (!leaves || n <= 0) return "null or empty leaf list";
+  probs.assign(problems, problems + np);
+  return build_tree(ndim, nb, probs, leaves, n, t);
+}
+
+int map_check_leaves(int ndim, int nb, const map_problem_desc* problems, int n_problems,
+                     const map_block_desc* leaves, int n, char* msg, int msg_cap) {
+  HostTree t;
+  std::vector<map_problem_desc> probs;
+  const std::string why = host_tree(ndim, nb, problems, n_problems, leaves, n, t, probs);
+  put_msg(msg, msg_cap, why);
+  return why.empty() ? MAP_OK : MAP_EINVAL;
+}
+
+int map_plan_leaves(int ndim, int nb, const map_problem_desc* problems, int n_problems,
+                    const map_block_desc* leaves, int n, const int8_t* flags, int max_level,
+                    map_block_desc* out, int cap, int* n_out, char* msg, int msg_cap) {
+  if (!flags || !n_out) {
+    put_msg(msg, msg_cap, "null argument");
+    return MAP_EINVAL;
+  }
+  HostTree t;
+  std::vector<map_problem_desc> probs;
+  std::string why = host_tree(ndim, nb, problems, n_problems, leaves, n, t, probs);
+  std::vector<map_block_desc> plan;
+  if (why.empty()) why = plan_regrid(t, probs, flags, max_level, plan);
+  if (!why.empty()) {
+    put_msg(msg, msg_cap, why);
+    return MAP_EINVAL;
+  }
+  *n_out = (int)plan.size();
+  if ((int)plan.size() > cap || !out) {
+    put_msg(msg, msg_cap, "output array too small for the new leaf list");
+    return MAP_ENOMEM;
+  }
+  memcpy(out, plan.data(), plan.size() * sizeof(map_block_desc));
+  put_msg(msg, msg_cap, "");
+  return MAP_OK;
+}
+
 long long map_kernel_launches(const map_pool* pool) { return pool ? pool->launches : 0; }
 
 const char* map_last_error(const map_pool* pool) {
