@@ -180,9 +180,29 @@ def cpu_baseline(params, seconds: float = 10.0):
         n += 1
     dt = time.perf_counter() - t0
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    return {"value": mesh.ncells * n / dt, "unit": METRIC, "cores": cores, "kind": "oracle",
-            "sample": f"{n} steps of a 64^3 periodic box (4^3 blocks of 16^3) of the same wave, "
-                      f"FP64 oracle, OpenMP over blocks, {dt:.1f} s"}
+    out = {"value": mesh.ncells * n / dt, "unit": METRIC, "cores": cores, "kind": "oracle",
+           "sample": f"{n} steps of a 64^3 periodic box (4^3 blocks of 16^3) of the same wave, "
+                     f"FP64 oracle, OpenMP over blocks, {dt:.1f} s"}
+    # the same oracle on one host thread (the OpenMP runtime's thread count, restored after)
+    import ctypes
+    try:
+        gomp = ctypes.CDLL("libgomp.so.1")
+    except OSError:
+        gomp = None
+    if gomp is not None:
+        nmax = gomp.omp_get_max_threads()
+        gomp.omp_set_num_threads(1)
+        try:
+            n1, t1 = 0, time.perf_counter()
+            while time.perf_counter() - t1 < seconds / 2:
+                orc.advance(params, 1)
+                n1 += 1
+            d1 = time.perf_counter() - t1
+        finally:
+            gomp.omp_set_num_threads(nmax)
+        out["single_thread"] = {"value": mesh.ncells * n1 / d1, "unit": METRIC, "cores": 1,
+                                "sample": f"{n1} steps of the same box on one thread, {d1:.1f} s"}
+    return out
 
 
 def run_reference(args):
