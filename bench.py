@@ -404,8 +404,15 @@ def main():
     main_prec = MAP_FP64 if (args.quick and args.prec == 64) else MAP_FP32_FIX64
     pool = Pool(mesh, main_prec, max_blocks=mesh.nleaves, stream=sptr)
     pool.write_leaves(U0)
-    # launch shape of the step kernel picked by the autotuner (untimed; the state is kept)
-    tune = pool.autotune(params, reps=3) if not args.no_tune else None
+    # launch shape of the step kernel picked by the autotuner (untimed; the state is kept);
+    # should a trial fail, the pool keeps its default shape and the line says why
+    tune = None
+    if not args.no_tune:
+        try:
+            tune = pool.autotune(params, reps=3)
+        except Exception as e:                               # MapError: a trial launch failed
+            pool.set_launch(0, 0, 0)
+            tune = {"error": str(e)[:200], "grid": 0, "w_pred": 0, "w_face": 0}
     for _ in range(args.warmup):
         pool.advance(params, 1)
     clocks = ClockSampler(local)
