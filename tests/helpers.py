@@ -58,3 +58,17 @@ def assemble_uniform(mesh, U: np.ndarray, var: int) -> np.ndarray:
     for b, (p, lv, i, j, k) in enumerate(mesh.leaves):
         out[k * bz:(k + 1) * bz, j * nb:(j + 1) * nb, i * nb:(i + 1) * nb] = U[b, var]
     return out
+
+
+def quadratic_estimate(a, b, c, h, eps, refine, X, Y):
+    """The Sec. 4.5 estimator of rho = a + b x^2 + c y^2 at cell centres (X, Y), in closed
+    form: the three-point first difference is 4 b x h (4 c y h) and the second difference
+    2 b h^2 (2 c h^2) exactly, so |du| = sqrt(3)/2 * 4 h sqrt(b^2 x^2 + c^2 y^2) and
+    |d2u| = 2 h^2 sqrt(b^2 + c^2).  Returns the first-difference part and the whole."""
+    B, F = refine["bias"], refine["filter"]
+    u = a + b * X * X + c * Y * Y
+    du = math.sqrt(3.0) / 2.0 * 4.0 * h * np.sqrt(b * b * X * X + c * c * Y * Y)
+    d2u = 2.0 * h * h * math.sqrt(b * b + c * c)
+    first = B * du / (np.abs(u) + eps)
+    second = (1.0 - B) * d2u / (du + F * (np.abs(u) + eps))
+    return first, first + second

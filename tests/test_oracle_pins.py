@@ -18,7 +18,7 @@ from workloads.problems import (advection_2d, alfven_wave, brio_wu, conserved_fr
                                 divb_bump, ensemble_problem, field_loop, orszag_tang, uniform_state)
 from oracle import Oracle
 from oracle import oracle as O
-from tests.helpers import assemble_uniform, l1, run_to_time
+from tests.helpers import assemble_uniform, l1, quadratic_estimate, run_to_time
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 SCHEMES = ("mmc", "lf", "weno")
@@ -570,6 +570,64 @@ def test_estimator_constant_and_linear():
             xlo = -0.5 + i * 8 * h
             want = 0.6 * (math.sqrt(3) / 2) * (2 * g * h) / (2.0 + g * (xlo - h / 2) + 1e-12)
             assert est[b] == pytest.approx(want, rel=1e-12)
+
+
+def test_estimator_second_difference_term():
+    """rho = a + b x^2 + c y^2 has the same nonzero second difference at every cell, so the
+    (1-B)|d2u| / (|du| + F(|u|+eps)) term is pinned against its closed form: a dropped (1-B),
+    eps outside the F factor (eps is 0.3 here, comparable to |u|), or |d2x| + |d2y| in place
+    of sqrt(d2x^2 + d2y^2) each move the block maxima by far more than the tolerance."""
+    a, b, c, eps = 0.2, 40.0, 20.0, 0.3
+    refine = dict(vars=("rho",), thr=0.36, coarsen=0.1, max_level=3, bias=0.6, filter=0.05,
+                  eps_rho=eps)
+
+    def quad(X, Y, Z, **_):
+        return conserved_from_primitive(a + b * X * X + c * Y * Y, 0, 0, 0, 0, 0, 0, 1.0, 5 / 3)
+
+    m = w.uniform_mesh(2, 8, (4, 4), lo=(-0.5, -0.5, 0), hi=(0.5, 0.5, 1), bc=w.mesh.OUTFLOW)
+    o = Oracle(m, w.evaluate_on_mesh(m, quad))
+    o.fill_ghosts()
+    f, est = o.flags(P(), refine)
+    h = 1.0 / 32
+    # the estimator runs over the interior and the first ghost ring; in the inner blocks
+    # (away from the outflow boundary) every cell there and its neighbours hold the quadratic
+    k = np.arange(-1, 9) + 0.5
+    checked = 0
+    for blk, (_, lv, i, j, _k) in enumerate(m.leaves):
+        if i not in (1, 2) or j not in (1, 2):
+            continue
+        X, Y = np.meshgrid(-0.5 + (i * 8 + k) * h, -0.5 + (j * 8 + k) * h)
+        first, full = quadratic_estimate(a, b, c, h, eps, refine, X, Y)
+        assert est[blk] == pytest.approx(float(full.max()), rel=1e-9)
+        # the flag decision rests on the second-difference term: the first-difference term
+        # alone stays below the threshold, the whole estimator exceeds it
+        assert float(first.max()) < 0.9 * refine["thr"] < 1.1 * refine["thr"] < float(full.max())
+        assert f[blk] == 1
+        checked += 1
+    assert checked == 4
+
+
+def test_estimator_second_difference_mutations_detected():
+    """The closed form above separates the plausible misreadings of the Sec. 4.5 estimator by
+    more than the tolerance used there (so each would fail that test)."""
+    a, b, c, eps, h = 0.2, 40.0, 20.0, 0.3, 1.0 / 32
+    r = dict(bias=0.6, filter=0.05)
+    k = np.arange(-1, 9) + 0.5
+    X, Y = np.meshgrid(-0.5 + (8 + k) * h, -0.5 + (8 + k) * h)
+    first, full = quadratic_estimate(a, b, c, h, eps, r, X, Y)
+    u = a + b * X * X + c * Y * Y
+    du = math.sqrt(3.0) / 2.0 * 4.0 * h * np.sqrt(b * b * X * X + c * c * Y * Y)
+    d2 = 2.0 * h * h * math.sqrt(b * b + c * c)
+    d2_abs = 2.0 * h * h * (abs(b) + abs(c))
+    variants = {
+        "no (1-B)": first + d2 / (du + r["filter"] * (u + eps)),
+        "eps outside F": first + (1 - r["bias"]) * d2 / (du + r["filter"] * u + eps),
+        "|d2x|+|d2y|": first + (1 - r["bias"]) * d2_abs / (du + r["filter"] * (u + eps)),
+        "no sqrt(3)/2 in the denominator": first + (1 - r["bias"]) * d2 / (du / (math.sqrt(3) / 2)
+                                                                           + r["filter"] * (u + eps)),
+    }
+    for name, v in variants.items():
+        assert abs(float(v.max()) / float(full.max()) - 1.0) > 1e-3, name
 
 
 def test_estimator_flags_refine_and_coarsen():
