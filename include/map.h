@@ -99,7 +99,8 @@ typedef struct {
   int scheme;         /* MAP_MMC, MAP_LF, MAP_WENO */
   int limiter;        /* MAP_MINMOD, MAP_VANLEER */
   double dt_override; /* > 0: use this dt instead of the CFL dt */
-  double fp64_fix_tau;/* FP32 pools: recompute p in FP64 where e_int < tau * e */
+  double fp64_fix_tau;/* FP32 pools: recompute p in FP64 where e_int < tau * e; <= 0: off
+                         (every p recovered in FP32, negative ones included) */
   int reflux;         /* 1: at every coarse/fine face the coarse leaf's flux is replaced by
                          the mean of the fine fluxes covering it (Sec. 4.2, boundary step
                          (2)), so the face carries one flux on both sides; 0: off */
@@ -194,7 +195,8 @@ int map_advance(map_pool* pool, const map_params* p, int nsteps);
 
 /* Device error word accumulated by the steps since the last check (rho <= 0, p < 0,
  * non-finite, a bounded wait for a plane copy that gave up), read and cleared;
- * synchronises.  MAP_OK, MAP_ETIMEOUT, MAP_ENONFINITE or MAP_ENEGPRES. */
+ * synchronises the pool stream and the pool's copy streams (so the asynchronous host
+ * copies are complete on return).  MAP_OK, MAP_ETIMEOUT, MAP_ENONFINITE or MAP_ENEGPRES. */
 int map_check(map_pool* pool);
 
 /* Refinement flags (Sec. 4.5): per leaf +1 refine, 0 keep, -1 may coarsen, from the
@@ -292,6 +294,24 @@ int map_write_leaves_async(map_pool* pool, const double* u);
  * nearest; an FP64 pool takes the FP32 values exactly. */
 int map_write_leaves_async_f32(map_pool* pool, const float* u);
 
+/* (No counterpart in the paper.)  Asynchronous form of map_read_leaves: the current state's
+ * leaf interiors, in the layout of map_read_leaves, are packed on the pool stream (after
+ * everything enqueued before the call) into one of two device staging buffers and copied to
+ * u_out on the pool's read copy stream, so the copy overlaps the steps enqueued after it and
+ * runs in the other direction of the link from map_write_leaves_async.  u_out (pinned, for
+ * a truly asynchronous copy) holds the state once map_check has returned (it synchronises
+ * the pool's copy streams) or the device has been synchronised; it must not be read or
+ * reused before.  A third call waits on the device for the copy of the first to finish
+ * before reusing its staging buffer.  Allocates the two buffers (n_leaves * 9 * nb^ndim
+ * values of the host layout's type each) on first use.  Errors: MAP_EINVAL, MAP_ESTATE,
+ * MAP_ECUDA. */
+int map_read_leaves_async(map_pool* pool, double* u_out);
+
+/* (No counterpart in the paper.)  map_read_leaves_async into an FP32 host layout (same
+ * shape): half the bytes.  An MAP_FP32_FIX64 pool's values are copied exactly; an FP64
+ * pool's are rounded to nearest. */
+int map_read_leaves_async_f32(map_pool* pool, float* u_out);
+
 /* (No counterpart in the paper.)  Asynchronous map_get_speeds: out[n_problems][5] is
  * written when the pool stream reaches
  * this point (pinned memory for a truly asynchronous copy); no synchronisation. */
@@ -326,8 +346,7 @@ int map_plan_leaves(int ndim, int nb, const map_problem_desc* problems, int n_pr
 
 /* Allocation-free CFL reduction (no counterpart in the paper; an interface addition).
  *
- * For callers that cannot allocate device memory: code that runs inside a CUDA-graph
- * capture and must not add allocation nodes, embedders whose device memory belongs to
+ * For callers that cannot allocate device memory: embedders whose device memory belongs to
  * another allocator (a framework's caching allocator, a fixed arena) and who forbid
  * cudaMalloc/cudaFree, and real-time loops that cannot afford the device synchronisation
  * cudaMalloc/cudaFree may cause.  Unlike map_cfl_dt it needs no pool: the caller passes
@@ -336,17 +355,26 @@ int map_plan_leaves(int ndim, int nb, const map_problem_desc* problems, int n_pr
  * u_dev: device pointer to nblocks blocks of one problem with uniform spacing dx[ndim],
  *   in the pool layout [block][9][nz+4][nb+4][nb+4] (nz = nb in 3D, the z extent is 1 in
  *   2D), FP64 (precision MAP_FP64) or FP32 (MAP_FP32_FIX64); ghost cells are not read.
+ * p: checked as map_cfl_dt checks it (MAP_EINVAL on the same bad values).  Thermal
+ *   conduction is not covered: p->conduction other than MAP_COND_OFF is rejected with
+ *   MAP_EINVAL, because its time-step bound (Sec. 3.6) needs a second reduction.
  * out (host): dt, c_h, c_p, psi damping factor, alpha_g -- the same quantities, from the
- *   same formulas, as map_cfl_dt and map_get_speeds for one problem.
+ *   same formulas, as map_cfl_dt and map_get_speeds for one problem without conduction.  A
+ *   NaN anywhere in the interior makes alpha_g NaN and the call return MAP_ENONFINITE, as
+ *   map_cfl_dt does.
  * The per-block partial maxima live in one file-scope static device array sized for
  *   MAP_NOALLOC_MAX_BLOCKS blocks (512 KB); every GPU that loads the library holds it until
  *   the process exits.  nblocks above that maximum is rejected with MAP_EINVAL (text in
  *   map_last_error(NULL)).
  * The first call on a device looks up the array's device address (cudaGetSymbolAddress)
- *   with that device current; make that first call before any stream capture.
+ *   with that device current and keeps it for the process; make that first call before any
+ *   stream capture.  A device reset (cudaDeviceReset) invalidates the kept address: do not
+ *   call this entry point on a device after resetting it.  Host threads may call it
+ *   concurrently (the kept addresses are atomic), subject to the race below.
  * All calls share the array: calls whose kernels overlap on the GPU (different streams,
  *   no ordering between them) race and give wrong results.  Runs on `stream` (a
- *   cudaStream_t, NULL = legacy default stream) and synchronises it.
+ *   cudaStream_t, NULL = legacy default stream), copies the five results to `out` and
+ *   synchronises the stream before it returns.
  * Errors: MAP_EINVAL, MAP_ECUDA, MAP_ENONFINITE (dt not finite and positive). */
 #define MAP_NOALLOC_MAX_BLOCKS 65536
 int map_cfl_dt_noalloc(const void* u_dev, int precision, int ndim, int nb, int nblocks,

@@ -99,6 +99,8 @@ _SIGS = {
     "map_write_leaves_async": (C.c_int, [C.c_void_p, C.c_void_p]),
     "map_write_leaves_async_f32": (C.c_int, [C.c_void_p, C.c_void_p]),
     "map_get_speeds_async": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "map_read_leaves_async": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "map_read_leaves_async_f32": (C.c_int, [C.c_void_p, C.c_void_p]),
     "map_autotune": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
     "map_set_launch": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int]),
     "map_test_fail_waits": (C.c_int, [C.c_void_p, C.c_int]),
@@ -306,6 +308,14 @@ class Pool:
     def write_leaves_async_f32_ptr(self, host_ptr: int):
         """Asynchronous write from an FP32 host layout (see map_write_leaves_async_f32)."""
         self._ck(load().map_write_leaves_async_f32(self.h, C.c_void_p(host_ptr)), "map_write_leaves_async_f32")
+
+    def read_leaves_async_ptr(self, host_ptr: int):
+        """Asynchronous read of the state into host memory (see map_read_leaves_async)."""
+        self._ck(load().map_read_leaves_async(self.h, C.c_void_p(host_ptr)), "map_read_leaves_async")
+
+    def read_leaves_async_f32_ptr(self, host_ptr: int):
+        """Asynchronous read into an FP32 host layout (see map_read_leaves_async_f32)."""
+        self._ck(load().map_read_leaves_async_f32(self.h, C.c_void_p(host_ptr)), "map_read_leaves_async_f32")
 
     def speeds_async_ptr(self, host_ptr: int):
         """Asynchronous read of [n_problems][5] speeds into host memory at host_ptr."""

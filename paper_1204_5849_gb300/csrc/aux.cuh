@@ -140,6 +140,13 @@ __global__ void __launch_bounds__(256) restrict_kernel(T* __restrict__ u, const 
   }
 }
 
+// Maximum that keeps a NaN from either side (fmax drops it): a NaN cell anywhere makes the
+// reduced signal speed NaN, so the time step built from it is rejected.
+template <typename T>
+__device__ __forceinline__ T nan_max(T a, T b) {
+  return (a != a) ? a : ((b != b) ? b : fmax(a, b));
+}
+
 template <typename T>
 __device__ __forceinline__ void load_global(const T* b, size_t S, int c, T* w) {
 #pragma unroll
@@ -175,23 +182,19 @@ __global__ void __launch_bounds__(256) cfl_kernel(const T* __restrict__ u, const
       load_global<T>(ub, S, cc, w);
       const T p = pressure<T>(w, P);
       T a = alpha_p<T, 0>(w, p, P);
-      a = fmax(a, alpha_p<T, 1>(w, p, P));
-      if (NDIM == 3) a = fmax(a, alpha_p<T, 2>(w, p, P));
-      if (a != a) am = a;            // NaN wins
-      else if (!(am != am)) am = fmax(am, a);
+      a = nan_max<T>(a, alpha_p<T, 1>(w, p, P));
+      if (NDIM == 3) a = nan_max<T>(a, alpha_p<T, 2>(w, p, P));
+      am = nan_max<T>(am, a);
       if (cond) {
         // kappa T / p read as kappa / rho, kappa = kappa0 T^(5/2), T = max(p, 0) / rho
         const T tt = (p < T(0) ? T(0) : p) / w[RHO];
         const T kr = kap0 * (tt * tt * sqrt(tt)) / w[RHO];
-        if (kr != kr) km = kr;
-        else if (!(km != km)) km = fmax(km, kr);
+        km = nan_max<T>(km, kr);
       }
     }
     for (int o = 16; o > 0; o >>= 1) {
-      const T t = __shfl_xor_sync(0xffffffffu, am, o);
-      am = (t != t) ? t : fmax(am, t);
-      const T t2 = __shfl_xor_sync(0xffffffffu, km, o);
-      km = (t2 != t2) ? t2 : fmax(km, t2);
+      am = nan_max<T>(am, __shfl_xor_sync(0xffffffffu, am, o));
+      km = nan_max<T>(km, __shfl_xor_sync(0xffffffffu, km, o));
     }
     if ((threadIdx.x & 31) == 0) {
       red[threadIdx.x >> 5] = (double)am;
@@ -201,8 +204,8 @@ __global__ void __launch_bounds__(256) cfl_kernel(const T* __restrict__ u, const
     if (threadIdx.x == 0) {
       double a = 0.0, kk = 0.0;
       for (int q = 0; q < (int)(blockDim.x + 31) / 32; ++q) {
-        a = (red[q] != red[q]) ? red[q] : fmax(a, red[q]);
-        kk = (redk[q] != redk[q]) ? redk[q] : fmax(kk, redk[q]);
+        a = nan_max<double>(a, red[q]);
+        kk = nan_max<double>(kk, redk[q]);
       }
       atomicMax(&dyn[geo[blk].problem].alpha_bits, (unsigned long long)__double_as_longlong(a));
       if (kappa0 > 0.0) atomicMax(&dyn[geo[blk].problem].kmax_bits, (unsigned long long)__double_as_longlong(kk));
@@ -235,20 +238,16 @@ __global__ void __launch_bounds__(256) cfl_partial_kernel(const T* __restrict__ 
       load_global<T>(ub, S, cc, w);
       const T p = pressure<T>(w, P);
       T a = alpha_p<T, 0>(w, p, P);
-      a = fmax(a, alpha_p<T, 1>(w, p, P));
-      if (NDIM == 3) a = fmax(a, alpha_p<T, 2>(w, p, P));
-      if (a != a) am = a;
-      else if (!(am != am)) am = fmax(am, a);
+      a = nan_max<T>(a, alpha_p<T, 1>(w, p, P));
+      if (NDIM == 3) a = nan_max<T>(a, alpha_p<T, 2>(w, p, P));
+      am = nan_max<T>(am, a);
     }
-    for (int o = 16; o > 0; o >>= 1) {
-      const T t = __shfl_xor_sync(0xffffffffu, am, o);
-      am = (t != t) ? t : ((am != am) ? am : fmax(am, t));
-    }
+    for (int o = 16; o > 0; o >>= 1) am = nan_max<T>(am, __shfl_xor_sync(0xffffffffu, am, o));
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = am;
     __syncthreads();
     if (threadIdx.x == 0) {
       double a = 0.0;
-      for (int q = 0; q < (int)(blockDim.x + 31) / 32; ++q) a = (red[q] != red[q] || a != a) ? (a != a ? a : red[q]) : fmax(a, red[q]);
+      for (int q = 0; q < (int)(blockDim.x + 31) / 32; ++q) a = nan_max<double>(a, red[q]);
       partial[blk] = a;     // every slot < nblocks is written before it is read
     }
     __syncthreads();
@@ -270,13 +269,17 @@ __global__ void __launch_bounds__(256) flags_kernel(FlagLaunch L) {
   const R gm1 = (R)(L.gamma - 1.0);
   const R bias = (R)L.r.bias, filt = (R)L.r.filter;
   const R half_sqrt3 = (R)(1.7320508075688772 / 2.0);
+  // the pool's pressure recovery (FP32 pools: with its FP64 fallback at low e_int / e)
+  Phys<T> PP;
+  PP.gamma = (T)L.gamma;
+  PP.gm1 = (T)gm1;
+  PP.ch = T(0);
+  PP.tau = (T)L.tau;
   auto pres = [&](const T* ub, int c) -> R {
     R w[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) w[v] = (R)ub[(size_t)v * S + c];
-    R m2 = w[MX] * w[MX] + w[MY] * w[MY] + w[MZ] * w[MZ];
-    R b2 = w[BX] * w[BX] + w[BY] * w[BY] + w[BZ] * w[BZ];
-    return gm1 * (w[EN] - R(0.5) * m2 / w[RHO] - R(0.5) * b2);
+    return pressure<T>(w, PP);
   };
   const int offs[3] = {1, NP, P2};
   for (int bi = blockIdx.x; bi < L.nblocks; bi += gridDim.x) {
@@ -388,12 +391,13 @@ __global__ void __launch_bounds__(256) pack_kernel(PackLaunch L) {
     const int blk = L.blocks[bi];
     T* ub = u + (size_t)blk * NV * S;
     double* hb = L.host_layout + (size_t)bi * NV * NI;
-    const float* hf = reinterpret_cast<const float*>(L.host_layout) + (size_t)bi * NV * NI;
+    float* hf = reinterpret_cast<float*>(L.host_layout) + (size_t)bi * NV * NI;
     for (int q = threadIdx.x; q < NV * NI; q += blockDim.x) {
       const int v = q / NI, c = q % NI;
       const int i = c % NB, j = (c / NB) % NB, k = NDIM == 3 ? c / (NB * NB) : 0;
       const int cc = ((NDIM == 3 ? k + NG : 0) * NP + j + NG) * NP + i + NG;
       if (L.to_pool) ub[(size_t)v * S + cc] = L.staging_f32 ? (T)hf[q] : (T)hb[q];
+      else if (L.staging_f32) hf[q] = (float)ub[(size_t)v * S + cc];
       else hb[q] = (double)ub[(size_t)v * S + cc];
     }
   }

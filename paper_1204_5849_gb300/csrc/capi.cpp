@@ -56,6 +56,13 @@ struct map_pool {
   cudaStream_t copy_stream = nullptr;
   cudaEvent_t copied[2] = {nullptr, nullptr}, consumed[2] = {nullptr, nullptr};
   int wslot = 0;
+  // asynchronous host reads: the pack into one of two read staging buffers runs on the pool
+  // stream, the copy out on a second copy stream (the other direction of the link)
+  void* rstaging[2] = {nullptr, nullptr};
+  size_t rstaging_bytes = 0;
+  cudaStream_t rcopy_stream = nullptr;
+  cudaEvent_t rpacked[2] = {nullptr, nullptr}, rcopied[2] = {nullptr, nullptr};
+  int rslot = 0;
   size_t staging_elems = 0;
   int8_t* flags = nullptr;
   double* est = nullptr;
@@ -220,6 +227,15 @@ int map_destroy_pool(map_pool* pool) {
       cudaEventDestroy(pool->consumed[k]);
     }
     cudaStreamDestroy(pool->copy_stream);
+  }
+  if (pool->rcopy_stream) {
+    cudaStreamSynchronize(pool->rcopy_stream);
+    for (int k = 0; k < 2; ++k) {
+      cudaFree(pool->rstaging[k]);
+      cudaEventDestroy(pool->rpacked[k]);
+      cudaEventDestroy(pool->rcopied[k]);
+    }
+    cudaStreamDestroy(pool->rcopy_stream);
   }
   cudaFree(pool->flags);
   cudaFree(pool->est);
@@ -423,6 +439,47 @@ int map_write_leaves_async(map_pool* pool, const double* u) { return write_leave
 
 int map_write_leaves_async_f32(map_pool* pool, const float* u) { return write_leaves_async(pool, u, 1); }
 
+// pack the current state into read staging buffer k (pool stream), then copy it to the host
+// on the read copy stream; the next pack into buffer k waits for that copy
+static int read_leaves_async(map_pool* pool, void* u, int f32) {
+  if (!pool || !u) return fail(pool, MAP_EINVAL, "null argument");
+  if (!pool->have_tree) return fail(pool, MAP_ESTATE, "no tree");
+  const int n = pool->tree.nleaves;
+  const size_t bytes = (size_t)n * interior_elems(pool) * (f32 ? sizeof(float) : sizeof(double));
+  if (!pool->rcopy_stream) {
+    CK(cudaStreamCreateWithFlags(&pool->rcopy_stream, cudaStreamNonBlocking));
+    for (int k = 0; k < 2; ++k) {
+      CK(cudaEventCreateWithFlags(&pool->rpacked[k], cudaEventDisableTiming));
+      CK(cudaEventCreateWithFlags(&pool->rcopied[k], cudaEventDisableTiming));
+      CK(cudaEventRecord(pool->rcopied[k], pool->rcopy_stream));
+    }
+  }
+  if (bytes > pool->rstaging_bytes) {
+    CK(cudaStreamSynchronize(pool->rcopy_stream));
+    CK(cudaStreamSynchronize(pool->stream));
+    for (int k = 0; k < 2; ++k) {
+      cudaFree(pool->rstaging[k]);
+      pool->rstaging[k] = nullptr;
+      CK(cudaMalloc(&pool->rstaging[k], bytes));
+    }
+    pool->rstaging_bytes = bytes;
+  }
+  const int k = pool->rslot;
+  pool->rslot ^= 1;
+  CK(cudaStreamWaitEvent(pool->stream, pool->rcopied[k], 0));
+  int rc = pack(pool, pool->dt.leaf_ids, n, 0, (double*)pool->rstaging[k], f32);
+  if (rc) return rc;
+  CK(cudaEventRecord(pool->rpacked[k], pool->stream));
+  CK(cudaStreamWaitEvent(pool->rcopy_stream, pool->rpacked[k], 0));
+  CK(cudaMemcpyAsync(u, pool->rstaging[k], bytes, cudaMemcpyDeviceToHost, pool->rcopy_stream));
+  CK(cudaEventRecord(pool->rcopied[k], pool->rcopy_stream));
+  return MAP_OK;
+}
+
+int map_read_leaves_async(map_pool* pool, double* u) { return read_leaves_async(pool, u, 0); }
+
+int map_read_leaves_async_f32(map_pool* pool, float* u) { return read_leaves_async(pool, u, 1); }
+
 int map_read_leaves(map_pool* pool, double* u) {
   if (!pool || !u) return fail(pool, MAP_EINVAL, "null argument");
   if (!pool->have_tree) return fail(pool, MAP_ESTATE, "no tree");
@@ -546,19 +603,37 @@ static bool params_equal(const map_params& a, const map_params& b) {
          a.grad_t_max == b.grad_t_max;
 }
 
-static int check_params(map_pool* pool, const map_params* p) {
-  if (!p) return fail(pool, MAP_EINVAL, "null params");
-  if (!(p->gamma > 1.0) || !(p->c_cfl > 0.0)) return fail(pool, MAP_EINVAL, "gamma must exceed 1 and c_cfl be positive");
-  if (p->scheme < 0 || p->scheme > 2 || p->limiter < 0 || p->limiter > 1) return fail(pool, MAP_EINVAL, "bad scheme or limiter");
-  if (p->ch_mode < 0 || p->ch_mode > 2 || p->cp_mode < 0 || p->cp_mode > 1) return fail(pool, MAP_EINVAL, "bad c_h / c_p mode");
-  if (p->cp_mode == MAP_CP_FROM_CD && !(p->c_d > 0.0 && p->c_d < 1.0)) return fail(pool, MAP_EINVAL, "c_d must lie in (0,1)");
-  if (p->eta < 0.0) return fail(pool, MAP_EINVAL, "eta must be >= 0");
-  if (p->riemann != MAP_RIEMANN_LF && p->riemann != MAP_RIEMANN_HLLC) return fail(pool, MAP_EINVAL, "bad riemann");
-  if (p->conduction < MAP_COND_OFF || p->conduction > MAP_COND_ALIGNED) return fail(pool, MAP_EINVAL, "bad conduction mode");
-  if (p->conduction && !(p->kappa0 > 0.0)) return fail(pool, MAP_EINVAL, "conduction needs kappa0 > 0");
-  if (!(p->grad_t_max >= 0.0)) return fail(pool, MAP_EINVAL, "grad_t_max must be >= 0");
+// Threshold of the FP32 pressure recovery's FP64 fallback: tau > 0 recomputes p in FP64
+// where e_int < tau e; tau <= 0 turns the fallback off (-inf: the comparison never holds for
+// e >= 0), so the FP32 form then recovers every pressure in FP32.  FP64 pools ignore it.
+static double fix_tau(const map_pool* pool, const map_params* p) {
+  if (is64(pool)) return 0.0;
+  return p->fp64_fix_tau > 0.0 ? p->fp64_fix_tau : -INFINITY;
+}
+
+}  // extern "C"
+
+// The parameter checks that need no pool: nullptr when p is acceptable, else the reason.
+const char* mapgb::params_problem(const map_params* p) {
+  if (!p) return "null params";
+  if (!(p->gamma > 1.0) || !(p->c_cfl > 0.0)) return "gamma must exceed 1 and c_cfl be positive";
+  if (p->scheme < 0 || p->scheme > 2 || p->limiter < 0 || p->limiter > 1) return "bad scheme or limiter";
+  if (p->ch_mode < 0 || p->ch_mode > 2 || p->cp_mode < 0 || p->cp_mode > 1) return "bad c_h / c_p mode";
+  if (p->cp_mode == MAP_CP_FROM_CD && !(p->c_d > 0.0 && p->c_d < 1.0)) return "c_d must lie in (0,1)";
+  if (!(p->eta >= 0.0)) return "eta must be >= 0";
+  if (p->riemann != MAP_RIEMANN_LF && p->riemann != MAP_RIEMANN_HLLC) return "bad riemann";
+  if (p->conduction < MAP_COND_OFF || p->conduction > MAP_COND_ALIGNED) return "bad conduction mode";
+  if (p->conduction && !(p->kappa0 > 0.0)) return "conduction needs kappa0 > 0";
+  if (!(p->grad_t_max >= 0.0)) return "grad_t_max must be >= 0";
   if (p->riemann == MAP_RIEMANN_HLLC && p->scheme == MAP_MMC)
-    return fail(pool, MAP_EINVAL, "HLLC is an interface flux of LF and WENO; MMC takes MAP_RIEMANN_LF");
+    return "HLLC is an interface flux of LF and WENO; MMC takes MAP_RIEMANN_LF";
+  return nullptr;
+}
+
+extern "C" {
+
+static int check_params(map_pool* pool, const map_params* p) {
+  if (const char* why = params_problem(p)) return fail(pool, MAP_EINVAL, why);
   if (!pool->have_tree) return fail(pool, MAP_ESTATE, "no tree");
   size_t smem = is64(pool) ? step_smem_f64(kcfg(pool), p->scheme, p->eta > 0.0)
                            : step_smem_f32(kcfg(pool), p->scheme, p->eta > 0.0);
@@ -598,7 +673,7 @@ static int step_launches(map_pool* pool, const map_params* p, bool fused) {
   S.dyn = pool->dyn;
   S.gamma = p->gamma;
   S.eta = p->eta;
-  S.tau = is64(pool) ? 0.0 : (p->fp64_fix_tau > 0.0 ? p->fp64_fix_tau : 0.0);
+  S.tau = fix_tau(pool, p);
   S.eglm = p->eglm;
   S.scheme = p->scheme;
   S.limiter = p->limiter;
@@ -706,7 +781,7 @@ static int conduction_launches(map_pool* pool, const map_params* p) {
     C.nblocks = pool->tree.nleaves;
     C.geo = pool->dt.geo;
     C.gamma = p->gamma;
-    C.tau = is64(pool) ? 0.0 : (p->fp64_fix_tau > 0.0 ? p->fp64_fix_tau : 0.0);
+    C.tau = fix_tau(pool, p);
     C.kappa0 = p->kappa0;
     C.grad_t_max = p->grad_t_max;
     C.mode = p->conduction;
@@ -850,6 +925,9 @@ int map_check(map_pool* pool) {
   CK(cudaMemcpyAsync(&e, pool->err_word, sizeof(unsigned), cudaMemcpyDeviceToHost, pool->stream));
   CK(cudaMemsetAsync(pool->err_word, 0, sizeof(unsigned), pool->stream));
   CK(cudaStreamSynchronize(pool->stream));
+  // the asynchronous host copies are complete too once map_check returns
+  if (pool->copy_stream) CK(cudaStreamSynchronize(pool->copy_stream));
+  if (pool->rcopy_stream) CK(cudaStreamSynchronize(pool->rcopy_stream));
   if (e & 4u) return fail(pool, MAP_ETIMEOUT, "a bounded device wait for a plane copy gave up");
   if (e & 1u) return fail(pool, MAP_ENONFINITE, "a leaf cell became non-finite");
   if (e & 2u) return fail(pool, MAP_ENEGPRES, "a leaf cell has rho <= 0 or p < 0");
@@ -866,6 +944,7 @@ int map_flag_refine(map_pool* pool, const map_params* p, const map_refine_params
   F.nblocks = pool->tree.nleaves;
   F.geo = pool->dt.geo;
   F.gamma = p->gamma;
+  F.tau = fix_tau(pool, p);
   F.r = *r;
   F.flags = pool->flags;
   F.est = pool->est;

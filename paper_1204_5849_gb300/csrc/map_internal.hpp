@@ -117,6 +117,10 @@ struct HostTree {
   void reset();
 };
 
+// The checks of map_params that need no pool (capi.cpp): nullptr when p is acceptable,
+// else the reason.
+const char* params_problem(const map_params* p);
+
 // Build the tree; returns an empty string on success, else the reason.
 std::string build_tree(int ndim, int nb, const std::vector<map_problem_desc>& probs,
                        const map_block_desc* leaves, int n, HostTree& t);
@@ -252,6 +256,7 @@ struct FlagLaunch {
   int nblocks;
   const BlockGeo* geo;
   double gamma;
+  double tau = 0.0;          // FP32 pools: threshold of the pressure recovery's FP64 fallback
   map_refine_params r;
   int8_t* flags;
   double* est;
@@ -272,7 +277,7 @@ struct PackLaunch {
   const int* blocks;       // pool ids in caller leaf order
   int nblocks;
   int to_pool;             // 1: staging -> pool, 0: pool -> staging
-  int staging_f32 = 0;     // 1: the staging holds floats (FP32 host layout), to_pool only
+  int staging_f32 = 0;     // 1: the staging holds floats (FP32 host layout)
 };
 
 struct RegridLaunch {

@@ -1,17 +1,19 @@
 // noalloc.cu -- an allocation-free variant of the CFL reduction.
 //
-// Some callers cannot allocate device memory: code running inside a CUDA-graph
-// capture that must not add allocation nodes, embedders whose memory is owned by another
+// Some callers cannot allocate device memory: embedders whose memory is owned by another
 // allocator (a framework's caching allocator or a fixed arena) and who forbid
 // cudaMalloc/cudaFree, and real-time loops that must not synchronise the device the way
 // cudaMalloc/cudaFree may.  map_cfl_dt_noalloc serves them: the caller passes the state
 // (already in device memory) and receives dt; the kernel's scratch (one partial maximum
 // per block) lives in a file-scope static device array of fixed size, so no call
 // allocates.  The array is resident on every GPU that loads the library until the process
-// exits, and all calls share it.
+// exits, and all calls share it.  The call is blocking: it copies the five results to the
+// caller's host memory and synchronises its stream.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdio.h>
+
+#include <atomic>
 
 #include "map_internal.hpp"
 #include "physics.cuh"
@@ -27,8 +29,10 @@ static constexpr int kNoAllocMaxBlocks = MAP_NOALLOC_MAX_BLOCKS;
 static __device__ __align__(256) double g_noalloc_scratch[kNoAllocMaxBlocks + 8];
 
 // Device address of g_noalloc_scratch per device, looked up once per device with that
-// device current (host code may not use the symbol itself as an address).
-static double* g_scratch_addr[64] = {nullptr};
+// device current (host code may not use the symbol itself as an address).  Atomic because
+// host threads may make their first calls concurrently; each stores the same address.  A
+// device reset invalidates the kept address (documented at the declaration).
+static std::atomic<double*> g_scratch_addr[64];
 
 // Reduces the partial maxima and computes dt, c_h, c_p and the damping factor exactly as
 // the pool's finalisation does; result[0..4] = dt, c_h, c_p, damping, alpha_g.
@@ -88,8 +92,13 @@ extern "C" int map_cfl_dt_noalloc(const void* u_dev, int precision, int ndim, in
     set_global_error(msg);
     return MAP_EINVAL;
   }
-  if (!(p->gamma > 1.0) || !(p->c_cfl > 0.0)) {
-    set_global_error("map_cfl_dt_noalloc: gamma must exceed 1 and c_cfl be positive");
+  if (const char* why = params_problem(p)) {
+    snprintf(msg, sizeof msg, "map_cfl_dt_noalloc: %s", why);
+    set_global_error(msg);
+    return MAP_EINVAL;
+  }
+  if (p->conduction != MAP_COND_OFF) {
+    set_global_error("map_cfl_dt_noalloc: thermal conduction is not covered (its dt bound needs a second reduction)");
     return MAP_EINVAL;
   }
   int dev = 0;
@@ -98,7 +107,8 @@ extern "C" int map_cfl_dt_noalloc(const void* u_dev, int precision, int ndim, in
     set_global_error("map_cfl_dt_noalloc: no usable current CUDA device");
     return MAP_ECUDA;
   }
-  if (!g_scratch_addr[dev]) {
+  double* partial = g_scratch_addr[dev].load(std::memory_order_acquire);
+  if (!partial) {
     // set-up, once per device, with that device current (first call on the device)
     void* addr = nullptr;
     e = cudaGetSymbolAddress(&addr, g_noalloc_scratch);
@@ -107,9 +117,9 @@ extern "C" int map_cfl_dt_noalloc(const void* u_dev, int precision, int ndim, in
       set_global_error(msg);
       return MAP_ECUDA;
     }
-    g_scratch_addr[dev] = (double*)addr;
+    partial = (double*)addr;
+    g_scratch_addr[dev].store(partial, std::memory_order_release);
   }
-  double* partial = g_scratch_addr[dev];
   double* result = partial + kNoAllocMaxBlocks;
   cudaStream_t s = (cudaStream_t)stream;
   double mindx = dx[0];
