@@ -344,6 +344,54 @@ int map_plan_leaves(int ndim, int nb, const map_problem_desc* problems, int n_pr
                     const map_block_desc* leaves, int n, const int8_t* flags, int max_level,
                     map_block_desc* out, int cap, int* n_out, char* msg, int msg_cap);
 
+/* ---- Partition over processes: Sec. 4.2 (load balance: the blocks in curve order are cut
+ * into ranges of equal block count, one per process) and Sec. 4.3 (boundary conditions
+ * between processes: each process receives the blocks its ghost cells are built from).
+ * Every process holds the whole tree and a pool sized for it (the paper replicates the
+ * block list on every process too); it steps, reduces and sums only its own leaves.  One
+ * step of a partitioned pool, per process:
+ *   1. map_pack_leaves of the leaves each peer needs from it, the transfer (the caller's:
+ *      NCCL or any other), map_unpack_leaves of the leaves it needs from each peer;
+ *   2. map_fill_ghosts (the own leaves' ghosts are then those of the whole pool);
+ *   3. map_local_alpha, the maximum over processes (the caller's all-reduce), map_set_alpha:
+ *      dt, c_h, c_p exactly as map_cfl_dt on the whole pool gives them;
+ *   4. map_step (own leaves only); map_conservation gives the own leaves' sums.
+ * A partitioned pool steps MMC and LF without thermal conduction, and with reflux off where
+ * coarse/fine faces exist (map_step returns MAP_EUNSUPPORTED otherwise): WENO's second stage,
+ * conduction substeps and reflux would each need another exchange inside the step.
+ * map_advance is refused (MAP_ESTATE) while a subset is active.
+ *
+ * map_plan_partition (host only, no pool, no GPU): for a leaf list as map_set_tree takes it,
+ *   owner_out[n] = the process (0..nranks-1) stepping each leaf -- Morton-order ranges of
+ *   equal count, the first n % nranks one leaf longer -- and need_out[nranks * n]:
+ *   need_out[r * n + i] = 1 where process r needs leaf i's interior for its own leaves'
+ *   ghost fill (its own leaves included): same-level and restriction sources, the leaves
+ *   under a restricted parent, prolongation sources, and, where a source's own ghosts are
+ *   read (prolongation stencils), that source's sources in turn.  Process r receives leaf i
+ *   from owner_out[i] where need_out[r * n + i] = 1 and owner_out[i] != r.  MAP_EINVAL (text
+ *   in msg) if the list is not a valid tree.
+ * map_set_active: the leaves (caller indices, n of them) this pool steps, reduces (map_cfl_dt,
+ *   map_local_alpha) and sums (map_conservation); leaves = NULL or n < 0 restores all.  A new
+ *   tree (map_set_tree, map_regrid) restores all.  MAP_EINVAL for a bad or repeated index.
+ * map_pack_leaves / map_unpack_leaves: the interiors of the n listed leaves (caller indices)
+ *   to / from dev_buf, a device buffer of n * 9 * nb^ndim values in the pool's precision
+ *   (double for MAP_FP64, float for MAP_FP32_FIX64; leaf-major, then [9][nz][nb][nb]),
+ *   caller-owned, on the pool stream.  Unpacking is a host write: the next fill rebuilds
+ *   every ghost region.
+ * map_local_alpha: the maximum signal speed alpha_g (Sec. 3.7) over the active leaves, per
+ *   problem, into alpha_out[n_problems] (host); synchronises.
+ * map_set_alpha: finalises dt, c_h, c_p and the damping factor from the given alpha_g per
+ *   problem (>= 0) as map_cfl_dt does after its own reduction; map_step then uses them.
+ *   MAP_ENONFINITE if a dt is not finite and positive. */
+int map_plan_partition(int ndim, int nb, const map_problem_desc* problems, int n_problems,
+                       const map_block_desc* leaves, int n, int nranks, int* owner_out,
+                       unsigned char* need_out, char* msg, int msg_cap);
+int map_set_active(map_pool* pool, const int* leaves, int n);
+int map_pack_leaves(map_pool* pool, const int* leaves, int n, void* dev_buf);
+int map_unpack_leaves(map_pool* pool, const int* leaves, int n, const void* dev_buf);
+int map_local_alpha(map_pool* pool, const map_params* p, double* alpha_out);
+int map_set_alpha(map_pool* pool, const map_params* p, const double* alpha);
+
 /* Allocation-free CFL reduction (no counterpart in the paper; an interface addition).
  *
  * For callers that cannot allocate device memory: embedders whose device memory belongs to

@@ -5,9 +5,10 @@ include/map.h); this package holds its sources (csrc/), the in-tree build (_buil
 and a thin ctypes binding (binding.py).
 """
 
-from .binding import (MAP_FP32_FIX64, MAP_FP64, MapError, Pool, check_leaves, exported_symbols, load,
-                      make_params, make_refine, plan_leaves)
+from .binding import (MAP_FP32_FIX64, MAP_FP64, MapError, Partition, Pool, check_leaves, exported_symbols,
+                      load, make_params, make_refine, plan_leaves, plan_partition)
 from .autotune import choose_block_size
 
 __all__ = ["Pool", "MapError", "MAP_FP64", "MAP_FP32_FIX64", "load", "exported_symbols",
-           "make_params", "make_refine", "choose_block_size", "check_leaves", "plan_leaves"]
+           "make_params", "make_refine", "choose_block_size", "check_leaves", "plan_leaves", "Partition",
+           "plan_partition"]

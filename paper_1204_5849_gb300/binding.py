@@ -120,6 +120,13 @@ _SIGS = {
     "map_plan_leaves": (C.c_int, [C.c_int, C.c_int, C.c_void_p, C.c_int, C.POINTER(map_block_desc), C.c_int,
                                   C.c_void_p, C.c_int, C.POINTER(map_block_desc), C.c_int, C.POINTER(C.c_int),
                                   C.c_char_p, C.c_int]),
+    "map_plan_partition": (C.c_int, [C.c_int, C.c_int, C.c_void_p, C.c_int, C.POINTER(map_block_desc), C.c_int,
+                                     C.c_int, C.c_void_p, C.c_void_p, C.c_char_p, C.c_int]),
+    "map_set_active": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
+    "map_pack_leaves": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
+    "map_unpack_leaves": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
+    "map_local_alpha": (C.c_int, [C.c_void_p, C.POINTER(map_params), C.c_void_p]),
+    "map_set_alpha": (C.c_int, [C.c_void_p, C.POINTER(map_params), C.c_void_p]),
 }
 
 NOALLOC_MAX_BLOCKS = 65536
@@ -170,6 +177,69 @@ def plan_leaves(mesh, flags: np.ndarray, max_level: int) -> np.ndarray:
     if rc != MAP_OK:
         raise MapError(rc, "map_plan_leaves", msg.value.decode())
     return _leaves_to_array(arr, n.value)
+
+
+def plan_partition(mesh, nranks: int):
+    """map_plan_partition (host only, no GPU): owner[n] (the process stepping each leaf) and
+    need[nranks, n] (1 where a process needs a leaf's interior for its ghost fill)."""
+    owner = np.zeros(mesh.nleaves, dtype=np.int32)
+    need = np.zeros((nranks, mesh.nleaves), dtype=np.uint8)
+    msg = C.create_string_buffer(256)
+    rc = load().map_plan_partition(mesh.ndim, mesh.nb, _problems(mesh), len(mesh.problems), _leaves(mesh),
+                                   mesh.nleaves, int(nranks), _ptr(owner), _ptr(need), msg, 256)
+    if rc != MAP_OK:
+        raise MapError(rc, "map_plan_partition", msg.value.decode())
+    return owner, need
+
+
+class Partition:
+    """The leaves of a mesh cut over nranks processes (map_plan_partition) and, for one
+    process, what it exchanges with each peer before its ghost fill."""
+
+    def __init__(self, mesh, nranks: int, rank: int):
+        self.nranks, self.rank = int(nranks), int(rank)
+        self.owner, self.need = plan_partition(mesh, nranks)
+        self.own = np.flatnonzero(self.owner == rank).astype(np.int32)
+
+    def sends(self, peer: int) -> np.ndarray:
+        """Own leaves the peer needs, in increasing caller index."""
+        return np.flatnonzero((self.owner == self.rank) & (self.need[peer] != 0)).astype(np.int32)
+
+    def recvs(self, peer: int) -> np.ndarray:
+        """The peer's leaves this process needs, in increasing caller index."""
+        return np.flatnonzero((self.owner == peer) & (self.need[self.rank] != 0)).astype(np.int32)
+
+    def exchange(self, pool, dist, device) -> int:
+        """Halo exchange through torch.distributed (device tensors for NCCL, CPU tensors for
+        gloo): map_pack_leaves per peer, send/recv, map_unpack_leaves.  Returns the bytes
+        received."""
+        import torch
+        dtype = torch.float64 if pool.precision == MAP_FP64 else torch.float32
+        per = 9 * int(np.prod(pool.interior_shape()[1:]))
+        ops, inbox = [], []
+        for peer in range(self.nranks):
+            if peer == self.rank:
+                continue
+            snd, rcv = self.sends(peer), self.recvs(peer)
+            if len(snd):
+                buf = torch.empty(len(snd) * per, dtype=dtype, device="cuda")
+                pool.pack_leaves(snd, buf.data_ptr())
+                torch.cuda.synchronize()
+                ops.append(dist.P2POp(dist.isend, buf if device == "cuda" else buf.cpu(), peer))
+            if len(rcv):
+                buf = torch.empty(len(rcv) * per, dtype=dtype, device=device)
+                ops.append(dist.P2POp(dist.irecv, buf, peer))
+                inbox.append((rcv, buf))
+        if ops:
+            for r in dist.batch_isend_irecv(ops):
+                r.wait()
+        got = 0
+        for rcv, buf in inbox:
+            dev = buf if buf.is_cuda else buf.cuda()
+            pool.unpack_leaves(rcv, dev.data_ptr())
+            torch.cuda.synchronize()
+            got += buf.numel() * buf.element_size()
+        return got
 
 
 def load(path: str = LIB_PATH):
@@ -423,6 +493,31 @@ class Pool:
 
     def set_launch(self, grid: int = 0, w_pred: int = 0, w_face: int = 0):
         self._ck(load().map_set_launch(self.h, int(grid), int(w_pred), int(w_face)), "map_set_launch")
+
+    # -- partitioned pools (map_set_active and the calls around it)
+    def set_active(self, leaves):
+        if leaves is None:
+            self._ck(load().map_set_active(self.h, None, -1), "map_set_active")
+            return
+        a = np.ascontiguousarray(leaves, dtype=np.int32)
+        self._ck(load().map_set_active(self.h, _ptr(a), len(a)), "map_set_active")
+
+    def pack_leaves(self, leaves, dev_ptr: int):
+        a = np.ascontiguousarray(leaves, dtype=np.int32)
+        self._ck(load().map_pack_leaves(self.h, _ptr(a), len(a), C.c_void_p(dev_ptr)), "map_pack_leaves")
+
+    def unpack_leaves(self, leaves, dev_ptr: int):
+        a = np.ascontiguousarray(leaves, dtype=np.int32)
+        self._ck(load().map_unpack_leaves(self.h, _ptr(a), len(a), C.c_void_p(dev_ptr)), "map_unpack_leaves")
+
+    def local_alpha(self, params: Dict) -> np.ndarray:
+        out = np.zeros(len(self.mesh.problems))
+        self._ck(load().map_local_alpha(self.h, C.byref(make_params(params)), _ptr(out)), "map_local_alpha")
+        return out
+
+    def set_alpha(self, params: Dict, alpha):
+        a = np.ascontiguousarray(alpha, dtype=np.float64)
+        self._ck(load().map_set_alpha(self.h, C.byref(make_params(params)), _ptr(a)), "map_set_alpha")
 
     def speeds(self) -> np.ndarray:
         out = np.zeros((len(self.mesh.problems), 5))

@@ -26,10 +26,17 @@ struct DevTree {
   int nrtasks = 0;
   void* freg = nullptr;        // face registers, tree.nslots slots
   std::vector<int> leaf_off, parent_off, residual_off;  // offsets per level (host)
+  // partitioned pools (map_set_active): the leaves this pool steps, reduces and sums
+  int* act_all = nullptr;      // pool ids, Morton order
+  int* act_level = nullptr;    // pool ids, concatenated by level
+  std::vector<int> act_off;    // offsets per level (host)
+  int n_act = 0;
+  int* xfer_ids = nullptr;     // pool ids of the leaves of one map_pack_leaves / map_unpack_leaves
 };
 
 struct map_pool {
   int ndim = 0, nb = 0, precision = 0, max_blocks = 0, nprob = 0;
+  bool partial = false;        // map_set_active chose a subset of the leaves
   std::vector<map_problem_desc> probs;
   cudaStream_t stream = nullptr;
   bool own_stream = false;
@@ -126,7 +133,11 @@ static void free_tree(map_pool* pool) {
   cudaFree(pool->dt.refl);
   cudaFree(pool->dt.rtasks);
   cudaFree(pool->dt.freg);
+  cudaFree(pool->dt.act_all);
+  cudaFree(pool->dt.act_level);
+  cudaFree(pool->dt.xfer_ids);
   pool->dt = DevTree();
+  pool->partial = false;
 }
 
 static void drop_graphs(map_pool* pool) {
@@ -498,7 +509,8 @@ int map_read_leaves(map_pool* pool, double* u) {
 static int fill_on(map_pool* pool, int q) {
   const HostTree& t = pool->tree;
   const DevTree& D = pool->dt;
-  const bool residual = pool->pushed[q];
+  // a partitioned pool's ghosts may come from leaves another process steps: every region
+  const bool residual = pool->pushed[q] && !pool->partial;
   for (int L = t.maxlev - 1; L >= 0; --L) {
     RestrictLaunch R;
     R.u = pool->buf[q];
@@ -576,13 +588,13 @@ static int alpha_device(map_pool* pool, const map_params* p) {
   CK(launch_zero_alpha(pool->dyn, pool->nprob, pool->stream, &pool->launches));
   CflLaunch C;
   C.u = pool->buf[pool->cur];
-  C.blocks = pool->dt.all_leaves;
-  C.nblocks = pool->tree.nleaves;
+  C.blocks = pool->partial ? pool->dt.act_all : pool->dt.all_leaves;
+  C.nblocks = pool->partial ? pool->dt.n_act : pool->tree.nleaves;
   C.geo = pool->dt.geo;
   C.dyn = pool->dyn;
   C.gamma = p->gamma;
   C.kappa0 = p->conduction ? p->kappa0 : 0.0;
-  CK(DISPATCH(pool, cfl, C));
+  if (C.nblocks > 0) CK(DISPATCH(pool, cfl, C));
   return MAP_OK;
 }
 
@@ -645,6 +657,20 @@ static int check_params(map_pool* pool, const map_params* p) {
   return MAP_OK;
 }
 
+// What a partitioned pool cannot do inside one map_step: the WENO stage state and the
+// conduction substeps need their halo leaves exchanged between the stages, and reflux at a
+// coarse/fine face needs the face fluxes of leaves another process may step.
+static int check_partial(map_pool* pool, const map_params* p) {
+  if (!pool->partial) return MAP_OK;
+  if (p->scheme == MAP_WENO)
+    return fail(pool, MAP_EUNSUPPORTED, "a partitioned pool steps MMC and LF only (WENO's second stage needs an exchange)");
+  if (p->conduction)
+    return fail(pool, MAP_EUNSUPPORTED, "a partitioned pool steps without thermal conduction (its substeps need exchanges)");
+  if (p->reflux && pool->dt.nrtasks > 0)
+    return fail(pool, MAP_EUNSUPPORTED, "a partitioned pool with coarse/fine faces steps with reflux off");
+  return MAP_OK;
+}
+
 int map_cfl_dt(map_pool* pool, const map_params* p, double* dt_out) {
   if (!pool) return MAP_EINVAL;
   int rc = check_params(pool, p);
@@ -697,18 +723,21 @@ static int step_launches(map_pool* pool, const map_params* p, bool fused) {
     S.stage = stage;
     S.sums = with_fused ? pool->sums : nullptr;
     S.dyn_next = with_fused ? pool->dyn : nullptr;
+    const DevTree& D = pool->dt;
     if (is64(pool)) {
       for (int L = 0; L <= t.maxlev; ++L) {
-        S.blocks = pool->dt.level_leaves + pool->dt.leaf_off[L];
-        S.nblocks = pool->dt.leaf_off[L + 1] - pool->dt.leaf_off[L];
+        const std::vector<int>& off = pool->partial ? D.act_off : D.leaf_off;
+        S.blocks = (pool->partial ? D.act_level : D.level_leaves) + off[L];
+        S.nblocks = off[L + 1] - off[L];
+        if (S.nblocks == 0) continue;
         S.grid = pool->tune_grid;
         CK(DISPATCH(pool, step, S));
       }
     } else {
-      S.blocks = pool->dt.all_leaves;
-      S.nblocks = t.nleaves;
+      S.blocks = pool->partial ? D.act_all : D.all_leaves;
+      S.nblocks = pool->partial ? D.n_act : t.nleaves;
       S.grid = pool->tune_grid;
-      CK(DISPATCH(pool, step, S));
+      if (S.nblocks > 0) CK(DISPATCH(pool, step, S));
     }
     return MAP_OK;
   };
@@ -822,6 +851,8 @@ int map_step(map_pool* pool, const map_params* p) {
   int rc = check_params(pool, p);
   if (rc) return rc;
   if (!pool->have_dt && !(p->dt_override > 0.0)) return fail(pool, MAP_ESTATE, "no time step: call map_cfl_dt first");
+  rc = check_partial(pool, p);
+  if (rc) return rc;
   if (p->dt_override > 0.0 && !pool->have_dt) {
     rc = cfl_device(pool, p);
     if (rc) return rc;
@@ -848,6 +879,8 @@ int map_advance(map_pool* pool, const map_params* p, int nsteps) {
   if (!pool) return MAP_EINVAL;
   int rc = check_params(pool, p);
   if (rc) return rc;
+  if (pool->partial)
+    return fail(pool, MAP_ESTATE, "a partitioned pool steps with map_step, between the exchanges of its halo leaves");
   if (nsteps <= 0) return MAP_OK;
   if (p->conduction) {
     // the substep count depends on dt: each step runs eagerly (fill, dt, update, conduction)
@@ -1042,11 +1075,11 @@ int map_conservation(map_pool* pool, double* sums_out) {
   CK(cudaMemsetAsync(pool->sums, 0, sizeof(double) * kNV * pool->nprob, pool->stream));
   SumLaunch L;
   L.u = pool->buf[pool->cur];
-  L.blocks = pool->dt.all_leaves;
-  L.nblocks = pool->tree.nleaves;
+  L.blocks = pool->partial ? pool->dt.act_all : pool->dt.all_leaves;
+  L.nblocks = pool->partial ? pool->dt.n_act : pool->tree.nleaves;
   L.geo = pool->dt.geo;
   L.sums = pool->sums;
-  CK(DISPATCH(pool, sums, L));
+  if (L.nblocks > 0) CK(DISPATCH(pool, sums, L));
   CK(cudaMemcpyAsync(sums_out, pool->sums, sizeof(double) * kNV * pool->nprob, cudaMemcpyDeviceToHost, pool->stream));
   CK(cudaStreamSynchronize(pool->stream));
   pool->sums_valid = true;
@@ -1263,6 +1296,145 @@ int map_plan_leaves(int ndim, int nb, const map_problem_desc* problems, int n_pr
   }
   memcpy(out, plan.data(), plan.size() * sizeof(map_block_desc));
   put_msg(msg, msg_cap, "");
+  return MAP_OK;
+}
+
+// ---- partition over processes (Sec. 4.2 load balance; Sec. 4.3 inter-processor boundaries)
+
+int map_plan_partition(int ndim, int nb, const map_problem_desc* problems, int n_problems,
+                       const map_block_desc* leaves, int n, int nranks, int* owner_out,
+                       unsigned char* need_out, char* msg, int msg_cap) {
+  if (!owner_out || !need_out || nranks < 1) {
+    put_msg(msg, msg_cap, "null argument or nranks < 1");
+    return MAP_EINVAL;
+  }
+  HostTree t;
+  std::vector<map_problem_desc> probs;
+  const std::string why = host_tree(ndim, nb, problems, n_problems, leaves, n, t, probs);
+  if (!why.empty()) {
+    put_msg(msg, msg_cap, why);
+    return MAP_EINVAL;
+  }
+  std::vector<int> owner;
+  std::vector<unsigned char> need;
+  plan_partition(t, nranks, owner, need);
+  memcpy(owner_out, owner.data(), owner.size() * sizeof(int));
+  memcpy(need_out, need.data(), need.size());
+  put_msg(msg, msg_cap, "");
+  return MAP_OK;
+}
+
+int map_set_active(map_pool* pool, const int* leaves, int n) {
+  if (!pool) return MAP_EINVAL;
+  if (!pool->have_tree) return fail(pool, MAP_ESTATE, "no tree");
+  const HostTree& t = pool->tree;
+  DevTree& D = pool->dt;
+  cudaFree(D.act_all);
+  cudaFree(D.act_level);
+  D.act_all = D.act_level = nullptr;
+  D.n_act = 0;
+  pool->partial = false;
+  drop_graphs(pool);
+  pool->have_dt = false;
+  pool->alpha_ready = false;
+  pool->sums_valid = false;
+  if (!leaves || n < 0) return MAP_OK;
+  std::vector<char> on(t.nleaves, 0);
+  for (int q = 0; q < n; ++q) {
+    if (leaves[q] < 0 || leaves[q] >= t.nleaves) return fail(pool, MAP_EINVAL, "active leaf index out of range");
+    if (on[leaves[q]]) return fail(pool, MAP_EINVAL, "active leaf listed twice");
+    on[leaves[q]] = 1;
+  }
+  std::vector<int> all, lev;
+  for (int blk : t.all_leaves)
+    if (on[t.geo[blk].leaf]) all.push_back(blk);
+  D.act_off.assign(t.maxlev + 2, 0);
+  for (int L = 0; L <= t.maxlev; ++L) {
+    D.act_off[L] = (int)lev.size();
+    for (int blk : t.leaves_by_level[L])
+      if (on[t.geo[blk].leaf]) lev.push_back(blk);
+  }
+  D.act_off[t.maxlev + 1] = (int)lev.size();
+  if (!all.empty()) {
+    CK(upload(&D.act_all, all, pool->stream));
+    CK(upload(&D.act_level, lev, pool->stream));
+  }
+  CK(cudaStreamSynchronize(pool->stream));
+  D.n_act = (int)all.size();
+  pool->partial = true;
+  return MAP_OK;
+}
+
+static int transfer_leaves(map_pool* pool, const int* leaves, int n, void* dev_buf, int to_pool) {
+  if (!pool || (n > 0 && (!leaves || !dev_buf)) || n < 0) return fail(pool, MAP_EINVAL, "null argument");
+  if (!pool->have_tree) return fail(pool, MAP_ESTATE, "no tree");
+  const HostTree& t = pool->tree;
+  if (n > t.nleaves) return fail(pool, MAP_EINVAL, "more leaves than the tree has");
+  if (n == 0) return MAP_OK;
+  std::vector<int> ids(n);
+  for (int q = 0; q < n; ++q) {
+    if (leaves[q] < 0 || leaves[q] >= t.nleaves) return fail(pool, MAP_EINVAL, "leaf index out of range");
+    ids[q] = t.leaf_to_block[leaves[q]];
+  }
+  DevTree& D = pool->dt;
+  if (!D.xfer_ids) CK(cudaMalloc(&D.xfer_ids, (size_t)t.nleaves * sizeof(int)));
+  // stream-ordered behind the previous transfer's kernel, which read the same id array
+  CK(cudaMemcpyAsync(D.xfer_ids, ids.data(), (size_t)n * sizeof(int), cudaMemcpyHostToDevice, pool->stream));
+  CK(cudaStreamSynchronize(pool->stream));   // the host id array goes out of scope
+  if (to_pool) {
+    pool->have_dt = false;
+    pool->alpha_ready = false;
+    pool->pushed[pool->cur] = false;
+    pool->sums_valid = false;
+  }
+  return pack(pool, D.xfer_ids, n, to_pool, (double*)dev_buf, is64(pool) ? 0 : 1);
+}
+
+int map_pack_leaves(map_pool* pool, const int* leaves, int n, void* dev_buf) {
+  return transfer_leaves(pool, leaves, n, dev_buf, 0);
+}
+
+int map_unpack_leaves(map_pool* pool, const int* leaves, int n, const void* dev_buf) {
+  return transfer_leaves(pool, leaves, n, const_cast<void*>(dev_buf), 1);
+}
+
+int map_local_alpha(map_pool* pool, const map_params* p, double* alpha_out) {
+  if (!pool || !alpha_out) return MAP_EINVAL;
+  int rc = check_params(pool, p);
+  if (rc) return rc;
+  rc = alpha_device(pool, p);
+  if (rc) return rc;
+  std::vector<ProbDyn> dyn(pool->nprob);
+  CK(cudaMemcpyAsync(dyn.data(), pool->dyn, sizeof(ProbDyn) * pool->nprob, cudaMemcpyDeviceToHost, pool->stream));
+  CK(cudaStreamSynchronize(pool->stream));
+  for (int q = 0; q < pool->nprob; ++q) {
+    const unsigned long long b = dyn[q].alpha_bits;
+    double a;
+    memcpy(&a, &b, sizeof a);
+    alpha_out[q] = a;
+  }
+  pool->alpha_ready = false;
+  return MAP_OK;
+}
+
+int map_set_alpha(map_pool* pool, const map_params* p, const double* alpha) {
+  if (!pool || !alpha) return MAP_EINVAL;
+  int rc = check_params(pool, p);
+  if (rc) return rc;
+  for (int q = 0; q < pool->nprob; ++q)
+    if (!(alpha[q] >= 0.0)) return fail(pool, MAP_EINVAL, "alpha_g must be >= 0 (and not NaN)");
+  static_assert(sizeof(unsigned long long) == sizeof(double), "alpha bits");
+  CK(cudaMemcpy2DAsync((char*)pool->dyn + offsetof(ProbDyn, alpha_bits), sizeof(ProbDyn), alpha, sizeof(double),
+                       sizeof(double), pool->nprob, cudaMemcpyHostToDevice, pool->stream));
+  CK(launch_finalize(make_finalize(pool, p), pool->stream, &pool->launches));
+  std::vector<ProbDyn> dyn(pool->nprob);
+  CK(cudaMemcpyAsync(dyn.data(), pool->dyn, sizeof(ProbDyn) * pool->nprob, cudaMemcpyDeviceToHost, pool->stream));
+  CK(cudaStreamSynchronize(pool->stream));
+  pool->have_dt = true;
+  pool->alpha_ready = false;
+  for (int q = 0; q < pool->nprob; ++q)
+    if (!(isfinite(dyn[q].dt) && dyn[q].dt > 0.0))
+      return fail(pool, MAP_ENONFINITE, "time step is not finite and positive (non-finite or zero signal speed)");
   return MAP_OK;
 }
 

@@ -130,6 +130,11 @@ std::string build_tree(int ndim, int nb, const std::vector<map_problem_desc>& pr
 std::string plan_regrid(const HostTree& t, const std::vector<map_problem_desc>& probs, const int8_t* flags,
                         int max_level, std::vector<map_block_desc>& out);
 
+// Partition of the leaves over nranks (Morton ranges of equal count, Sec. 4.2) and, per
+// rank, the leaves whose interiors its ghost fill reads (own ones included):
+// owner[caller leaf] = rank, need[r * n + caller leaf] = 1 where rank r needs that leaf.
+void plan_partition(const HostTree& t, int nranks, std::vector<int>& owner, std::vector<unsigned char>& need);
+
 // Regrid tasks from an old tree to a new one; empty string on success.
 std::string build_regrid(const HostTree& old_t, const HostTree& new_t,
                          std::vector<RegridTask>& tasks);

@@ -723,4 +723,95 @@ std::string plan_regrid(const HostTree& t, const std::vector<map_problem_desc>& 
   return "";
 }
 
+// ---------------------------------------------------------------------------------------
+// Partition over ranks (Sec. 4.2 load balance): the leaves in Morton order are cut into
+// nranks contiguous ranges of equal count (the first n % nranks ranges one longer).  A rank
+// then needs, besides its own leaves, the interiors of every leaf its ghost fill reads: the
+// dependency closure of the fill of its own leaves.
+//   - a region copying from a leaf reads that leaf's cells; where the index map reaches its
+//     ghost cells, that leaf's own regions are needed too;
+//   - a region prolonging from a coarser leaf reads the coarse cell and its neighbours, which
+//     may be ghosts: that leaf's regions are needed too;
+//   - a region copying from a parent reads the restriction of all its leaf descendants.
+namespace {
+
+// does a copy region (rx, ry, rz) of a destination block read ghost cells of its source?
+bool copy_reads_ghosts(const GhostRegion& g, int ndim, int nb, const int r[3]) {
+  for (int d = 0; d < ndim; ++d) {
+    const int lo = r[d] == 0 ? 0 : (r[d] == 1 ? kNG : kNG + nb);
+    const int hi = r[d] == 0 ? kNG : (r[d] == 1 ? kNG + nb : nb + 2 * kNG);   // exclusive
+    const int s0 = g.m[d] * lo + g.a[d], s1 = g.m[d] * (hi - 1) + g.a[d];
+    const int smin = s0 < s1 ? s0 : s1, smax = s0 < s1 ? s1 : s0;
+    if (smin < kNG || smax >= kNG + nb) return true;
+  }
+  return false;
+}
+
+void add_descendant_leaves(const HostTree& t, int blk, std::vector<unsigned char>& need_int) {
+  if (t.geo[blk].leaf >= 0) {
+    need_int[blk] = 1;
+    return;
+  }
+  for (int q = 0; q < (t.ndim == 3 ? 8 : 4); ++q) {
+    const int c = t.children[(size_t)blk * 8 + q];
+    if (c >= 0) add_descendant_leaves(t, c, need_int);
+  }
+}
+
+}  // namespace
+
+void plan_partition(const HostTree& t, int nranks, std::vector<int>& owner, std::vector<unsigned char>& need) {
+  const int n = t.nleaves;
+  owner.assign(n, 0);
+  need.assign((size_t)nranks * n, 0);
+  // Morton order = pool ids 0..n-1 (t.all_leaves); caller index = geo[id].leaf
+  std::vector<int> rank_of_block(t.nblocks, -1);
+  for (int r = 0; r < nranks; ++r) {
+    const long long b0 = (long long)n * r / nranks, b1 = (long long)n * (r + 1) / nranks;
+    for (long long q = b0; q < b1; ++q) {
+      const int blk = t.all_leaves[q];
+      rank_of_block[blk] = r;
+      owner[t.geo[blk].leaf] = r;
+    }
+  }
+  std::vector<unsigned char> need_int(t.nblocks), need_gh(t.nblocks);
+  std::vector<int> work;
+  for (int r = 0; r < nranks; ++r) {
+    std::fill(need_int.begin(), need_int.end(), 0);
+    std::fill(need_gh.begin(), need_gh.end(), 0);
+    work.clear();
+    for (int q = 0; q < n; ++q) {
+      const int blk = t.all_leaves[q];
+      if (rank_of_block[blk] == r) {
+        need_int[blk] = 1;
+        need_gh[blk] = 1;
+        work.push_back(blk);
+      }
+    }
+    while (!work.empty()) {
+      const int blk = work.back();
+      work.pop_back();
+      for (int id = 0; id < 27; ++id) {
+        const int rr[3] = {id % 3, (id / 3) % 3, id / 9};
+        if (id == 13 || (t.ndim == 2 && rr[2] != 1)) continue;
+        const GhostRegion& g = t.regions[(size_t)blk * 27 + id];
+        const int src = g.src;
+        if (src < 0) continue;
+        if (t.geo[src].leaf < 0) {
+          add_descendant_leaves(t, src, need_int);
+          continue;
+        }
+        need_int[src] = 1;
+        const bool ghosts = g.kind == 1 || copy_reads_ghosts(g, t.ndim, t.nb, rr);
+        if (ghosts && !need_gh[src]) {
+          need_gh[src] = 1;
+          work.push_back(src);
+        }
+      }
+    }
+    for (int blk = 0; blk < t.nblocks; ++blk)
+      if (need_int[blk] && t.geo[blk].leaf >= 0) need[(size_t)r * n + t.geo[blk].leaf] = 1;
+  }
+}
+
 }  // namespace mapgb
