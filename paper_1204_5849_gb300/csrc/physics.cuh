@@ -32,6 +32,15 @@ struct Phys {
 template <typename T>
 __device__ __forceinline__ T dmax(T a, T b) { return a > b ? a : b; }
 
+// a / b.  FP64: the plain quotient (rounds as the same formula written in plain C).  FP32:
+// the fast quotient, reciprocal times numerator (within 2 ulp); every FP32 quotient on the
+// step path has a denominator (a density, a cell spacing, a sum of slopes, a WENO weight sum)
+// far below the 2^126 range where the fast form flushes to zero.
+template <typename T>
+__device__ __forceinline__ T qdiv(T a, T b) { return a / b; }
+template <>
+__device__ __forceinline__ float qdiv<float>(float a, float b) { return __fdividef(a, b); }
+
 // p = (gamma-1) (e - m^2/(2 rho) - B^2/2)   (Sec. 2, total energy density)
 template <typename T>
 __device__ __forceinline__ T pressure(const T* w, const Phys<T>& P) {
@@ -44,7 +53,7 @@ template <>
 __device__ __forceinline__ float pressure<float>(const float* w, const Phys<float>& P) {
   float m2 = w[MX] * w[MX] + w[MY] * w[MY] + w[MZ] * w[MZ];
   float b2 = w[BX] * w[BX] + w[BY] * w[BY] + w[BZ] * w[BZ];
-  float kin = 0.5f * m2 * (1.0f / w[RHO]);
+  float kin = 0.5f * m2 * qdiv(1.0f, w[RHO]);
   float eint = w[EN] - kin - 0.5f * b2;
   if (eint < P.tau * w[EN]) {
     // low internal-energy fraction: recover p in FP64 from the same stored values
@@ -63,7 +72,7 @@ __device__ __forceinline__ void flux_p(const T* w, T p, const Phys<T>& P, T* f) 
   T rho = w[RHO];
   T v0, v1, v2;
   if constexpr (std::is_same<T, float>::value) {
-    const T ir = T(1) / rho;   // one reciprocal per state in FP32
+    const T ir = qdiv(T(1), rho);   // one reciprocal per state in FP32
     v0 = w[MX] * ir; v1 = w[MY] * ir; v2 = w[MZ] * ir;
   } else {
     v0 = w[MX] / rho; v1 = w[MY] / rho; v2 = w[MZ] / rho;
@@ -92,7 +101,7 @@ __device__ __forceinline__ T alpha_p(const T* w, T p, const Phys<T>& P) {
   T rho = w[RHO];
   if (p < T(0)) p = T(0);
   if constexpr (std::is_same<T, float>::value) {
-    const T ir = T(1) / rho;
+    const T ir = qdiv(T(1), rho);
     T a2 = P.gamma * p * ir;
     T b2 = (w[BX] * w[BX] + w[BY] * w[BY] + w[BZ] * w[BZ]) * ir;
     T bd2 = w[BX + D] * w[BX + D] * ir;
@@ -124,7 +133,7 @@ __device__ __forceinline__ T fast_speed(const T* w, T p, const Phys<T>& P) {
   T rho = w[RHO];
   if (p < T(0)) p = T(0);
   if constexpr (std::is_same<T, float>::value) {
-    const T ir = T(1) / rho;
+    const T ir = qdiv(T(1), rho);
     T a2 = P.gamma * p * ir;
     T b2 = (w[BX] * w[BX] + w[BY] * w[BY] + w[BZ] * w[BZ]) * ir;
     T bd2 = w[BX + D] * w[BX + D] * ir;
@@ -255,7 +264,7 @@ __device__ __forceinline__ T minmod(T a, T b) {
 template <typename T, int LIM>
 __device__ __forceinline__ T limiter(T a, T b) {
   if (LIM == 0) return minmod<T>(a, b);
-  return (a * b > T(0)) ? (T(2) * a * b) / (a + b) : T(0);
+  return (a * b > T(0)) ? qdiv(T(2) * a * b, a + b) : T(0);
 }
 
 // WENO two-stencil reconstruction around u0 (Sec. 3.3): the left state of the face on
@@ -265,12 +274,12 @@ template <typename T>
 __device__ __forceinline__ void weno_faces(T um, T u0, T up, T& minus_right, T& plus_left) {
   const T eps = T(1e-12);
   T dp = up - u0, dm = u0 - um;
-  T ap = T(1) / ((eps + dp * dp) * (eps + dp * dp));
-  T am = T(1) / ((eps + dm * dm) * (eps + dm * dm));
+  T ap = qdiv(T(1), (eps + dp * dp) * (eps + dp * dp));
+  T am = qdiv(T(1), (eps + dm * dm) * (eps + dm * dm));
   T wm = T(0.5) * (u0 + up), vm = T(0.5) * (T(3) * u0 - um);
   T wp = T(0.5) * (T(3) * u0 - up), vp = T(0.5) * (u0 + um);
-  minus_right = (T(2) * ap * wm + am * vm) / (T(2) * ap + am);
-  plus_left = (ap * wp + T(2) * am * vp) / (ap + T(2) * am);
+  minus_right = qdiv(T(2) * ap * wm + am * vm, T(2) * ap + am);
+  plus_left = qdiv(ap * wp + T(2) * am * vp, ap + T(2) * am);
 }
 
 template <typename T>
@@ -309,7 +318,7 @@ __device__ __forceinline__ float2 limiter2(float2 a, float2 b) {
   const float2 pr = mul(a, b);
   const float2 s = add(a, b);
   const float2 q = mul(splat(2.0f), pr);
-  return make_float2(pr.x > 0.0f ? q.x / s.x : 0.0f, pr.y > 0.0f ? q.y / s.y : 0.0f);
+  return make_float2(pr.x > 0.0f ? __fdividef(q.x, s.x) : 0.0f, pr.y > 0.0f ? __fdividef(q.y, s.y) : 0.0f);
 }
 
 // pressure of two states (same FP64 fallback rule as pressure<float>)
@@ -336,7 +345,7 @@ __device__ __forceinline__ float2 pressure2(const float2* w, const Phys<float>& 
 // physical flux in direction D of two states; if alpha != nullptr also their local speeds
 template <int D>
 __device__ __forceinline__ void flux2(const float2* w, const Phys<float>& P, float2* f, float2* alpha) {
-  const float2 ir = make_float2(1.0f / w[RHO].x, 1.0f / w[RHO].y);
+  const float2 ir = make_float2(__fdividef(1.0f, w[RHO].x), __fdividef(1.0f, w[RHO].y));
   const float2 p = pressure2(w, P, ir);
   const float2 v0 = mul(w[MX], ir), v1 = mul(w[MY], ir), v2 = mul(w[MZ], ir);
   float2 b2 = mul(w[BX], w[BX]);

@@ -105,13 +105,13 @@ __device__ __forceinline__ void eglm_src(const T* const* pl, int c, const T* dx2
   constexpr int P2 = NP * NP;
   const T* p0 = pl[1];
   T divb = T(0);
-  divb += (p0[BX * P2 + c + 1] - p0[BX * P2 + c - 1]) / dx2[0];
-  divb += (p0[BY * P2 + c + NP] - p0[BY * P2 + c - NP]) / dx2[1];
-  if (NDIM == 3) divb += (pl[2][BZ * P2 + c] - pl[0][BZ * P2 + c]) / dx2[2];
+  divb += qdiv<T>((p0[BX * P2 + c + 1] - p0[BX * P2 + c - 1]), dx2[0]);
+  divb += qdiv<T>((p0[BY * P2 + c + NP] - p0[BY * P2 + c - NP]), dx2[1]);
+  if (NDIM == 3) divb += qdiv<T>((pl[2][BZ * P2 + c] - pl[0][BZ * P2 + c]), dx2[2]);
   T bg = T(0);
-  bg += p0[BX * P2 + c] * ((p0[PSI * P2 + c + 1] - p0[PSI * P2 + c - 1]) / dx2[0]);
-  bg += p0[BY * P2 + c] * ((p0[PSI * P2 + c + NP] - p0[PSI * P2 + c - NP]) / dx2[1]);
-  if (NDIM == 3) bg += p0[BZ * P2 + c] * ((pl[2][PSI * P2 + c] - pl[0][PSI * P2 + c]) / dx2[2]);
+  bg += p0[BX * P2 + c] * (qdiv<T>((p0[PSI * P2 + c + 1] - p0[PSI * P2 + c - 1]), dx2[0]));
+  bg += p0[BY * P2 + c] * (qdiv<T>((p0[PSI * P2 + c + NP] - p0[PSI * P2 + c - NP]), dx2[1]));
+  if (NDIM == 3) bg += p0[BZ * P2 + c] * (qdiv<T>((pl[2][PSI * P2 + c] - pl[0][PSI * P2 + c]), dx2[2]));
   s[MX] += -divb * p0[BX * P2 + c];
   s[MY] += -divb * p0[BY * P2 + c];
   s[MZ] += -divb * p0[BZ * P2 + c];
@@ -123,14 +123,14 @@ template <typename T, int NDIM, int NP>
 __device__ __forceinline__ void current(const T* const* pl, int c, const T* dx2, T* J) {
   constexpr int P2 = NP * NP;
   const T* p0 = pl[1];
-  T dBz_dy = (p0[BZ * P2 + c + NP] - p0[BZ * P2 + c - NP]) / dx2[1];
-  T dBz_dx = (p0[BZ * P2 + c + 1] - p0[BZ * P2 + c - 1]) / dx2[0];
-  T dBy_dx = (p0[BY * P2 + c + 1] - p0[BY * P2 + c - 1]) / dx2[0];
-  T dBx_dy = (p0[BX * P2 + c + NP] - p0[BX * P2 + c - NP]) / dx2[1];
+  T dBz_dy = qdiv<T>((p0[BZ * P2 + c + NP] - p0[BZ * P2 + c - NP]), dx2[1]);
+  T dBz_dx = qdiv<T>((p0[BZ * P2 + c + 1] - p0[BZ * P2 + c - 1]), dx2[0]);
+  T dBy_dx = qdiv<T>((p0[BY * P2 + c + 1] - p0[BY * P2 + c - 1]), dx2[0]);
+  T dBx_dy = qdiv<T>((p0[BX * P2 + c + NP] - p0[BX * P2 + c - NP]), dx2[1]);
   T dBy_dz = T(0), dBx_dz = T(0);
   if (NDIM == 3) {
-    dBy_dz = (pl[2][BY * P2 + c] - pl[0][BY * P2 + c]) / dx2[2];
-    dBx_dz = (pl[2][BX * P2 + c] - pl[0][BX * P2 + c]) / dx2[2];
+    dBy_dz = qdiv<T>((pl[2][BY * P2 + c] - pl[0][BY * P2 + c]), dx2[2]);
+    dBx_dz = qdiv<T>((pl[2][BX * P2 + c] - pl[0][BX * P2 + c]), dx2[2]);
   }
   J[0] = dBz_dy - dBy_dz;
   J[1] = dBx_dz - dBz_dx;
@@ -146,9 +146,9 @@ __device__ __forceinline__ void resist_src(const T* const* jl, const T* const* p
   const T* j0 = jl[1];
   auto cd = [&](const T* const* L, int comp, int d) -> T {
     if (d >= NDIM) return T(0);
-    if (d == 0) return (L[1][comp * P2 + c + 1] - L[1][comp * P2 + c - 1]) / dx2[0];
-    if (d == 1) return (L[1][comp * P2 + c + NP] - L[1][comp * P2 + c - NP]) / dx2[1];
-    return (L[2][comp * P2 + c] - L[0][comp * P2 + c]) / dx2[2];
+    if (d == 0) return qdiv<T>((L[1][comp * P2 + c + 1] - L[1][comp * P2 + c - 1]), dx2[0]);
+    if (d == 1) return qdiv<T>((L[1][comp * P2 + c + NP] - L[1][comp * P2 + c - NP]), dx2[1]);
+    return qdiv<T>((L[2][comp * P2 + c] - L[0][comp * P2 + c]), dx2[2]);
   };
   (void)j0;
   T rx = eta * cd(jl, 1, 2) - eta * cd(jl, 2, 1);
@@ -174,7 +174,7 @@ __device__ __forceinline__ void resist_src(const T* const* jl, const T* const* p
       else t = Jy * Bx - Jx * By;
       q[sg] = eta * t;
     }
-    re += (q[1] - q[0]) / dx2[d];
+    re += qdiv<T>((q[1] - q[0]), dx2[d]);
   }
   s[BX] += rx;
   s[BY] += ry;
@@ -309,13 +309,13 @@ template <typename T, int NDIM>
 __device__ __forceinline__ void eglm_src_col(const T* pc, int PS, int RS, int c, const T* zm, const T* zp,
                                              const T* dx2, T* s) {
   T divb = T(0);
-  divb += (pc[BX * PS + c + 1] - pc[BX * PS + c - 1]) / dx2[0];
-  divb += (pc[BY * PS + c + RS] - pc[BY * PS + c - RS]) / dx2[1];
-  if (NDIM == 3) divb += (zp[BZ] - zm[BZ]) / dx2[2];
+  divb += qdiv<T>((pc[BX * PS + c + 1] - pc[BX * PS + c - 1]), dx2[0]);
+  divb += qdiv<T>((pc[BY * PS + c + RS] - pc[BY * PS + c - RS]), dx2[1]);
+  if (NDIM == 3) divb += qdiv<T>((zp[BZ] - zm[BZ]), dx2[2]);
   T bg = T(0);
-  bg += pc[BX * PS + c] * ((pc[PSI * PS + c + 1] - pc[PSI * PS + c - 1]) / dx2[0]);
-  bg += pc[BY * PS + c] * ((pc[PSI * PS + c + RS] - pc[PSI * PS + c - RS]) / dx2[1]);
-  if (NDIM == 3) bg += pc[BZ * PS + c] * ((zp[PSI] - zm[PSI]) / dx2[2]);
+  bg += pc[BX * PS + c] * (qdiv<T>((pc[PSI * PS + c + 1] - pc[PSI * PS + c - 1]), dx2[0]));
+  bg += pc[BY * PS + c] * (qdiv<T>((pc[PSI * PS + c + RS] - pc[PSI * PS + c - RS]), dx2[1]));
+  if (NDIM == 3) bg += pc[BZ * PS + c] * (qdiv<T>((zp[PSI] - zm[PSI]), dx2[2]));
   s[MX] += -divb * pc[BX * PS + c];
   s[MY] += -divb * pc[BY * PS + c];
   s[MZ] += -divb * pc[BZ * PS + c];
@@ -331,9 +331,9 @@ __device__ __forceinline__ void resist_src_col(const T* jc, int cj, const T* jzm
   constexpr int PJ = RW * RW, PU = NP * NP;
   auto cdJ = [&](int comp, int d) -> T {
     if (d >= NDIM) return T(0);
-    if (d == 0) return (jc[comp * PJ + cj + 1] - jc[comp * PJ + cj - 1]) / dx2[0];
-    if (d == 1) return (jc[comp * PJ + cj + RW] - jc[comp * PJ + cj - RW]) / dx2[1];
-    return (jzp[comp] - jzm[comp]) / dx2[2];
+    if (d == 0) return qdiv<T>((jc[comp * PJ + cj + 1] - jc[comp * PJ + cj - 1]), dx2[0]);
+    if (d == 1) return qdiv<T>((jc[comp * PJ + cj + RW] - jc[comp * PJ + cj - RW]), dx2[1]);
+    return qdiv<T>((jzp[comp] - jzm[comp]), dx2[2]);
   };
   T rx = eta * cdJ(1, 2) - eta * cdJ(2, 1);
   T ry = eta * cdJ(2, 0) - eta * cdJ(0, 2);
@@ -362,7 +362,7 @@ __device__ __forceinline__ void resist_src_col(const T* jc, int cj, const T* jzm
       else t = Jy * Bx - Jx * By;
       q[sg] = eta * t;
     }
-    re += (q[1] - q[0]) / dx2[d];
+    re += qdiv<T>((q[1] - q[0]), dx2[d]);
   }
   s[BX] += rx;
   s[BY] += ry;
