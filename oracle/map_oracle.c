@@ -263,11 +263,13 @@ static double minmod(double a, double b) {
 
 /* Limiter as a function of two differences.
  * kind 0 minmod, 1 van Leer (harmonic mean when a, b agree in sign, else 0), 2 the
- * literal form of Sec. 3.1, phi(r) b with phi(r) = r for |r| <= 1 and 1 otherwise.
+ * literal form of Sec. 3.1, phi(r) b with phi(r) = r for |r| <= 1 and 1 otherwise, 3 no
+ * limiting, phi = 1 (returns b; a test option that turns MMC into its unlimited form).
  * For MMC, phi(r) g with r = a/b equals this function of (a, b) (division free); a zero
- * denominator gives 0. */
+ * denominator gives 0.  Kinds 2 and 3 are MMC options only. */
 double orc_limiter(int kind, double a, double b) {
   if (kind == 0) return minmod(a, b);
+  if (kind == 3) return b;
   if (kind == 1) {
     FLOPS(1);
     if (!(a * b > 0.0)) return 0.0;

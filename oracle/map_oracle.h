@@ -30,7 +30,7 @@ typedef struct {
   double eta;       /* uniform resistivity */
   int eglm;         /* 1: EGLM non-conservative sources on; 0: GLM */
   int scheme;       /* 0 MMC, 1 LF, 2 WENO */
-  int limiter;      /* 0 minmod, 1 van Leer, 2 literal Roe form (MMC only) */
+  int limiter;      /* 0 minmod, 1 van Leer, 2 literal Roe form, 3 none (2, 3: MMC only) */
   double dt_override; /* > 0: use this dt */
   int reflux;       /* 1: coarse fluxes at coarse/fine faces replaced by the fine ones */
   int riemann;      /* interface flux of LF and WENO: 0 f_m (Lax-Friedrichs), 1 HLLC */

@@ -658,3 +658,48 @@ def test_brio_wu_robust_and_one_dimensional(scheme):
     assert np.all(G == G[:, :1, :])
     rho = G[0, 0]
     assert rho[:n // 4].mean() > 0.9 and rho[-n // 4:].mean() < 0.2
+
+
+# --- MMC reduces to Lax-Wendroff for a linear wave of constant speed (Sec. 3.1) ---------
+
+@pytest.mark.parametrize("sign", (1, -1))
+@pytest.mark.parametrize("mode", (1, 3, 7))
+def test_mmc_unlimited_is_lax_wendroff_on_the_glm_pair(sign, mode):
+    """The (B_x, psi) pair of the x sweep is linear with the fixed speed c_h (Q4), so on a
+    y-uniform strip with rho, v, p, B_y, B_z uniform the characteristic variable
+    w = psi + sign c_h B_x is advected at sign c_h and nothing else feeds back into it.
+    MMC with phi = 1 then reduces by hand to the Lax-Wendroff scheme: h = c_h w_i is the
+    upwind flux, u~ the upwind predictor, g+ = c_h (w~_{i+1} - w_i), so
+    fhat = c_h (w_i + (1 - nu)(w_{i+1} - w_i) / 2), whose one-step factor on
+    exp(i theta j) is 1 - i nu sin(theta) - nu^2 (1 - cos(theta)) (nu = sign c_h dt / dx).
+    A dropped 1/2, a g term on the wrong face or a predictor with the wrong sign each
+    change that factor."""
+    n, nb, ch = 64, 16, 2.0
+    m = w.uniform_mesh(2, nb, (n // nb, 1), lo=(0, 0, 0), hi=(1, nb / n, 1))
+    dx = 1.0 / n
+    nu = 0.4
+    dt = nu * dx / ch
+    A, phi0 = 1e-2, 0.3
+    theta = 2 * math.pi * mode / n
+
+    def ic(X, Y, Z, **_):
+        wv = A * np.cos(2 * math.pi * mode * (X - dx / 2) + phi0)      # theta j + phi0
+        U = conserved_from_primitive(np.ones_like(X), 0.0, 0.0, 0.0, wv / (2 * sign * ch), 0.0, 0.0,
+                                     1.0, 5 / 3)
+        U[8] = wv / 2
+        return U
+    U0 = w.evaluate_on_mesh(m, ic)
+    o = Oracle(m, U0)
+    p = P(scheme="mmc", limiter="none", eglm=0, ch_mode="fixed", ch=ch, cp_mode="fixed", cp=0.0,
+          dt_override=dt)
+    o.fill_ghosts()
+    o.cfl(p)
+    o.step(p)
+    U = o.get_state()
+    wnew = assemble_uniform(m, U, 8)[0, 0] + sign * ch * assemble_uniform(m, U, 4)[0, 0]
+    wother = assemble_uniform(m, U, 8)[0, 0] - sign * ch * assemble_uniform(m, U, 4)[0, 0]
+    j = np.arange(n)
+    G = 1 - 1j * (sign * nu) * math.sin(theta) - nu * nu * (1 - math.cos(theta))
+    want = np.real(G * A * np.exp(1j * (theta * j + phi0)))
+    np.testing.assert_allclose(wnew, want, rtol=0, atol=1e-14)
+    np.testing.assert_allclose(wother, 0.0, rtol=0, atol=1e-15)
