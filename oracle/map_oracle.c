@@ -15,7 +15,9 @@
  * Readings where the paper is silent or garbled are stated at the place they are used.
  *
  * Parity unpinned: the MMC multi-D face speeds (one u-speed and one u~-speed per face,
- * used for every split term of that face's flux) and long-time AMR runs.
+ * used for every split term of that face's flux) and long-time AMR runs.  The rest of MMC
+ * is pinned where the speed is constant (every reading then coincides): unlimited, it is
+ * Lax-Wendroff on the linear GLM pair.
  */
 #include "map_oracle.h"
 

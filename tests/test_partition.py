@@ -197,3 +197,29 @@ def test_gloo_halo_exchange_matches_single_process(name, world):
         assert fill_ok, (name, rank)
         assert step_ok, (name, rank)
         assert received > 0
+
+
+def test_plan_rejects_bad_input():
+    from paper_1204_5849_gb300 import MapError, plan_partition
+    mesh = w.uniform_mesh(2, 16, (2, 2))
+    with pytest.raises(MapError) as ei:
+        plan_partition(mesh, 0)
+    assert ei.value.code == -1
+    bad = w.uniform_mesh(2, 16, (2, 2))
+    bad.leaves = bad.leaves[:3]                        # a hole in the domain
+    with pytest.raises(MapError) as ej:
+        plan_partition(bad, 2)
+    assert ej.value.code == -1
+
+
+def test_more_processes_than_leaves_leaves_some_idle():
+    """Equal-count ranges with more processes than leaves: the first n processes own one
+    leaf each, the rest none (and need nothing)."""
+    from paper_1204_5849_gb300 import plan_partition
+    mesh = w.uniform_mesh(2, 16, (2, 2))
+    owner, need = plan_partition(mesh, 6)
+    counts = np.bincount(owner, minlength=6)
+    assert sorted(counts.tolist()) == [0, 0, 1, 1, 1, 1]
+    for r in range(6):
+        if counts[r] == 0:
+            assert need[r].sum() == 0
