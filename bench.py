@@ -349,6 +349,18 @@ def run_workload(args):
         G[prec] = pool.read_leaves()
         pool.close()
     out["error_fp32_vs_fp64"] = dict(steps=nacc, **error_table(G[MAP_FP32_FIX64], G[MAP_FP64]))
+    if len(mesh0.problems) > 1:
+        # per problem: the largest per-variable L1 of the FP32 form against the FP64 form
+        prob = np.array([lf[0] for lf in mesh0.leaves])
+        per = []
+        for q in range(len(mesh0.problems)):
+            sel = prob == q
+            t = error_table(G[MAP_FP32_FIX64][sel], G[MAP_FP64][sel])["l1_rel"]
+            per.append(max(t.values()))
+        cells = [int(mesh0.problems[q].nbase[0] * mesh0.nb) for q in range(len(mesh0.problems))]
+        out["error_fp32_vs_fp64_per_problem"] = {
+            "steps": nacc, "l1_rel_max_over_variables": per, "edge_cells": cells,
+            "max": max(per), "median": float(np.median(per))}
     print(json.dumps(out))
 
 

@@ -607,8 +607,15 @@ def test_full_size_config_against_oracle(gpulib, name):
     pool.close()
     b = pool_for(mesh, MAP_FP32_FIX64, U0)
     b.advance(dict(p, fp64_fix_tau=1e-2), 2)
-    assert rel_l1(b.read_leaves(), R).max() <= 1e-5
+    G = b.read_leaves()
+    assert rel_l1(G, R).max() <= 1e-5
     assert b.check() == 0
+    if len(mesh.problems) > 1:
+        # each problem of the ensemble on its own (the aggregate could hide a small one)
+        prob = np.array([lf[0] for lf in mesh.leaves])
+        for q in range(len(mesh.problems)):
+            sel = prob == q
+            assert rel_l1(G[sel], R[sel]).max() <= 1e-5, q
 
 
 # --- diagnostics: conservation sums, speeds, flags, regrid, error word --------------------
