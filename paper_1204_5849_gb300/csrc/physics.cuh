@@ -252,12 +252,15 @@ __device__ __forceinline__ void lf_flux(const T* a, const T* b, const Phys<T>& P
   }
 }
 
-// minmod(a,b) = sgn(a) max(0, min(|a|, sgn(a) b))
+// minmod(a,b) = sgn(a) max(0, min(|a|, sgn(a) b)), written without branches: the smaller
+// magnitude with the common sign where a and b are both positive or both negative, else +0
+// (bitwise the value of the branching form for every input, signed zeros and NaN included)
 template <typename T>
 __device__ __forceinline__ T minmod(T a, T b) {
-  if (a > T(0)) { T m = a < b ? a : b; return m > T(0) ? m : T(0); }
-  if (a < T(0)) { T m = -a < -b ? -a : -b; return m > T(0) ? -m : T(0); }
-  return T(0);
+  const T m = fmin(fabs(a), fabs(b));
+  const bool pos = a > T(0) && b > T(0);
+  const bool neg = a < T(0) && b < T(0);
+  return pos ? m : (neg ? -m : T(0));
 }
 
 // limiter(a, b): 0 minmod, 1 van Leer (2ab/(a+b) when ab > 0, else 0)
