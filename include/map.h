@@ -244,17 +244,19 @@ int map_last_sums(map_pool* pool, double* sums_out);
 
 /* Launch shape chosen by map_autotune. */
 typedef struct {
-  int grid;           /* step-kernel CTAs: 0 = one per block, else a persistent grid */
+  int grid;           /* step-kernel CTAs: 0 = the default (one per block in 3D; for FP32
+                         pools in 2D a persistent grid of two per SM), a value >= the
+                         block count = one per block, else a persistent grid */
   int w_pred, w_face; /* warp-schedule cost of a predictor unit and of a face unit */
-  double ms_default;  /* step launches with the default shape (one CTA per block, default
+  double ms_default;  /* step launches with the default shape (grid 0, default
                          weights: 3:1 for 3D LF, 3:2 for 3D MMC, 7:4 in 2D, 1:1 for WENO) */
   double ms_best;     /* with the chosen shape */
   int trials;
 } map_tune_result;
 
 /* Autotuner (no counterpart in the paper): times this pool's step launches on its current
- * tree and state under candidate launch shapes -- one CTA per block or a persistent grid of
- * 1-16 x the SM count, then warp-schedule weight ratios from 1:1 to 6:1 for the per-plane
+ * tree and state under candidate launch shapes -- the default, one CTA per block, or a
+ * persistent grid of 1-16 x the SM count, then warp-schedule weight ratios from 1:1 to 6:1 for the per-plane
  * work list -- and keeps the
  * fastest for later map_step / map_advance calls (results are bitwise the same under every
  * shape; the fused FP64 sums may differ in rounding).  The state is not changed: trials
@@ -271,7 +273,9 @@ int map_autotune(map_pool* pool, const map_params* p, int reps, map_tune_result*
 int map_test_fail_waits(map_pool* pool, int on);
 
 /* (No counterpart in the paper.)  Sets the launch shape directly (grid 0 and weights 0
- * restore the defaults). */
+ * restore the defaults).  A persistent grid of the FP32 form gives each CTA a contiguous
+ * Morton range of blocks, over whose runs of one problem and level the kernel reduces its
+ * fused alpha_g and sums once. */
 int map_set_launch(map_pool* pool, int grid, int w_pred, int w_face);
 
 /* (No counterpart in the paper.)  Thermal conduction of the last step, per problem: the

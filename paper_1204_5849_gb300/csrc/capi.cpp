@@ -32,6 +32,11 @@ struct DevTree {
   std::vector<int> act_off;    // offsets per level (host)
   int n_act = 0;
   int* xfer_ids = nullptr;     // pool ids of the leaves of one map_pack_leaves / map_unpack_leaves
+  // the FP32 single launch's block list for a persistent grid of chunk_grid CTAs: CTA c's
+  // grid-stride positions c, c + G, ... hold a contiguous Morton range of the leaves
+  int* chunk_ids = nullptr;
+  int chunk_grid = 0;
+  bool chunk_partial = false;
 };
 
 struct map_pool {
@@ -83,6 +88,7 @@ struct map_pool {
   // launch shape of the step kernel (map_autotune / map_set_launch): CTAs (0 = one per
   // block) and warp-schedule weights (0 = defaults)
   int tune_grid = 0, tune_wp = 0, tune_wf = 0;
+  int nsm = 0;                 // SM count of the pool's device
   int fail_waits = 0;        // test hook: the step kernel's plane waits give up at once
   long long launches = 0;
   std::string err;
@@ -136,6 +142,7 @@ static void free_tree(map_pool* pool) {
   cudaFree(pool->dt.act_all);
   cudaFree(pool->dt.act_level);
   cudaFree(pool->dt.xfer_ids);
+  cudaFree(pool->dt.chunk_ids);
   pool->dt = DevTree();
   pool->partial = false;
 }
@@ -169,6 +176,11 @@ int map_create_pool(const map_pool_desc* d, void* stream, map_pool** out) {
   if (d->precision != MAP_FP64 && d->precision != MAP_FP32_FIX64) return fail(nullptr, MAP_EINVAL, "bad precision");
   if (d->max_blocks < 1 || d->n_problems < 1 || !d->problems) return fail(nullptr, MAP_EINVAL, "bad capacity or problems");
   pool = new map_pool();
+  {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&pool->nsm, cudaDevAttrMultiProcessorCount, dev);
+  }
   pool->ndim = d->ndim;
   pool->nb = d->nb;
   pool->precision = d->precision;
@@ -690,6 +702,50 @@ int map_cfl_dt(map_pool* pool, const map_params* p, double* dt_out) {
   return MAP_OK;
 }
 
+// Grid of the FP32 single step launch: the tuned one, else one CTA per block in 3D and, in
+// 2D (256-cell blocks, whose per-block reductions weigh), a persistent grid of two CTAs per
+// SM (the residency of the 2D FP32 kernels).
+static int step_grid(const map_pool* pool) {
+  if (pool->tune_grid > 0) return pool->tune_grid;
+  if (!is64(pool) && pool->ndim == 2 && pool->nsm > 0) return 2 * pool->nsm;
+  return 0;
+}
+
+// The block list of the FP32 single launch with grid G: for a persistent grid, the leaves
+// (or the active ones) reordered so that each CTA's grid-stride positions hold one contiguous
+// Morton range (its blocks then share problem and level in long runs, over which the kernel
+// reduces its fused diagnostics once).  Built outside stream capture; during a capture
+// without it the plain order is used.
+static int step_block_list(map_pool* pool, int G, const int** list) {
+  DevTree& D = pool->dt;
+  const HostTree& t = pool->tree;
+  const int n = pool->partial ? D.n_act : t.nleaves;
+  *list = pool->partial ? D.act_all : D.all_leaves;
+  if (G <= 0 || G >= n) return MAP_OK;
+  if (D.chunk_ids && D.chunk_grid == G && D.chunk_partial == pool->partial) {
+    *list = D.chunk_ids;
+    return MAP_OK;
+  }
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(pool->stream, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return MAP_OK;
+  std::vector<int> src(n), perm(n);
+  CK(cudaMemcpyAsync(src.data(), *list, (size_t)n * sizeof(int), cudaMemcpyDeviceToHost, pool->stream));
+  CK(cudaStreamSynchronize(pool->stream));
+  int start = 0;
+  for (int c = 0; c < G; ++c) {
+    const int len = c < n ? (n - 1 - c) / G + 1 : 0;   // positions c, c + G, ... below n
+    for (int k = 0; k < len; ++k) perm[c + (size_t)k * G] = src[start + k];
+    start += len;
+  }
+  if (!D.chunk_ids) CK(cudaMalloc(&D.chunk_ids, (size_t)t.nleaves * sizeof(int)));
+  CK(cudaMemcpyAsync(D.chunk_ids, perm.data(), (size_t)n * sizeof(int), cudaMemcpyHostToDevice, pool->stream));
+  CK(cudaStreamSynchronize(pool->stream));
+  D.chunk_grid = G;
+  D.chunk_partial = pool->partial;
+  *list = D.chunk_ids;
+  return MAP_OK;
+}
+
 // launches of one step on buffer pool->cur; flips cur.  fused: also reduce alpha of the
 // new state into dyn (next dt) and the FP64 sums.
 static int step_launches(map_pool* pool, const map_params* p, bool fused) {
@@ -734,9 +790,10 @@ static int step_launches(map_pool* pool, const map_params* p, bool fused) {
         CK(DISPATCH(pool, step, S));
       }
     } else {
-      S.blocks = pool->partial ? D.act_all : D.all_leaves;
       S.nblocks = pool->partial ? D.n_act : t.nleaves;
-      S.grid = pool->tune_grid;
+      S.grid = step_grid(pool);
+      const int rcl = step_block_list(pool, S.grid, &S.blocks);
+      if (rcl) return rcl;
       if (S.nblocks > 0) CK(DISPATCH(pool, step, S));
     }
     return MAP_OK;
@@ -1106,8 +1163,8 @@ int map_set_launch(map_pool* pool, int grid, int w_pred, int w_face) {
 
 // Times the step launches (scheme update with its fused reductions, WENO's mid-step fill,
 // reflux) from the current buffer under candidate launch shapes and keeps the fastest: first
-// the grid (one CTA per block, or k = 1, 2, 3, 4, 6, 8, 12, 16 times the SM count as a persistent
-// grid, below the block count) with the
+// the grid (the default, one CTA per block, or k = 1, 2, 3, 4, 6, 8, 12, 16 times the SM count
+// as a persistent grid, below the block count) with the
 // default weights, then the warp-schedule weights with that grid.  The trials write only the
 // other buffers; ghosts are refilled and dt recomputed first, and the step constants and sums
 // are restored afterwards, so the state and what later calls see are unchanged.
@@ -1160,6 +1217,11 @@ int map_autotune(map_pool* pool, const map_params* p, int reps, map_tune_result*
   int bg = 0, bwp = dwp, bwf = dwf;
   rc = trial(0, dwp, dwf, &best);
   const float base = best;
+  if (rc == MAP_OK && step_grid(pool) > 0) {
+    // the default is persistent here: try one CTA per block as well
+    rc = trial(pool->tree.nleaves, dwp, dwf, &t);
+    if (rc == MAP_OK && t < best) { best = t; bg = pool->tree.nleaves; }
+  }
   const int K[] = {1, 2, 3, 4, 6, 8, 12, 16};
   for (int k : K) {
     if (rc) break;
@@ -1333,6 +1395,7 @@ int map_set_active(map_pool* pool, const int* leaves, int n) {
   cudaFree(D.act_level);
   D.act_all = D.act_level = nullptr;
   D.n_act = 0;
+  D.chunk_grid = 0;
   pool->partial = false;
   drop_graphs(pool);
   pool->have_dt = false;

@@ -1053,9 +1053,17 @@ step_kernel(StepArgsT<T> A) {
       __syncthreads();
     }
     if (!ok) break;
-    // per-block reductions of the fused diagnostics (one problem per block), in T within
-    // each warp (TwoSum pairs for the sums), then FP64 across warps
-    if (A.dyn_next || A.sums) {
+    // reductions of the fused diagnostics, in T within each warp (TwoSum pairs for the sums),
+    // then FP64 across warps.  The per-thread maxima and compensated sums keep accumulating
+    // over the CTA's consecutive blocks of one problem and level (equal cell volumes) and are
+    // reduced once that run ends -- a persistent grid given contiguous block ranges reduces
+    // once per run instead of once per block (the decision is the same on every thread)
+    bool flush = true;
+    if (bi + (int)gridDim.x < A.nblocks) {
+      const BlockGeo gn = A.geo[A.blocks[bi + gridDim.x]];
+      flush = gn.problem != gg.problem || gn.level != gg.level;
+    }
+    if ((A.dyn_next || A.sums) && flush) {
       double* red = reinterpret_cast<double*>(sf);     // (NV+1) x 32 doubles
       const int lane = tid & 31, wid = tid >> 5;
       T am = alpha_max;
