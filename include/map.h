@@ -363,7 +363,10 @@ int map_plan_leaves(int ndim, int nb, const map_problem_desc* problems, int n_pr
  * A partitioned pool steps MMC and LF without thermal conduction, and with reflux off where
  * coarse/fine faces exist (map_step returns MAP_EUNSUPPORTED otherwise): WENO's second stage,
  * conduction substeps and reflux would each need another exchange inside the step.
- * map_advance is refused (MAP_ESTATE) while a subset is active.
+ * map_advance is refused (MAP_ESTATE) while a subset is active.  map_flag_refine flags every
+ * leaf of the pool, but only the own leaves' flags rest on current values: gather them from
+ * the processes (the paper's all-gather of refinement flags) before planning a regrid, which
+ * every process then applies to its whole tree (map_regrid restores all leaves as active).
  *
  * map_plan_partition (host only, no pool, no GPU): for a leaf list as map_set_tree takes it,
  *   owner_out[n] = the process (0..nranks-1) stepping each leaf -- Morton-order ranges of
