@@ -49,19 +49,25 @@ __device__ __forceinline__ T pressure(const T* w, const Phys<T>& P) {
   return P.gm1 * (w[EN] - T(0.5) * m2 / w[RHO] - T(0.5) * b2);
 }
 
+// The FP64 recovery of the pressure from FP32 stored values (the fallback of the FP32 form
+// where e_int is a small fraction of e).  Out of line: it runs rarely, and kept inline its
+// FP64 registers and code weigh on the hot FP32 path around every pressure.
+static __device__ __noinline__ float pressure_fp64(float rho, float mx, float my, float mz, float bx, float by,
+                                           float bz, float en, float gm1) {
+  const double m2d = (double)mx * mx + (double)my * my + (double)mz * mz;
+  const double b2d = (double)bx * bx + (double)by * by + (double)bz * bz;
+  const double ed = (double)en - 0.5 * m2d / (double)rho - 0.5 * b2d;
+  return (float)((double)gm1 * ed);
+}
+
 template <>
 __device__ __forceinline__ float pressure<float>(const float* w, const Phys<float>& P) {
   float m2 = w[MX] * w[MX] + w[MY] * w[MY] + w[MZ] * w[MZ];
   float b2 = w[BX] * w[BX] + w[BY] * w[BY] + w[BZ] * w[BZ];
   float kin = 0.5f * m2 * qdiv(1.0f, w[RHO]);
   float eint = w[EN] - kin - 0.5f * b2;
-  if (eint < P.tau * w[EN]) {
-    // low internal-energy fraction: recover p in FP64 from the same stored values
-    double m2d = (double)w[MX] * w[MX] + (double)w[MY] * w[MY] + (double)w[MZ] * w[MZ];
-    double b2d = (double)w[BX] * w[BX] + (double)w[BY] * w[BY] + (double)w[BZ] * w[BZ];
-    double ed = (double)w[EN] - 0.5 * m2d / (double)w[RHO] - 0.5 * b2d;
-    return (float)((double)P.gm1 * ed);
-  }
+  // low internal-energy fraction: recover p in FP64 from the same stored values
+  if (eint < P.tau * w[EN]) return pressure_fp64(w[RHO], w[MX], w[MY], w[MZ], w[BX], w[BY], w[BZ], w[EN], P.gm1);
   return P.gm1 * eint;
 }
 
@@ -324,7 +330,10 @@ __device__ __forceinline__ float2 limiter2(float2 a, float2 b) {
   return make_float2(pr.x > 0.0f ? __fdividef(q.x, s.x) : 0.0f, pr.y > 0.0f ? __fdividef(q.y, s.y) : 0.0f);
 }
 
-// pressure of two states (same FP64 fallback rule as pressure<float>)
+// pressure of two states (same FP64 fallback rule as pressure<float>); OOL: the FP64
+// recovery out of line (as pressure<float> has it) or inline, whichever measures faster in
+// the calling kernel (inline in the 3D 16^3 kernels, which sit at their register cap)
+template <bool OOL>
 __device__ __forceinline__ float2 pressure2(const float2* w, const Phys<float>& P, float2 ir) {
   float2 m2 = mul(w[MX], w[MX]);
   m2 = fma(w[MY], w[MY], m2);
@@ -335,21 +344,34 @@ __device__ __forceinline__ float2 pressure2(const float2* w, const Phys<float>& 
   const float2 kin = mul(mul(splat(0.5f), m2), ir);
   const float2 eint = sub(sub(w[EN], kin), mul(splat(0.5f), b2));
   float2 p = mul(splat(P.gm1), eint);
+  if constexpr (OOL) {
+    if (eint.x < P.tau * w[EN].x)
+      p.x = pressure_fp64(w[RHO].x, w[MX].x, w[MY].x, w[MZ].x, w[BX].x, w[BY].x, w[BZ].x, w[EN].x, P.gm1);
+    if (eint.y < P.tau * w[EN].y)
+      p.y = pressure_fp64(w[RHO].y, w[MX].y, w[MY].y, w[MZ].y, w[BX].y, w[BY].y, w[BZ].y, w[EN].y, P.gm1);
+    return p;
+  }
   if (eint.x < P.tau * w[EN].x || eint.y < P.tau * w[EN].y) {
+    auto fp64 = [&](const float* q) {
+      const double m2d = (double)q[MX] * q[MX] + (double)q[MY] * q[MY] + (double)q[MZ] * q[MZ];
+      const double b2d = (double)q[BX] * q[BX] + (double)q[BY] * q[BY] + (double)q[BZ] * q[BZ];
+      const double ed = (double)q[EN] - 0.5 * m2d / (double)q[RHO] - 0.5 * b2d;
+      return (float)((double)P.gm1 * ed);
+    };
     float wx[NV], wy[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) { wx[v] = w[v].x; wy[v] = w[v].y; }
-    if (eint.x < P.tau * w[EN].x) p.x = pressure<float>(wx, P);
-    if (eint.y < P.tau * w[EN].y) p.y = pressure<float>(wy, P);
+    if (eint.x < P.tau * w[EN].x) p.x = fp64(wx);
+    if (eint.y < P.tau * w[EN].y) p.y = fp64(wy);
   }
   return p;
 }
 
 // physical flux in direction D of two states; if alpha != nullptr also their local speeds
-template <int D>
+template <int D, bool OOL = true>
 __device__ __forceinline__ void flux2(const float2* w, const Phys<float>& P, float2* f, float2* alpha) {
   const float2 ir = make_float2(__fdividef(1.0f, w[RHO].x), __fdividef(1.0f, w[RHO].y));
-  const float2 p = pressure2(w, P, ir);
+  const float2 p = pressure2<OOL>(w, P, ir);
   const float2 v0 = mul(w[MX], ir), v1 = mul(w[MY], ir), v2 = mul(w[MZ], ir);
   float2 b2 = mul(w[BX], w[BX]);
   b2 = fma(w[BY], w[BY], b2);
@@ -388,10 +410,10 @@ __device__ __forceinline__ void flux2(const float2* w, const Phys<float>& P, flo
 }
 
 // Lax-Friedrichs flux of the face whose left state is lane x and right state lane y
-template <int D>
+template <int D, bool OOL = true>
 __device__ __forceinline__ void lf_flux2(const float2* ab, const Phys<float>& P, float* f) {
   float2 F[NV], al;
-  flux2<D>(ab, P, F, &al);
+  flux2<D, OOL>(ab, P, F, &al);
   const float a = al.x > al.y ? al.x : al.y;
 #pragma unroll
   for (int v = 0; v < NV; ++v) {

@@ -607,7 +607,7 @@ step_kernel(StepArgsT<T> A) {
                 const T ph = limiter<T, LIM>(w[v] - plm[v * P2 + cm], plp[v * P2 + cp] - w[v]);
                 ab[v] = pair::fma(pair::splat(ph), make_float2(0.5f, -0.5f), pair::splat(w[v]));
               }
-              pair::flux2<D>(ab, P, fab, nullptr);
+              pair::flux2<D, !(NDIM == 3 && NB == 16)>(ab, P, fab, nullptr);
 #pragma unroll
               for (int v = 0; v < NV; ++v) acc[v] -= lamh[D] * (fab[v].x - fab[v].y);
             } else {
@@ -680,7 +680,7 @@ step_kernel(StepArgsT<T> A) {
           ab[v] = pair::fma(ph, make_float2(0.5f, -0.5f), tt);
         }
         exch_xy(yd, ab);
-        pair::lf_flux2<0>(ab, *reinterpret_cast<const Phys<float>*>(&P), reinterpret_cast<float*>(F));
+        pair::lf_flux2<0, !(NDIM == 3 && NB == 16)>(ab, *reinterpret_cast<const Phys<float>*>(&P), reinterpret_cast<float*>(F));
       } else {
         T a[NV], b[NV];
 #pragma unroll
@@ -765,7 +765,7 @@ step_kernel(StepArgsT<T> A) {
           const float2 tt = make_float2(t0p[v * RING + rown], t1p[v * RING + rown]);
           ab[v] = pair::fma(ph, make_float2(0.5f, -0.5f), tt);
         }
-        pair::lf_flux2<2>(ab, *reinterpret_cast<const Phys<float>*>(&P), reinterpret_cast<float*>(F));
+        pair::lf_flux2<2, !(NDIM == 3 && NB == 16)>(ab, *reinterpret_cast<const Phys<float>*>(&P), reinterpret_cast<float*>(F));
       } else {
         T a[NV], b[NV];
 #pragma unroll
