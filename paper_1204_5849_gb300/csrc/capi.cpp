@@ -96,6 +96,17 @@ struct map_pool {
   cudaGraphExec_t graph[4] = {nullptr, nullptr, nullptr, nullptr};
   long long graph_kernels[4] = {0, 0, 0, 0};
   map_params graph_params{};
+  // conduction substep loops captured as graphs, keyed by substep count, buffer, the pushed
+  // state of the first fill and reflux (cond_params: the parameters they were captured for)
+  struct CondGraph {
+    int nmax = 0, cur = 0;
+    bool pushed = false, rf = false, seen = false;
+    cudaGraphExec_t ex = nullptr;
+    long long kernels = 0;
+  };
+  CondGraph cond_graph[8];
+  int cond_next = 0;
+  map_params cond_params{};
   bool graph_valid[4] = {false, false, false, false};
 };
 
@@ -148,6 +159,10 @@ static void free_tree(map_pool* pool) {
 }
 
 static void drop_graphs(map_pool* pool) {
+  for (auto& c : pool->cond_graph) {
+    if (c.ex) cudaGraphExecDestroy(c.ex);
+    c = map_pool::CondGraph();
+  }
   for (int q = 0; q < 4; ++q) {
     if (pool->graph[q]) cudaGraphExecDestroy(pool->graph[q]);
     pool->graph[q] = nullptr;
@@ -839,6 +854,8 @@ static int step_launches(map_pool* pool, const map_params* p, bool fused) {
 // dt / n per problem with the subcycle (dt and dt_c of the reduction before the step), else
 // one; each refills the ghosts (the first all variables, then the energy alone), updates the
 // energy in place and refluxes it at coarse/fine faces.  Reads dt back to size the loop.
+static int conduction_substep(map_pool* pool, const map_params* p, int it, bool rf);
+
 static int conduction_launches(map_pool* pool, const map_params* p) {
   const int np = pool->nprob;
   std::vector<ProbDyn> dyn(np);
@@ -858,7 +875,66 @@ static int conduction_launches(map_pool* pool, const map_params* p) {
   CK(cudaMemcpyAsync(pool->hsub, pool->hsub_h.data(), sizeof(double) * np, cudaMemcpyHostToDevice, pool->stream));
   CK(cudaMemcpyAsync(pool->nsub, pool->nsub_h.data(), sizeof(int) * np, cudaMemcpyHostToDevice, pool->stream));
   const bool rf = p->reflux != 0 && pool->dt.nrtasks > 0;
-  for (int it = 0; it < nmax; ++it) {
+  // The substep loop is launch-bound on small meshes (a fill and a conduction launch per
+  // substep): the second time a (substep count, buffer, fill kind) recurs it is captured into
+  // a graph, and later steps replay it.  Substep sizes and counts are read from device memory
+  // by the kernels, so a replay covers any dt with the same count.
+  if (!params_equal(pool->cond_params, *p)) {
+    drop_graphs(pool);
+    pool->cond_params = *p;
+  }
+  const bool pushed0 = pool->pushed[pool->cur];
+  map_pool::CondGraph* hit = nullptr;
+  for (auto& c : pool->cond_graph)
+    if (c.seen && c.nmax == nmax && c.cur == pool->cur && c.pushed == pushed0 && c.rf == rf) hit = &c;
+  if (hit && hit->ex) {
+    CK(cudaGraphLaunch(hit->ex, pool->stream));
+    pool->launches += hit->kernels;
+    pool->pushed[pool->cur] = false;
+    return MAP_OK;
+  }
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  CK(cudaStreamIsCapturing(pool->stream, &cs));
+  const bool capture = hit && cs == cudaStreamCaptureStatusNone;
+  if (!hit) {
+    map_pool::CondGraph& c = pool->cond_graph[pool->cond_next];
+    pool->cond_next = (pool->cond_next + 1) % 8;
+    if (c.ex) cudaGraphExecDestroy(c.ex);
+    c = map_pool::CondGraph();
+    c.nmax = nmax;
+    c.cur = pool->cur;
+    c.pushed = pushed0;
+    c.rf = rf;
+    c.seen = true;                 // first time: run eagerly (this also sets kernel attributes)
+  }
+  const long long before = pool->launches;
+  if (capture) CK(cudaStreamBeginCapture(pool->stream, cudaStreamCaptureModeThreadLocal));
+  int lrc = MAP_OK;
+  for (int it = 0; it < nmax && lrc == MAP_OK; ++it) lrc = conduction_substep(pool, p, it, rf);
+  if (capture) {
+    cudaGraph_t g = nullptr;
+    cudaError_t ce = cudaStreamEndCapture(pool->stream, &g);
+    if (lrc == MAP_OK && ce == cudaSuccess && g) {
+      cudaGraphExec_t ex = nullptr;
+      if (cudaGraphInstantiate(&ex, g, 0) == cudaSuccess) {
+        hit->ex = ex;
+        hit->kernels = pool->launches - before;
+      }
+    }
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    if (lrc) return lrc;
+    if (!hit->ex) return fail(pool, MAP_ECUDA, "capture of the conduction substeps failed");
+    CK(cudaGraphLaunch(hit->ex, pool->stream));
+  }
+  if (lrc) return lrc;
+  pool->pushed[pool->cur] = false;       // the energy ghosts are stale now
+  return MAP_OK;
+}
+
+// one conduction substep (fill, energy update, energy reflux) on the current buffer
+static int conduction_substep(map_pool* pool, const map_params* p, int it, bool rf) {
+  {
     int rc = it == 0 ? fill_on(pool, pool->cur) : fill_energy_on(pool, pool->cur);
     if (rc) return rc;
     CondLaunch C;
@@ -899,7 +975,6 @@ static int conduction_launches(map_pool* pool, const map_params* p) {
       CK(DISPATCH(pool, reflux, R));
     }
   }
-  pool->pushed[pool->cur] = false;       // the energy ghosts are stale now
   return MAP_OK;
 }
 
