@@ -245,7 +245,7 @@ int map_last_sums(map_pool* pool, double* sums_out);
 /* Launch shape chosen by map_autotune. */
 typedef struct {
   int grid;           /* step-kernel CTAs: 0 = the default (one per block in 3D; for FP32
-                         pools in 2D a persistent grid of two per SM), a value >= the
+                         pools in 2D a persistent grid of four per SM), a value >= the
                          block count = one per block, else a persistent grid */
   int w_pred, w_face; /* warp-schedule cost of a predictor unit and of a face unit */
   double ms_default;  /* step launches with the default shape (grid 0, default

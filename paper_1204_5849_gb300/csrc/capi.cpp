@@ -718,11 +718,11 @@ int map_cfl_dt(map_pool* pool, const map_params* p, double* dt_out) {
 }
 
 // Grid of the FP32 single step launch: the tuned one, else one CTA per block in 3D and, in
-// 2D (256-cell blocks, whose per-block reductions weigh), a persistent grid of two CTAs per
-// SM (the residency of the 2D FP32 kernels).
+// 2D (256-cell blocks, whose per-block reductions weigh), a persistent grid of four CTAs per
+// SM (the residency of the 128-thread 2D FP32 kernels).
 static int step_grid(const map_pool* pool) {
   if (pool->tune_grid > 0) return pool->tune_grid;
-  if (!is64(pool) && pool->ndim == 2 && pool->nsm > 0) return 2 * pool->nsm;
+  if (!is64(pool) && pool->ndim == 2 && pool->nsm > 0) return 4 * pool->nsm;
   return 0;
 }
 

@@ -39,11 +39,11 @@ cudaError_t launch_step_one(const StepLaunch& L, cudaStream_t s) {
   A.refl = RFX ? L.refl : nullptr;
   int wp = L.w_pred, wf = L.w_face;
   if (wp <= 0 || wf <= 0) default_schedule_weights(NDIM, NB, SCHEME, &wp, &wf);
-  build_schedule<NDIM, NB>(wp, wf, SCHEME != SCH_WENO || res, A.sched);
+  build_schedule<NDIM, NB, step_threads<T, NDIM, NB>()>(wp, wf, SCHEME != SCH_WENO || res, A.sched);
   A.fail_waits = L.fail_waits;
   const int grid = L.grid > 0 ? (L.grid < L.nblocks ? L.grid : L.nblocks) : L.nblocks;
   if (grid <= 0) return cudaSuccess;
-  kern<<<grid, NB * NB, smem, s>>>(A);
+  kern<<<grid, step_threads<T, NDIM, NB>(), smem, s>>>(A);
   return cudaGetLastError();
 }
 

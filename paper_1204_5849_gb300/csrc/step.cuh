@@ -13,7 +13,8 @@
 //
 // Layout: a pool block is [9][NZ][NP][NP] with NP = NB + 4 (two ghost layers); NZ = NP in
 // 3D and 1 in 2D.  One CTA owns one block at a time (grid-stride over the block list) and
-// has NB*NB threads, thread (tx,ty) owning interior column (tx+2, ty+2).  In 3D the CTA
+// has NB*NB threads, thread (tx,ty) owning interior column (tx+2, ty+2) -- except the 2D
+// 16^2 FP32 kernels, whose 128 threads own two columns each (step_threads).  In 3D the CTA
 // marches in z keeping a rolling window in shared memory: four u planes (z..z+3, one in
 // flight), the u~ planes and, with resistivity, the J planes (z-1..z+1 for 16^3 blocks; z,
 // z+1 for 8^3, whose update carries its own column's plane z-1 values in registers); x- and
@@ -395,13 +396,22 @@ __device__ __forceinline__ void exch_xy(bool yd, V* w) {
 template <int N>
 struct Pad32 { static constexpr int value = (N + 31) / 32 * 32; };
 
+// Threads per CTA of the step kernel: one per interior column, except in the 2D 16^2 FP32
+// kernels, whose 128 threads take two columns each in the update.  Their predictor and face
+// phases (10 and 17 warp units in separate barrier intervals) then leave fewer warps idle at
+// each barrier, and four CTAs reside per SM instead of two, at the same 128 registers.
+template <typename T, int NDIM, int NB>
+__host__ __device__ constexpr int step_threads() {
+  return (sizeof(T) == 4 && NDIM == 2 && NB == 16) ? 128 : NB * NB;
+}
+
 // The per-plane work list of the step kernel: warp-sized units of predictor ring cells (NPU,
 // corners left out),
-// then the x faces and y faces in one numbering (NFU), over NW warps.
-template <int NDIM, int NB>
+// then the x faces and y faces in one numbering (NFU), over the NW warps of NT threads.
+template <int NDIM, int NB, int NT>
 struct WorkList {
   using G = Geo<NDIM, NB>;
-  static constexpr int NW = G::NT / 32;
+  static constexpr int NW = NT / 32;
   static constexpr int NPU = Pad32<G::NPC>::value / 32;
   static constexpr int NFU = Pad32<2 * G::NFACE>::value / 32;   // x faces, then y faces
   static constexpr int NU = NPU + NFU;
@@ -413,9 +423,9 @@ struct WorkList {
 // and a face unit w_face (their relative cost; default_schedule_weights unless tuned).  s[w][15] holds the
 // number of units of warp w, s[w][0..] the units.  Without a predictor (WENO without
 // resistivity) its units are left out, so they do not displace face units.
-template <int NDIM, int NB>
+template <int NDIM, int NB, int NT>
 inline void build_schedule(int w_pred, int w_face, bool pred, unsigned char (&s)[8][16]) {
-  using W = WorkList<NDIM, NB>;
+  using W = WorkList<NDIM, NB, NT>;
   int load[8] = {0}, cnt[8] = {0};
   for (int q = 0; q < 8; ++q)
     for (int k = 0; k < 16; ++k) s[q][k] = 0;
@@ -444,17 +454,19 @@ __device__ __forceinline__ void two_sum_acc(T& hi, T& lo, T h2, T l2) {
 // Without it none of that code exists in the kernel.
 // Resident CTAs per SM the register budget is sized for: the 3D 8^3 window (at most 36 KB of
 // shared memory) lets 6 CTAs reside, so asking for 8 would only cap the registers at 128 and
-// spill the column state.
+// spill the column state; four 128-thread 2D 16^2 CTAs take the 128 registers two 256-thread
+// ones did.
 template <typename T, int NDIM, int NB>
 constexpr int step_min_ctas() {
-  return sizeof(T) != 4 ? 1 : NB == 16 ? 2 : NDIM == 3 ? 6 : 8;
+  return sizeof(T) != 4 ? 1 : NB == 16 ? (NDIM == 2 ? 4 : 2) : NDIM == 3 ? 6 : 8;
 }
 
 template <typename T, int NDIM, int NB, int SCHEME, int LIM, int STAGE, int FLX, bool RFX>
-__global__ void __launch_bounds__(NB * NB, step_min_ctas<T, NDIM, NB>())
+__global__ void __launch_bounds__(step_threads<T, NDIM, NB>(), step_min_ctas<T, NDIM, NB>())
 step_kernel(StepArgsT<T> A) {
   using G = Geo<NDIM, NB>;
-  constexpr int NP = G::NP, P2 = G::P2, NZ = G::NZ, S = G::S, NT = G::NT;
+  constexpr int NP = G::NP, P2 = G::P2, NZ = G::NZ, S = G::S;
+  constexpr int NT = step_threads<T, NDIM, NB>(), CPT = NB * NB / NT;   // columns per thread
   constexpr int UPL = G::UPL, WPL = G::WPL, RW = G::RW, RING = G::RING, NFACE = G::NFACE;
   constexpr bool HAS_T = SCHEME != SCH_WENO;
   extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -470,14 +482,15 @@ step_kernel(StepArgsT<T> A) {
   __shared__ PushEntry spush[27];
 
   const int tid = threadIdx.x;
-  const int tx = tid % NB, ty = tid / NB;
-  const int cown = (ty + NG) * NP + (tx + NG);          // own column, full plane layout
-  const int rown = (ty + 1) * RW + (tx + 1);            // own column, ring layout
+  // the thread's column (CPT > 1: the current one of its columns in the update)
+  int tx = tid % NB, ty = tid / NB;
+  int cown = (ty + NG) * NP + (tx + NG);                // own column, full plane layout
+  int rown = (ty + 1) * RW + (tx + 1);                  // own column, ring layout
 
   // warp schedule of the per-plane work list (WorkList, build_schedule), the same on every
   // block; thread 0 copies it from the arguments with constant indices
-  constexpr int NW = WorkList<NDIM, NB>::NW;
-  constexpr int NPU = WorkList<NDIM, NB>::NPU;
+  constexpr int NW = WorkList<NDIM, NB, NT>::NW;
+  constexpr int NPU = WorkList<NDIM, NB, NT>::NPU;
   __shared__ int sched[NW][16];
   __shared__ RefluxLeaf srl;               // the block's face-register slot and coarse-side mask
   if (tid == 0) {
@@ -894,151 +907,161 @@ step_kernel(StepArgsT<T> A) {
       }
       const T* P0 = uslot(z);
       const T* T0 = HAS_T ? tslot(z) : nullptr;
-      T acc[NV];
-      if (SCHEME == SCH_WENO) {
+#pragma unroll 1
+      for (int cc = 0; cc < CPT; ++cc) {
+        if (CPT > 1) {
+          const int col = tid + cc * NT;
+          tx = col % NB;
+          ty = col / NB;
+          cown = (ty + NG) * NP + (tx + NG);
+          rown = (ty + 1) * RW + (tx + 1);
+        }
+        T acc[NV];
+        if (SCHEME == SCH_WENO) {
 #pragma unroll
-        for (int v = 0; v < NV; ++v) acc[v] = T(0);
-      } else {
-        ldw<T, P2>(P0, cown, acc);
-      }
-#pragma unroll
-      for (int v = 0; v < NV; ++v) {
-        const T fr = sfx[v * NFACE + ty * (NB + 1) + tx + 1];
-        const T fl = sfx[v * NFACE + ty * (NB + 1) + tx];
-        if (SCHEME == SCH_WENO) acc[v] -= (fr - fl) / dxT[0];
-        else acc[v] -= lam[0] * (fr - fl);
-      }
-#pragma unroll
-      for (int v = 0; v < NV; ++v) {
-        const T fr = sfy[v * NFACE + (ty + 1) * NB + tx];
-        const T fl = sfy[v * NFACE + ty * NB + tx];
-        if (SCHEME == SCH_WENO) acc[v] -= (fr - fl) / dxT[1];
-        else acc[v] -= lam[1] * (fr - fl);
-      }
-      // z faces
-      if (NDIM == 3) {
+          for (int v = 0; v < NV; ++v) acc[v] = T(0);
+        } else {
+          ldw<T, P2>(P0, cown, acc);
+        }
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
-          if (SCHEME == SCH_WENO) acc[v] -= (Fzhi[v] - Fzlo[v]) / dxT[2];
-          else acc[v] -= lam[2] * (Fzhi[v] - Fzlo[v]);
-          Fzlo[v] = Fzhi[v];
+          const T fr = sfx[v * NFACE + ty * (NB + 1) + tx + 1];
+          const T fl = sfx[v * NFACE + ty * (NB + 1) + tx];
+          if (SCHEME == SCH_WENO) acc[v] -= (fr - fl) / dxT[0];
+          else acc[v] -= lam[0] * (fr - fl);
         }
-      }
-      // sources
-      T s[NV];
 #pragma unroll
-      for (int v = 0; v < NV; ++v) s[v] = T(0);
-      T unext[NV];
-      if (NDIM == 3) ldw<T, P2>(uslot(z + 1), cown, unext);
-      if (A.eglm) {
-        if (SCHEME == SCH_LF) {
-          T tm[NV], tq[NV];
-#pragma unroll
-          for (int v = 0; v < NV; ++v) tm[v] = T(0);
-          if (NDIM == 3) {
-            if (G::CARRY) {
-              tm[BZ] = zm_bz;                                   // the z-1 values the sources read
-              tm[PSI] = zm_psi;
-            } else {
-              ldw<T, RING>(tslot(z - 1), rown, tm);
-            }
-            ldw<T, RING>(tslot(z + 1), rown, tq);
-          }
-          eglm_src_col<T, NDIM>(T0, RING, RW, rown, tm, tq, dx2, s);
-        } else {
-          eglm_src_col<T, NDIM>(P0, P2, NP, cown, uprev, unext, dx2, s);
+        for (int v = 0; v < NV; ++v) {
+          const T fr = sfy[v * NFACE + (ty + 1) * NB + tx];
+          const T fl = sfy[v * NFACE + ty * NB + tx];
+          if (SCHEME == SCH_WENO) acc[v] -= (fr - fl) / dxT[1];
+          else acc[v] -= lam[1] * (fr - fl);
         }
-      }
-      if (RES) {
-        T jm[3] = {T(0), T(0), T(0)}, jq[3] = {T(0), T(0), T(0)};
+        // z faces
         if (NDIM == 3) {
-          const T* j2 = jslot(z + 1);
-#pragma unroll
-          for (int q = 0; q < 3; ++q) {
-            jm[q] = G::CARRY ? zm_j[q] : jslot(z - 1)[q * RING + rown];
-            jq[q] = j2[q * RING + rown];
-          }
-        }
-        resist_src_col<T, NDIM, NP, RW>(jslot(z), rown, jm, jq, P0, cown, uprev, unext, dx2, eta, s);
-      }
-      // update and write
-      T out[NV];
-      const size_t gofs = (size_t)z * P2 + cown;
-      if (SCHEME == SCH_WENO) {
-        if (STAGE == 1) {
-#pragma unroll
-          for (int v = 0; v < NV; ++v) out[v] = P0[v * P2 + cown] + dt * (acc[v] + s[v]);
-        } else {
 #pragma unroll
           for (int v = 0; v < NV; ++v) {
-            T un = bb[(size_t)v * S + gofs];
-            out[v] = T(0.5) * ((un + P0[v * P2 + cown]) + dt * (acc[v] + s[v]));
+            if (SCHEME == SCH_WENO) acc[v] -= (Fzhi[v] - Fzlo[v]) / dxT[2];
+            else acc[v] -= lam[2] * (Fzhi[v] - Fzlo[v]);
+            Fzlo[v] = Fzhi[v];
           }
+        }
+        // sources
+        T s[NV];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) s[v] = T(0);
+        T unext[NV];
+        if (NDIM == 3) ldw<T, P2>(uslot(z + 1), cown, unext);
+        if (A.eglm) {
+          if (SCHEME == SCH_LF) {
+            T tm[NV], tq[NV];
+#pragma unroll
+            for (int v = 0; v < NV; ++v) tm[v] = T(0);
+            if (NDIM == 3) {
+              if (G::CARRY) {
+                tm[BZ] = zm_bz;                                   // the z-1 values the sources read
+                tm[PSI] = zm_psi;
+              } else {
+                ldw<T, RING>(tslot(z - 1), rown, tm);
+              }
+              ldw<T, RING>(tslot(z + 1), rown, tq);
+            }
+            eglm_src_col<T, NDIM>(T0, RING, RW, rown, tm, tq, dx2, s);
+          } else {
+            eglm_src_col<T, NDIM>(P0, P2, NP, cown, uprev, unext, dx2, s);
+          }
+        }
+        if (RES) {
+          T jm[3] = {T(0), T(0), T(0)}, jq[3] = {T(0), T(0), T(0)};
+          if (NDIM == 3) {
+            const T* j2 = jslot(z + 1);
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+              jm[q] = G::CARRY ? zm_j[q] : jslot(z - 1)[q * RING + rown];
+              jq[q] = j2[q * RING + rown];
+            }
+          }
+          resist_src_col<T, NDIM, NP, RW>(jslot(z), rown, jm, jq, P0, cown, uprev, unext, dx2, eta, s);
+        }
+        // update and write
+        T out[NV];
+        const size_t gofs = (size_t)z * P2 + cown;
+        if (SCHEME == SCH_WENO) {
+          if (STAGE == 1) {
+#pragma unroll
+            for (int v = 0; v < NV; ++v) out[v] = P0[v * P2 + cown] + dt * (acc[v] + s[v]);
+          } else {
+#pragma unroll
+            for (int v = 0; v < NV; ++v) {
+              T un = bb[(size_t)v * S + gofs];
+              out[v] = T(0.5) * ((un + P0[v * P2 + cown]) + dt * (acc[v] + s[v]));
+            }
+            out[PSI] = out[PSI] * damp;
+          }
+        } else {
+#pragma unroll
+          for (int v = 0; v < NV; ++v) out[v] = acc[v] + dt * s[v];
           out[PSI] = out[PSI] * damp;
         }
-      } else {
 #pragma unroll
-        for (int v = 0; v < NV; ++v) out[v] = acc[v] + dt * s[v];
-        out[PSI] = out[PSI] * damp;
-      }
+        for (int v = 0; v < NV; ++v) ob[(size_t)v * S + gofs] = out[v];
+        if (A.pushes) {
+          // the two interior layers next to a face/edge/corner go into the facing ghost
+          // region of the same-level neighbour there (padded 2,3 -> low side, NB,NB+1 -> high)
+          const int x = tx + NG, y = ty + NG;
+          const int fx = x < 2 * NG ? -1 : (x >= NB ? 1 : 0);
+          const int fy = y < 2 * NG ? -1 : (y >= NB ? 1 : 0);
+          const int fz = NDIM == 3 ? (z < 2 * NG ? -1 : (z >= NB ? 1 : 0)) : 0;
+          if (fx | fy | fz) {
+            for (int kz = 0; kz < (fz ? 2 : 1); ++kz)
+              for (int ky = 0; ky < (fy ? 2 : 1); ++ky)
+                for (int kx = 0; kx < (fx ? 2 : 1); ++kx) {
+                  const int ex = kx ? fx : 0, ey = ky ? fy : 0, ez = kz ? fz : 0;
+                  if (!(ex | ey | ez)) continue;
+                  const PushEntry pe = spush[(ex + 1) + 3 * (ey + 1) + 9 * (ez + 1)];
+                  if (pe.dst < 0) continue;
+                  T* db = A.u_out + (size_t)pe.dst * NV * S;
+                  const size_t dc = ((size_t)(z + pe.off[2]) * NP + (y + pe.off[1])) * NP + (x + pe.off[0]);
 #pragma unroll
-      for (int v = 0; v < NV; ++v) ob[(size_t)v * S + gofs] = out[v];
-      if (A.pushes) {
-        // the two interior layers next to a face/edge/corner go into the facing ghost
-        // region of the same-level neighbour there (padded 2,3 -> low side, NB,NB+1 -> high)
-        const int x = tx + NG, y = ty + NG;
-        const int fx = x < 2 * NG ? -1 : (x >= NB ? 1 : 0);
-        const int fy = y < 2 * NG ? -1 : (y >= NB ? 1 : 0);
-        const int fz = NDIM == 3 ? (z < 2 * NG ? -1 : (z >= NB ? 1 : 0)) : 0;
-        if (fx | fy | fz) {
-          for (int kz = 0; kz < (fz ? 2 : 1); ++kz)
-            for (int ky = 0; ky < (fy ? 2 : 1); ++ky)
-              for (int kx = 0; kx < (fx ? 2 : 1); ++kx) {
-                const int ex = kx ? fx : 0, ey = ky ? fy : 0, ez = kz ? fz : 0;
-                if (!(ex | ey | ez)) continue;
-                const PushEntry pe = spush[(ex + 1) + 3 * (ey + 1) + 9 * (ez + 1)];
-                if (pe.dst < 0) continue;
-                T* db = A.u_out + (size_t)pe.dst * NV * S;
-                const size_t dc = ((size_t)(z + pe.off[2]) * NP + (y + pe.off[1])) * NP + (x + pe.off[0]);
-#pragma unroll
-                for (int v = 0; v < NV; ++v) db[(size_t)v * S + dc] = out[v];
-              }
-        }
-      }
-      // cells next to a face where this block is the coarse side change again in the reflux
-      // pass, which checks them and adds them to the fused diagnostics itself
-      const int cm = RFX ? srl.coarse_mask : 0;
-      const bool refluxed = RFX && cm != 0 && (((cm & 1) && tx == 0) || ((cm & 2) && tx == NB - 1) ||
-                                        ((cm & 4) && ty == 0) || ((cm & 8) && ty == NB - 1) ||
-                                        (NDIM == 3 && (((cm & 16) && z == NG) || ((cm & 32) && z == NB + NG - 1))));
-      if (STAGE != 1 && !refluxed) {
-        bool fin = true;
-#pragma unroll
-        for (int v = 0; v < NV; ++v) fin = fin && isfinite(out[v]);
-        if (!fin) errbits |= 1u;
-        else {
-          T pr = pressure<T>(out, P);
-          if (!(out[RHO] > T(0)) || pr < T(0)) errbits |= 2u;
-          if (A.dyn_next) {
-            T am = alpha_p<T, 0>(out, pr, P);
-            am = dmax<T>(am, alpha_p<T, 1>(out, pr, P));
-            if (NDIM == 3) am = dmax<T>(am, alpha_p<T, 2>(out, pr, P));
-            alpha_max = dmax<T>(alpha_max, am);
+                  for (int v = 0; v < NV; ++v) db[(size_t)v * S + dc] = out[v];
+                }
           }
         }
-        if (!fin) alpha_max = (T)NAN;
-        if (A.sums) {
+        // cells next to a face where this block is the coarse side change again in the reflux
+        // pass, which checks them and adds them to the fused diagnostics itself
+        const int cm = RFX ? srl.coarse_mask : 0;
+        const bool refluxed = RFX && cm != 0 && (((cm & 1) && tx == 0) || ((cm & 2) && tx == NB - 1) ||
+                                          ((cm & 4) && ty == 0) || ((cm & 8) && ty == NB - 1) ||
+                                          (NDIM == 3 && (((cm & 16) && z == NG) || ((cm & 32) && z == NB + NG - 1))));
+        if (STAGE != 1 && !refluxed) {
+          bool fin = true;
 #pragma unroll
-          for (int v = 0; v < NV; ++v) {
-            // Kahan: csum - ccmp carries the column sum
-            const T y = out[v] - ccmp[v];
-            const T t = csum[v] + y;
-            ccmp[v] = (t - csum[v]) - y;
-            csum[v] = t;
+          for (int v = 0; v < NV; ++v) fin = fin && isfinite(out[v]);
+          if (!fin) errbits |= 1u;
+          else {
+            T pr = pressure<T>(out, P);
+            if (!(out[RHO] > T(0)) || pr < T(0)) errbits |= 2u;
+            if (A.dyn_next) {
+              T am = alpha_p<T, 0>(out, pr, P);
+              am = dmax<T>(am, alpha_p<T, 1>(out, pr, P));
+              if (NDIM == 3) am = dmax<T>(am, alpha_p<T, 2>(out, pr, P));
+              alpha_max = dmax<T>(alpha_max, am);
+            }
+          }
+          if (!fin) alpha_max = (T)NAN;
+          if (A.sums) {
+#pragma unroll
+            for (int v = 0; v < NV; ++v) {
+              // Kahan: csum - ccmp carries the column sum
+              const T y = out[v] - ccmp[v];
+              const T t = csum[v] + y;
+              ccmp[v] = (t - csum[v]) - y;
+              csum[v] = t;
+            }
           }
         }
-      }
-      if (NDIM == 3) ldw<T, P2>(P0, cown, uprev);
+        if (NDIM == 3) ldw<T, P2>(P0, cown, uprev);
+      }  // the thread's columns
       if (RFX && SCHEME != SCH_LF && srl.slot >= 0 && tid < 4 * NB) {
         // this plane's x and y boundary faces (still in the face buffer) into the face
         // register (LF writes them where it computes them: either place suits one scheme's
