@@ -615,10 +615,19 @@ step_kernel(StepArgsT<T> A) {
             if constexpr (std::is_same<T, float>::value) {
               // the two half-states u +- phi/2 in the lanes of a float2
               float2 ab[NV], fab[NV];
+              // the limited slopes of two variables at a time
 #pragma unroll
-              for (int v = 0; v < NV; ++v) {
-                const T ph = limiter<T, LIM>(w[v] - plm[v * P2 + cm], plp[v * P2 + cp] - w[v]);
-                ab[v] = pair::fma(pair::splat(ph), make_float2(0.5f, -0.5f), pair::splat(w[v]));
+              for (int v = 0; v + 1 < NV; v += 2) {
+                const float2 wv = make_float2(w[v], w[v + 1]);
+                const float2 lo = make_float2(plm[v * P2 + cm], plm[(v + 1) * P2 + cm]);
+                const float2 hi = make_float2(plp[v * P2 + cp], plp[(v + 1) * P2 + cp]);
+                const float2 ph = pair::limiter2<LIM>(pair::sub(wv, lo), pair::sub(hi, wv));
+                ab[v] = pair::fma(pair::splat(ph.x), make_float2(0.5f, -0.5f), pair::splat(w[v]));
+                ab[v + 1] = pair::fma(pair::splat(ph.y), make_float2(0.5f, -0.5f), pair::splat(w[v + 1]));
+              }
+              {
+                const T ph = limiter<T, LIM>(w[NV - 1] - plm[(NV - 1) * P2 + cm], plp[(NV - 1) * P2 + cp] - w[NV - 1]);
+                ab[NV - 1] = pair::fma(pair::splat(ph), make_float2(0.5f, -0.5f), pair::splat(w[NV - 1]));
               }
               pair::flux2<D, !(NDIM == 3 && NB == 16)>(ab, P, fab, nullptr);
 #pragma unroll
