@@ -317,8 +317,11 @@ int map_read_leaves_async(map_pool* pool, double* u_out);
 int map_read_leaves_async_f32(map_pool* pool, float* u_out);
 
 /* (No counterpart in the paper.)  Asynchronous map_get_speeds: out[n_problems][5] is
- * written when the pool stream reaches
- * this point (pinned memory for a truly asynchronous copy); no synchronisation. */
+ * written when the pool stream reaches this point; no synchronisation.  Page-locked host
+ * memory that CUDA maps into the device (cudaHostAlloc, cudaHostRegister, a framework's
+ * pinned tensors) is stored to by a one-warp kernel on the pool stream, so the values do not
+ * wait behind a large copy on a copy engine (an overlapped map_read_leaves_async); other host
+ * memory receives a copy on the pool stream. */
 int map_get_speeds_async(map_pool* pool, double* out);
 
 /* Per problem: dt, c_h, c_p, psi damping factor, alpha_g of the last CFL reduction

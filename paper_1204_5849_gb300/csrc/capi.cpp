@@ -1364,6 +1364,16 @@ int map_get_speeds_async(map_pool* pool, double* out) {
   static_assert(offsetof(ProbDyn, dt) == 0 && offsetof(ProbDyn, ch) == 8 && offsetof(ProbDyn, cp) == 16 &&
                 offsetof(ProbDyn, damp) == 24 && offsetof(ProbDyn, alpha_g) == 32,
                 "dt, c_h, c_p, damping, alpha_g lead ProbDyn");
+  // page-locked host memory mapped into the device's address space: a one-warp kernel stores
+  // the values there.  A small device-to-host copy on the pool stream would instead wait
+  // behind a large state copy running on the copy engine of that direction (an overlapped
+  // map_read_leaves_async), and hold the next step's launches back with it.
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, out) == cudaSuccess && a.type == cudaMemoryTypeHost && a.devicePointer) {
+    CK(launch_speeds_out(pool->dyn, pool->nprob, (double*)a.devicePointer, pool->stream, &pool->launches));
+    return MAP_OK;
+  }
+  cudaGetLastError();   // an unregistered pointer is not an error
   CK(cudaMemcpy2DAsync(out, 5 * sizeof(double), pool->dyn, sizeof(ProbDyn), 5 * sizeof(double), pool->nprob,
                        cudaMemcpyDeviceToHost, pool->stream));
   return MAP_OK;

@@ -55,6 +55,26 @@ __global__ void zero_alpha_kernel(ProbDyn* dyn, int n) {
   }
 }
 
+// dt, c_h, c_p, damping and alpha_g of every problem, stored by the GPU itself into host
+// memory it can address (page-locked and mapped): no copy engine takes part, so the store does
+// not queue behind the large state copies that the copy engines may be running.
+__global__ void speeds_out_kernel(const ProbDyn* __restrict__ dyn, int n, double* __restrict__ out) {
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
+    double* o = out + 5 * (size_t)p;
+    o[0] = dyn[p].dt;
+    o[1] = dyn[p].ch;
+    o[2] = dyn[p].cp;
+    o[3] = dyn[p].damp;
+    o[4] = dyn[p].alpha_g;
+  }
+}
+
+cudaError_t launch_speeds_out(const ProbDyn* dyn, int n, double* out, cudaStream_t s, long long* cnt) {
+  if (cnt) ++*cnt;
+  speeds_out_kernel<<<1, 128, 0, s>>>(dyn, n, out);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_finalize(const FinalizeLaunch& L, cudaStream_t s, long long* cnt) {
   if (cnt) ++*cnt;
   finalize_kernel<<<(L.nprob + 127) / 128, 128, 0, s>>>(L);

@@ -324,5 +324,7 @@ cudaError_t launch_step_hllc_rfx_f32(const KernelConfig&, const StepLaunch&, cud
 
 cudaError_t launch_finalize(const FinalizeLaunch&, cudaStream_t, long long*);
 cudaError_t launch_zero_alpha(ProbDyn* dyn, int nprob, cudaStream_t, long long*);
+// out: device address of host memory (n x 5 doubles) that the GPU can store to
+cudaError_t launch_speeds_out(const ProbDyn* dyn, int nprob, double* out, cudaStream_t, long long*);
 
 }  // namespace mapgb

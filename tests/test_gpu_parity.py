@@ -524,6 +524,35 @@ def test_async_writes_and_reads_match_the_synchronous_calls(gpulib, prec):
     np.testing.assert_array_equal(a.read_leaves(), b.read_leaves())
 
 
+def test_async_speeds_into_pinned_and_pageable_memory(gpulib):
+    """map_get_speeds_async on a pool of 130 problems (more than one warp of them): into pinned
+    host memory (stored there by the GPU) and into pageable memory (a copy), each after its own
+    step, equal to map_get_speeds of that step."""
+    import torch
+    from workloads.problems import ensemble_initial
+    mesh = w.ensemble_mesh(16, [32, 16, 48] * 43 + [16])
+    assert len(mesh.problems) == 130
+    U0 = ensemble_initial(mesh)
+    p = P(scheme="mmc", limiter="minmod")
+    a = pool_for(mesh, 1, U0)
+    b = pool_for(mesh, 1, U0)
+    pinned = torch.full((3, len(mesh.problems), 5), -1.0, dtype=torch.float64, pin_memory=True)
+    pageable = np.full((3, len(mesh.problems), 5), -1.0)
+    for k in range(3):
+        a.advance(p, 1)
+        a.speeds_async_ptr(pinned[k].data_ptr())
+        a.speeds_async_ptr(pageable[k].ctypes.data)
+    assert a.check() == 0                     # synchronises the pool stream
+    for k in range(3):
+        b.advance(p, 1)
+        ref = b.speeds()
+        np.testing.assert_array_equal(pinned[k].numpy(), ref)
+        np.testing.assert_array_equal(pageable[k], ref)
+    assert np.all(pinned.numpy()[:, :, 0] > 0)
+    a.close()
+    b.close()
+
+
 @pytest.mark.parametrize("prec", [0, 1])
 def test_async_state_reads_match_the_synchronous_read(gpulib, prec):
     """map_read_leaves_async (FP64 layout) and its FP32 form after every step of a write /
