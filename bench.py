@@ -479,12 +479,13 @@ def main():
         return
 
     # -------- end to end through the public API: pinned H2D of the inputs, D2H result ----
-    # every step copies the FP64 host state in (map_write_leaves_async: its own copy stream
+    # every step copies the host state in (map_write_leaves_async[_f32]: its own copy stream
     # and two staging buffers, so the copy for step k+1 overlaps step k), reads the step's
-    # result -- the new state (map_read_leaves_async: packed on the pool stream, copied out on
-    # a second copy stream into alternating pinned buffers) and dt, c_h, c_p, damping,
-    # alpha_g -- back into pinned memory; one synchronisation at the end.  The same with the
-    # blocking calls is reported as e2e.blocking_value.
+    # result -- the new state (map_read_leaves_async[_f32]: packed on the pool stream, copied
+    # out on a second copy stream into alternating pinned buffers) and dt, c_h, c_p, damping,
+    # alpha_g -- back into pinned memory; one synchronisation at the end.  e2e.value uses the
+    # FP32 host layout, the FP32 pool's own precision; e2e.fp64_host the FP64 layout, whose
+    # blocking calls give e2e.blocking_value_fp64_host.
     pinned = torch.empty(U0.shape, dtype=torch.float64, pin_memory=True)
     pinned.numpy()[...] = U0
     outs = [torch.empty(U0.shape, dtype=torch.float64, pin_memory=True) for _ in range(2)]
@@ -634,15 +635,18 @@ def main():
                              "bytes_per_cell": BYTES_PER_CELL_F32, "peak_source": f"{peak_kind} hbm_gbs",
                              "dram_gbs": traffic / (k_ms * 1e-3) / 1e9,
                              "dram_frac": traffic / (k_ms * 1e-3) / 1e9 / hbm}},
-        "e2e": {"value": e2e_val, "unit": METRIC, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                "steps": ne, "copies": "FP64 host state in (pinned, async copy stream, double-buffered staging), "
-                                       "the new FP64 state and the step's speeds out (pinned, async: "
-                                       "map_read_leaves_async on a second copy stream); one sync at the end",
-                "blocking_value": e2e_blocking,
-                "fp32_host": {"value": e2e32, "h2d_bytes_per_step": U0.nbytes // 2,
-                              "d2h_bytes_per_step": U0.nbytes // 2 + 5 * 8 * len(mesh.problems),
-                              "copies": "FP32 host state in (map_write_leaves_async_f32), FP32 state "
-                                        "(map_read_leaves_async_f32) and speeds out"}},
+        "e2e": {"value": e2e32, "unit": METRIC, "h2d_bytes_per_step": U0.nbytes // 2,
+                "d2h_bytes_per_step": U0.nbytes // 2 + 5 * 8 * len(mesh.problems), "steps": ne,
+                "host_layout": "fp32: the FP32 pool's own storage precision (an FP64 copy-in gives the "
+                               "same device state bit for bit; the FP32 read-back is exact)",
+                "copies": "FP32 host state in (pinned, map_write_leaves_async_f32: async copy stream, "
+                          "double-buffered staging), the new FP32 state and the step's speeds out "
+                          "(pinned, map_read_leaves_async_f32 on a second copy stream, "
+                          "map_get_speeds_async); one sync at the end",
+                "fp64_host": {"value": e2e_val, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                              "copies": "the same loop with the FP64 host layout both ways "
+                                        "(map_write_leaves_async, map_read_leaves_async)"},
+                "blocking_value_fp64_host": e2e_blocking},
         "gpu_launches": launches,
         "clocks": clk,
         "fp64_plain": {"value": f64_val, "unit": METRIC, "ms_per_step": f64_ms / n64, "steps": n64},
