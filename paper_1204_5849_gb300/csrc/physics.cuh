@@ -409,11 +409,15 @@ __device__ __forceinline__ void flux2(const float2* w, const Phys<float>& P, flo
   }
 }
 
-// Lax-Friedrichs flux of the face whose left state is lane x and right state lane y
+// Lax-Friedrichs flux of the face whose left state is lane x and right state lane y, less
+// pt_ref in its normal-momentum component: that component of each state carries the total
+// pressure p + B^2/2, and the offset, the same for every face whose fluxes the update
+// subtracts, keeps it from taking the FP32 digits of the small terms added to it
 template <int D, bool OOL = true>
-__device__ __forceinline__ void lf_flux2(const float2* ab, const Phys<float>& P, float* f) {
+__device__ __forceinline__ void lf_flux2(const float2* ab, const Phys<float>& P, float* f, float pt_ref = 0.0f) {
   float2 F[NV], al;
   flux2<D, OOL>(ab, P, F, &al);
+  F[MX + D] = sub(F[MX + D], splat(pt_ref));
   const float a = al.x > al.y ? al.x : al.y;
 #pragma unroll
   for (int v = 0; v < NV; ++v) {

@@ -469,6 +469,9 @@ step_kernel(StepArgsT<T> A) {
   constexpr int NT = step_threads<T, NDIM, NB>(), CPT = NB * NB / NT;   // columns per thread
   constexpr int UPL = G::UPL, WPL = G::WPL, RW = G::RW, RING = G::RING, NFACE = G::NFACE;
   constexpr bool HAS_T = SCHEME != SCH_WENO;
+  // PREF: the FP32 LF faces carry their normal-momentum flux less a per-block reference total
+  // pressure (kc[16]); the offset cancels in every flux difference of the update
+  constexpr bool PREF = std::is_same<T, float>::value && SCHEME == SCH_LF && FLX == FLX_LF;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw);           // UPL mbarriers
   volatile int* status = reinterpret_cast<volatile int*>(smem_raw + 48);
@@ -554,6 +557,14 @@ step_kernel(StepArgsT<T> A) {
       return good;
     };
 
+    // p + B^2/2 at cell c of a full plane (the faces' reference, any value would cancel)
+    auto total_pressure = [&](const T* pl, int c) -> T {
+      T w[NV];
+      ldw<T, P2>(pl, c, w);
+      const T b2 = w[BX] * w[BX] + w[BY] * w[BY] + w[BZ] * w[BZ];
+      const T m2 = w[MX] * w[MX] + w[MY] * w[MY] + w[MZ] * w[MZ];
+      return A.gm1 * (w[EN] - T(0.5) * m2 / w[RHO] - T(0.5) * b2) + T(0.5) * b2;
+    };
     // the block constants are valid after the first barrier of the block
     Phys<T> P;
     T lam[3], lamh[3], dx2[3], dxT[3], dt, hdt, damp;
@@ -702,7 +713,7 @@ step_kernel(StepArgsT<T> A) {
           ab[v] = pair::fma(ph, make_float2(0.5f, -0.5f), tt);
         }
         exch_xy(yd, ab);
-        pair::lf_flux2<0, !(NDIM == 3 && NB == 16)>(ab, *reinterpret_cast<const Phys<float>*>(&P), reinterpret_cast<float*>(F));
+        pair::lf_flux2<0, !(NDIM == 3 && NB == 16)>(ab, *reinterpret_cast<const Phys<float>*>(&P), reinterpret_cast<float*>(F), (float)kc[16]);
       } else {
         T a[NV], b[NV];
 #pragma unroll
@@ -735,7 +746,8 @@ step_kernel(StepArgsT<T> A) {
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
         T* rv = r + (size_t)v * NB * NB;
-        *rv = STAGE == 0 ? F[v] : (STAGE == 1 ? T(0.5) * F[v] : *rv + T(0.5) * F[v]);
+        const T fv = (PREF && v == MX + side / 2) ? F[v] + kc[16] : F[v];   // the full flux
+        *rv = STAGE == 0 ? fv : (STAGE == 1 ? T(0.5) * fv : *rv + T(0.5) * fv);
       }
     };
 
@@ -787,7 +799,7 @@ step_kernel(StepArgsT<T> A) {
           const float2 tt = make_float2(t0p[v * RING + rown], t1p[v * RING + rown]);
           ab[v] = pair::fma(ph, make_float2(0.5f, -0.5f), tt);
         }
-        pair::lf_flux2<2, !(NDIM == 3 && NB == 16)>(ab, *reinterpret_cast<const Phys<float>*>(&P), reinterpret_cast<float*>(F));
+        pair::lf_flux2<2, !(NDIM == 3 && NB == 16)>(ab, *reinterpret_cast<const Phys<float>*>(&P), reinterpret_cast<float*>(F), (float)kc[16]);
       } else {
         T a[NV], b[NV];
 #pragma unroll
@@ -875,12 +887,14 @@ step_kernel(StepArgsT<T> A) {
         }
         if (!ok) break;
         if (z == 0) read_constants();
+        if (PREF && z == 0 && tid == 0) kc[16] = total_pressure(uslot(NG), cown);   // read after the next barrier
         if (tid == 0 && z >= 1 && z + 3 <= NP - 1) issue_plane(z + 3);   // slot of z-1
         work(z + 1, PRED, z, z >= NG);                           // predictor z+1, faces of z
       } else {
         ok = wait_plane(0);
         if (!ok) break;
         read_constants();
+        if (PREF && tid == 0) kc[16] = total_pressure(uslot(0), cown);           // read after the next barrier
         if (PRED) {
           work(0, true, 0, false);
           __syncthreads();

@@ -941,10 +941,13 @@ def _wave_error(G, R, amp=1e-6):
 
 def test_fp32_alfven3d_small(gpulib):
     """Config-2 shape at 32^3 against the oracle after 10 steps: the background (rho, B_x, e)
-    to 1e-6 of its size, and the 1e-6 wave itself (m_y, m_z, B_y, B_z) to 2e-3 of its
-    amplitude in L1 (1e-2 in Linf).  FP32 carries the wave on an O(1) background: at this
-    resolution its rounding is 5e-4 of the amplitude (L1, measured); at 256^3 it is 1.7e-5
-    after 200 steps, below the scheme's own error against the closed form (7e-5)."""
+    to 1e-6 of its size, and the 1e-6 wave itself (m_y, m_z, B_y, B_z) to 1e-6 of its
+    amplitude in L1 (3e-6 in Linf; measured 6e-8 and 2e-7).  The normal-momentum flux of a
+    face carries the total pressure p + B^2/2 = 0.6, and the wave's dissipation term there
+    (about 1e-7) is near its FP32 spacing: the FP32 LF faces subtract a per-block reference
+    total pressure before the LF combination (it cancels in the update).  Without that offset
+    this error was 5e-4 of the amplitude (L1) and 3e-3 (Linf), concentrated at the wave's
+    crests, where the limiter leaves the largest jumps to dissipate."""
     from paper_1204_5849_gb300 import MAP_FP32_FIX64
     cfg = config_alfven3d(small=True)
     mesh = cfg["mesh"]
@@ -957,7 +960,7 @@ def test_fp32_alfven3d_small(gpulib):
     for v in (0, 4, 7):
         assert np.abs(G[:, v] - R[:, v]).mean() / np.abs(R[:, v]).mean() <= 1e-6
     l1, linf = _wave_error(G, R)
-    assert l1 <= 2e-3 and linf <= 1e-2, (l1, linf)
+    assert l1 <= 1e-6 and linf <= 3e-6, (l1, linf)
 
 
 # --- config 2 at full size (256^3): sampled blocks against the oracle's block step ------
