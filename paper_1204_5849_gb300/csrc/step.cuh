@@ -559,11 +559,10 @@ step_kernel(StepArgsT<T> A) {
 
     // p + B^2/2 at cell c of a full plane (the faces' reference, any value would cancel)
     auto total_pressure = [&](const T* pl, int c) -> T {
-      T w[NV];
-      ldw<T, P2>(pl, c, w);
-      const T b2 = w[BX] * w[BX] + w[BY] * w[BY] + w[BZ] * w[BZ];
-      const T m2 = w[MX] * w[MX] + w[MY] * w[MY] + w[MZ] * w[MZ];
-      return A.gm1 * (w[EN] - T(0.5) * m2 / w[RHO] - T(0.5) * b2) + T(0.5) * b2;
+      auto q = [&](int v) { return pl[v * P2 + c]; };
+      const T b2 = q(BX) * q(BX) + q(BY) * q(BY) + q(BZ) * q(BZ);
+      const T m2 = q(MX) * q(MX) + q(MY) * q(MY) + q(MZ) * q(MZ);
+      return A.gm1 * (q(EN) - T(0.5) * m2 / q(RHO) - T(0.5) * b2) + T(0.5) * b2;
     };
     // the block constants are valid after the first barrier of the block
     Phys<T> P;
@@ -746,7 +745,9 @@ step_kernel(StepArgsT<T> A) {
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
         T* rv = r + (size_t)v * NB * NB;
-        const T fv = (PREF && v == MX + side / 2) ? F[v] + kc[16] : F[v];   // the full flux
+        // the full flux: the normal-momentum component gets the faces' reference back
+        const bool vn = (v == MX && side < 2) || (v == MY && (side == 2 || side == 3)) || (v == MZ && side >= 4);
+        const T fv = (PREF && vn) ? F[v] + kc[16] : F[v];
         *rv = STAGE == 0 ? fv : (STAGE == 1 ? T(0.5) * fv : *rv + T(0.5) * fv);
       }
     };
