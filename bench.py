@@ -43,7 +43,7 @@ FLOPS_PER_CELL = 1652.0
 SMS, FP32_LANES_PER_SM = 152, 128
 # DRAM bytes (read + write) of one step-kernel launch on the 128^3 case (512 blocks),
 # from an ncu capture of the current kernel; traffic grows with the block count.
-STEP_KERNEL_DRAM_BYTES_512_BLOCKS = 162.774016e6 + 107.612928e6
+STEP_KERNEL_DRAM_BYTES_512_BLOCKS = 162.622464e6 + 107.649024e6
 
 
 NAMES = ("rho", "mx", "my", "mz", "bx", "by", "bz", "e", "psi")

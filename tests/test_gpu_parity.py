@@ -1001,7 +1001,7 @@ def test_config2_full_size_sampled(gpulib):
                 for v in (0, 4, 7):
                     assert np.abs(G[b, v] - R[0, v]).mean() / np.abs(R[0, v]).mean() <= 1e-6
                 l1, linf = _wave_error(G[b].reshape(1, 9, -1), R.reshape(1, 9, -1))
-                assert l1 <= 1e-5 and linf <= 2e-4, (b, l1, linf)
+                assert l1 <= 5e-7 and linf <= 1e-6, (b, l1, linf)     # measured <= 2.8e-8, 9.1e-8
         pool.close()
 
 
