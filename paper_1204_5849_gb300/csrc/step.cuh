@@ -62,7 +62,7 @@ struct Geo {
   static constexpr int P2 = NP * NP;
   static constexpr int NZ = NDIM == 3 ? NP : 1;
   static constexpr int S = NZ * P2;
-  static constexpr int NT = NB * NB;
+  static constexpr int NCOL = NB * NB;                 // interior columns (threads: step_threads)
   static constexpr int UPL = NDIM == 3 ? 4 : 1;   // u planes z..z+2 and one in flight
   // u~ and J ring planes.  3D 8^3: planes z and z+1 -- the update of plane z reads plane
   // z-1 only at its own column, and only u~ B_z, psi and J, which are carried in registers
