@@ -265,12 +265,22 @@ def test_fp64_reflux_off_matches_oracle(gpulib):
     assert rel_max(pool.read_leaves(), orc.get_state()).max() <= 1e-12
 
 
+_CONSERVING_MESHES = {
+    "3d_nb8_periodic": _REFLUX_MESHES["3d_nb8_periodic"],
+    # 2D 16^2: the 128-thread FP32 kernels (two columns per thread), persistent by default
+    "2d_nb16_periodic": lambda: w.radial_amr_mesh(2, 16, (2, 2), 2, radii=(0.16, 0.34), bc=w.mesh.PERIODIC,
+                                                  lo=(0, 0, 0), hi=(1, 1, 1), centre=(0.5, 0.5, 0)),
+}
+
+
+@pytest.mark.parametrize("geom", sorted(_CONSERVING_MESHES))
 @pytest.mark.parametrize("prec", [0, 1])
 @pytest.mark.parametrize("scheme", ["mmc", "lf", "weno"])
-def test_reflux_conserves_on_gpu(gpulib, prec, scheme):
+def test_reflux_conserves_on_gpu(gpulib, prec, scheme, geom):
     """Every source off: the totals hold to round-off with reflux (the batched form, whose
     sums are reduced inside the kernels, and a fresh reduction agree), and drift without."""
-    mesh = _REFLUX_MESHES["3d_nb8_periodic"]()
+    mesh = _CONSERVING_MESHES[geom]()
+    assert len(set(mesh.leaves[:, 1].tolist())) > 1
     U0 = _mixed_state(mesh)
     drift = {}
     for rf in (0, 1):
