@@ -269,8 +269,23 @@ int map_autotune(map_pool* pool, const map_params* p, int reps, map_tune_result*
  * bound (about a second) would: the kernel records the timeout, still waits (bounded) for
  * the copies in flight so none lands after the block has left, and leaves; map_check then
  * returns MAP_ETIMEOUT.  The step's output is not valid afterwards: write the state again.
- * 0 restores normal waits. */
+ * The grid barrier of the conduction loop (map_set_conduction_loop) gives up at once as well;
+ * with on = 2 only that barrier does.  0 restores normal waits. */
 int map_test_fail_waits(map_pool* pool, int on);
+
+/* (No counterpart in the paper.)  How the thermal-conduction substeps of a step run (Sec.
+ * 3.6).  on = 1 (the default): where the pool allows it -- a single-level tree over the
+ * whole pool, every ghost region a copy (same-level neighbours, periodic or outflow
+ * boundaries), leaves of 2D 16^2, 2D 8^2 or 3D 8^3 cells, and every leaf's CTA resident on
+ * the device at once -- one cooperative launch runs all substeps.  Each CTA keeps its leaf's
+ * state on chip and exchanges the interior energy with the leaves it borders through the
+ * energy slices of the two spare state buffers, with one bounded grid barrier per substep.
+ * A barrier that waits about a second without completing sets the timeout bit, and
+ * map_check then returns MAP_ETIMEOUT.  Elsewhere, and while the pool's stream is being
+ * captured: one ghost fill and one kernel per substep, graph-replayed.  on = 0 always takes
+ * that path.  The arithmetic is the same either way.  Returns MAP_OK or MAP_EINVAL (NULL
+ * pool). */
+int map_set_conduction_loop(map_pool* pool, int on);
 
 /* (No counterpart in the paper.)  Sets the launch shape directly (grid 0 and weights 0
  * restore the defaults).  A persistent grid of the FP32 form gives each CTA a contiguous

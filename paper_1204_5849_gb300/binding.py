@@ -104,6 +104,7 @@ _SIGS = {
     "map_autotune": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
     "map_set_launch": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int]),
     "map_test_fail_waits": (C.c_int, [C.c_void_p, C.c_int]),
+    "map_set_conduction_loop": (C.c_int, [C.c_void_p, C.c_int]),
     "map_last_conduction": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "map_get_speeds": (C.c_int, [C.c_void_p, C.c_void_p]),
     "map_kernel_launches": (C.c_longlong, [C.c_void_p]),
@@ -487,9 +488,15 @@ class Pool:
         return {"grid": r.grid, "w_pred": r.w_pred, "w_face": r.w_face, "ms_default": r.ms_default,
                 "ms_best": r.ms_best, "trials": r.trials}
 
-    def test_fail_waits(self, on: bool):
-        """Test hook: the step kernel's plane waits give up at once (map_test_fail_waits)."""
-        self._ck(load().map_test_fail_waits(self.h, 1 if on else 0), "map_test_fail_waits")
+    def test_fail_waits(self, on):
+        """Test hook (map_test_fail_waits): True / 1 every bounded wait gives up at once, 2 only
+        the conduction loop's grid barrier, False / 0 normal waits."""
+        self._ck(load().map_test_fail_waits(self.h, 2 if on == 2 else (1 if on else 0)), "map_test_fail_waits")
+
+    def set_conduction_loop(self, on: bool):
+        """Conduction substeps in one cooperative launch where the pool allows it (default),
+        or one fill and one kernel per substep (map_set_conduction_loop)."""
+        self._ck(load().map_set_conduction_loop(self.h, 1 if on else 0), "map_set_conduction_loop")
 
     def set_launch(self, grid: int = 0, w_pred: int = 0, w_face: int = 0):
         self._ck(load().map_set_launch(self.h, int(grid), int(w_pred), int(w_face)), "map_set_launch")

@@ -623,6 +623,65 @@ __global__ void __launch_bounds__(256) reflux_kernel(RefluxLaunch L) {
 // one-cell ring are staged in shared memory first; other leaves read this leaf's energy only
 // through their own ghost copies, so the in-place write is safe.  Boundary face fluxes go to
 // the face register's energy slot as fluxes of e along +d (-F) for reflux.
+
+// T and kappa of one cell from its state
+template <typename T>
+__device__ __forceinline__ void cond_tk(const T* w, const Phys<T>& P, T k0, T& tt, T& kk) {
+  T p = pressure<T>(w, P);
+  if (p < T(0)) p = T(0);
+  tt = p / w[RHO];
+  kk = k0 * (tt * tt * sqrt(tt));
+}
+
+// The energy rate of one interior cell: r its ring-region index (strides ro), sT / sK the
+// ring's T and kappa, bmean(j, d, side) the face mean of B_j on face side of direction d,
+// face(d, F) sees the two face fluxes of direction d (the reflux registers take them).  Both
+// conduction kernels call it, so their arithmetic is the same.
+template <typename T, int NDIM, typename BM, typename FF>
+__device__ __forceinline__ T cond_rate(const T* sT, const T* sK, int r, const int* ro, const BlockGeo& gg,
+                                       T gmax, int mode, BM bmean, FF face) {
+  T acc = T(0);
+#pragma unroll
+  for (int d = 0; d < NDIM; ++d) {
+    T F[2];
+#pragma unroll
+    for (int side = 0; side < 2; ++side) {
+      const int rl = side ? r : r - ro[d], rr = rl + ro[d];
+      T gn = (sT[rr] - sT[rl]) / (T)gg.dx[d];
+      if (gmax > T(0)) gn = fmax(-gmax, fmin(gmax, gn));
+      const T kf = sqrt(sK[rl] * sK[rr]);
+      if (mode == 1) {
+        F[side] = kf * gn;
+      } else {
+        T bf[3], b2 = T(0);
+#pragma unroll
+        for (int j2 = 0; j2 < 3; ++j2) {
+          bf[j2] = bmean(j2, d, side);
+          b2 += bf[j2] * bf[j2];
+        }
+        if (!(b2 > T(0))) {
+          F[side] = T(0);
+        } else {
+          T bg = bf[d] * gn;
+#pragma unroll
+          for (int t = 0; t < NDIM; ++t) {
+            if (t == d) continue;
+            const T dxt = (T)gg.dx[t];
+            T gt = T(0.5) * ((sT[rl + ro[t]] - sT[rl - ro[t]]) / (T(2) * dxt) +
+                             (sT[rr + ro[t]] - sT[rr - ro[t]]) / (T(2) * dxt));
+            if (gmax > T(0)) gt = fmax(-gmax, fmin(gmax, gt));
+            bg += bf[t] * gt;
+          }
+          F[side] = kf * bf[d] * bg / b2;
+        }
+      }
+    }
+    face(d, F);
+    acc += (F[1] - F[0]) / (T)gg.dx[d];
+  }
+  return acc;
+}
+
 template <typename T, int NDIM, int NB>
 __global__ void __launch_bounds__(256) conduction_kernel(CondLaunch L) {
   using G = Geo<NDIM, NB>;
@@ -651,11 +710,7 @@ __global__ void __launch_bounds__(256) conduction_kernel(CondLaunch L) {
     const int c = ((NDIM == 3 ? rk + 1 : 0) * NP + rj + 1) * NP + ri + 1;
     T w[NV];
     load_global<T>(ub, S, c, w);
-    T p = pressure<T>(w, P);
-    if (p < T(0)) p = T(0);
-    const T tt = p / w[RHO];
-    sT[r] = tt;
-    sK[r] = k0 * (tt * tt * sqrt(tt));
+    cond_tk<T>(w, P, k0, sT[r], sK[r]);
   }
   __syncthreads();
   const int slot = L.freg ? L.refl[blk].slot : -1;
@@ -667,53 +722,163 @@ __global__ void __launch_bounds__(256) conduction_kernel(CondLaunch L) {
     const int r = ((NDIM == 3 ? k + 1 : 0) * R + j + 1) * R + i + 1;
     const int c = ((NDIM == 3 ? k + NG : 0) * NP + j + NG) * NP + i + NG;
     const int ic[3] = {i, j, k};
-    T acc = T(0);
-#pragma unroll
-    for (int d = 0; d < NDIM; ++d) {
-      T F[2];
-#pragma unroll
-      for (int side = 0; side < 2; ++side) {
-        const int rl = side ? r : r - ro[d], rr = rl + ro[d];
-        const int cl = side ? c : c - po[d], cr = cl + po[d];
-        T gn = (sT[rr] - sT[rl]) / (T)gg.dx[d];
-        if (gmax > T(0)) gn = fmax(-gmax, fmin(gmax, gn));
-        const T kf = sqrt(sK[rl] * sK[rr]);
-        if (L.mode == 1) {
-          F[side] = kf * gn;
-        } else {
-          T bf[3], b2 = T(0);
-#pragma unroll
-          for (int j2 = 0; j2 < 3; ++j2) {
-            bf[j2] = T(0.5) * (ub[(size_t)(BX + j2) * S + cl] + ub[(size_t)(BX + j2) * S + cr]);
-            b2 += bf[j2] * bf[j2];
-          }
-          if (!(b2 > T(0))) {
-            F[side] = T(0);
-          } else {
-            T bg = bf[d] * gn;
-#pragma unroll
-            for (int t = 0; t < NDIM; ++t) {
-              if (t == d) continue;
-              const T dxt = (T)gg.dx[t];
-              T gt = T(0.5) * ((sT[rl + ro[t]] - sT[rl - ro[t]]) / (T(2) * dxt) +
-                               (sT[rr + ro[t]] - sT[rr - ro[t]]) / (T(2) * dxt));
-              if (gmax > T(0)) gt = fmax(-gmax, fmin(gmax, gt));
-              bg += bf[t] * gt;
-            }
-            F[side] = kf * bf[d] * bg / b2;
-          }
-        }
-      }
+    auto bmean = [&](int j2, int d, int side) -> T {
+      const int cl = side ? c : c - po[d], cr = cl + po[d];
+      return T(0.5) * (ub[(size_t)(BX + j2) * S + cl] + ub[(size_t)(BX + j2) * S + cr]);
+    };
+    auto face = [&](int d, const T* F) {
       if (R0) {
         const int da = d == 0 ? 1 : 0, db = d == 2 ? 1 : 2;
         const int t0 = ic[da], t1 = NDIM == 3 ? ic[db] : 0;
         if (ic[d] == 0) R0[(size_t)(2 * d) * NV * NB2 + (size_t)EN * NB2 + t1 * NB + t0] = -F[0];
         if (ic[d] == NB - 1) R0[(size_t)(2 * d + 1) * NV * NB2 + (size_t)EN * NB2 + t1 * NB + t0] = -F[1];
       }
-      acc += (F[1] - F[0]) / (T)gg.dx[d];
-    }
+    };
+    const T acc = cond_rate<T, NDIM>(sT, sK, r, ro, gg, gmax, L.mode, bmean, face);
     ub[(size_t)EN * S + c] = ub[(size_t)EN * S + c] + h * acc;
   }
+}
+
+// Grid-wide barrier number k of a cooperative launch (the barrier words zeroed before it):
+// thread 0 of each CTA arrives on bar[0]; the last arrival resets it and opens the barrier by
+// storing k + 1 in bar[1]; the others wait for that value, giving up after ~2^31 clock cycles
+// (about a second).  Returns false when this CTA gave up (give_up: the test hook, at once).
+__device__ __forceinline__ bool grid_barrier_bounded(unsigned* bar, unsigned nblocks, unsigned k, int give_up) {
+  __shared__ int ok_s;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    if (give_up) {
+      ok = 0;
+    } else {
+      const unsigned arrived = atomicAdd(&bar[0], 1u) + 1u;
+      if (arrived == nblocks) {
+        atomicExch(&bar[0], 0u);
+        __threadfence();
+        asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(bar + 1), "r"(k + 1u) : "memory");
+      } else {
+        const long long t0 = clock64();
+        for (;;) {
+          unsigned g;
+          asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(g) : "l"(bar + 1) : "memory");
+          if (g == k + 1u) break;
+          if (clock64() - t0 > (1ll << 31)) { ok = 0; break; }
+        }
+      }
+    }
+    ok_s = ok;
+  }
+  __syncthreads();
+  __threadfence();                                  // loads after the barrier see the others' stores
+  return ok_s != 0;
+}
+
+// The substep loop of cond_loop (CondLoopLaunch), one leaf per CTA of a cooperative launch.
+// The leaf's ring region (interior and one ghost layer) of every variable but psi stays in
+// shared memory over the loop.  Per substep: T and kappa on the ring, the interior energy
+// update (cond_rate, as conduction_kernel), the new interior energy into e_pp[it & 1], the
+// grid barrier, then the ring's ghost energy from the leaves it copies (all regions are
+// copies here, whose first ghost layer reads interior cells).  Leaves of problems with fewer
+// substeps take part in the barriers only.  After the loop the interior energy goes back to u;
+// its ghosts are stale, as after the per-substep path.
+template <typename T, int NDIM, int NB>
+__global__ void __launch_bounds__(256) cond_loop_kernel(CondLoopLaunch L) {
+  using G = Geo<NDIM, NB>;
+  constexpr int NP = G::NP, S = G::S;
+  constexpr int R = NB + 2;
+  constexpr int NR = NDIM == 3 ? R * R * R : R * R;
+  constexpr int NI = NDIM == 3 ? NB * NB * NB : NB * NB;
+  constexpr int NW = NV - 1;                        // rho, m, B, e (psi enters no T)
+  extern __shared__ __align__(16) unsigned char csm[];
+  T* sW = reinterpret_cast<T*>(csm);                // [NW][NR]
+  T* sT = sW + (size_t)NW * NR;
+  T* sK = sT + NR;
+  __shared__ GhostRegion reg[27];
+  const int blk = L.blocks[blockIdx.x];
+  const BlockGeo gg = L.geo[blk];
+  for (int q = threadIdx.x; q < 27; q += blockDim.x) reg[q] = L.regions[(size_t)blk * 27 + q];
+  const int ns = L.nsub[gg.problem];
+  const T h = (T)L.hsub[gg.problem];
+  T* ub = (T*)L.u + (size_t)blk * NV * S;
+  Phys<T> P;
+  P.gamma = (T)L.gamma;
+  P.gm1 = (T)(L.gamma - 1.0);
+  P.ch = T(0);
+  P.tau = (T)L.tau;
+  const T k0 = (T)L.kappa0, gmax = (T)L.grad_t_max;
+  auto padded = [&](int r) {                        // ring cell -> padded cell
+    const int ri = r % R, rj = (r / R) % R, rk = NDIM == 3 ? r / (R * R) : 0;
+    return ((NDIM == 3 ? rk + 1 : 0) * NP + rj + 1) * NP + ri + 1;
+  };
+  for (int r = threadIdx.x; r < NR; r += blockDim.x) {
+    const int c = padded(r);
+#pragma unroll
+    for (int v = 0; v < NW; ++v) sW[(size_t)v * NR + r] = ub[(size_t)v * S + c];
+  }
+  const int ro[3] = {1, R, R * R};
+  unsigned fail = 0;
+  for (int it = 0; it < L.nmax; ++it) {
+    __syncthreads();
+    const bool active = it < ns;
+    if (active) {
+      for (int r = threadIdx.x; r < NR; r += blockDim.x) {
+        T w[NV];
+#pragma unroll
+        for (int v = 0; v < NW; ++v) w[v] = sW[(size_t)v * NR + r];
+        w[PSI] = T(0);
+        cond_tk<T>(w, P, k0, sT[r], sK[r]);
+      }
+      __syncthreads();
+      T* eb = (T*)L.e_pp[it & 1] + (size_t)blk * NV * S + (size_t)EN * S;
+      for (int q = threadIdx.x; q < NI; q += blockDim.x) {
+        const int i = q % NB, j = (q / NB) % NB, k = NDIM == 3 ? q / (NB * NB) : 0;
+        const int r = ((NDIM == 3 ? k + 1 : 0) * R + j + 1) * R + i + 1;
+        auto bmean = [&](int j2, int d, int side) -> T {
+          const int rl = side ? r : r - ro[d], rr = rl + ro[d];
+          return T(0.5) * (sW[(size_t)(BX + j2) * NR + rl] + sW[(size_t)(BX + j2) * NR + rr]);
+        };
+        auto face = [](int, const T*) {};
+        const T acc = cond_rate<T, NDIM>(sT, sK, r, ro, gg, gmax, L.mode, bmean, face);
+        // only this thread reads or writes cell r's energy in this phase (the rates read T,
+        // kappa and B)
+        const T en = sW[(size_t)EN * NR + r] + h * acc;
+        sW[(size_t)EN * NR + r] = en;
+        eb[padded(r)] = en;
+      }
+    }
+    if (!grid_barrier_bounded(L.bar, (unsigned)L.nblocks, (unsigned)it, L.fail_waits)) {
+      fail = 4u;
+      break;
+    }
+    if (active && it + 1 < ns) {
+      // the ring's ghost energy: region (rx, ry, rz) maps padded index i to m i + a of its
+      // source leaf, an interior cell of that leaf for the first ghost layer
+      const T* ebase = (const T*)L.e_pp[it & 1];
+      for (int r = threadIdx.x; r < NR; r += blockDim.x) {
+        const int ri = r % R, rj = (r / R) % R, rk = NDIM == 3 ? r / (R * R) : 1;
+        const int rx = ri == 0 ? 0 : (ri == R - 1 ? 2 : 1), ry = rj == 0 ? 0 : (rj == R - 1 ? 2 : 1);
+        const int rz = NDIM == 3 ? (rk == 0 ? 0 : (rk == R - 1 ? 2 : 1)) : 1;
+        if (rx == 1 && ry == 1 && rz == 1) continue;
+        const GhostRegion& g = reg[rx + 3 * ry + 9 * rz];
+        const int si = g.m[0] * (ri + 1) + g.a[0], sj = g.m[1] * (rj + 1) + g.a[1];
+        const int sk = NDIM == 3 ? g.m[2] * (rk + 1) + g.a[2] : 0;
+        const size_t sc = (size_t)g.src * NV * S + (size_t)EN * S + ((size_t)sk * NP + sj) * NP + si;
+        sW[(size_t)EN * NR + r] = __ldcg(ebase + sc);
+      }
+    }
+  }
+  __syncthreads();
+  if (fail) {
+    if (threadIdx.x == 0) atomicOr(L.err_word, fail);
+    return;
+  }
+  if (ns > 0)
+    for (int q = threadIdx.x; q < NI; q += blockDim.x) {
+      const int i = q % NB, j = (q / NB) % NB, k = NDIM == 3 ? q / (NB * NB) : 0;
+      const int r = ((NDIM == 3 ? k + 1 : 0) * R + j + 1) * R + i + 1;
+      ub[(size_t)EN * S + padded(r)] = sW[(size_t)EN * NR + r];
+    }
 }
 
 }  // namespace mapgb

@@ -89,7 +89,14 @@ struct map_pool {
   // block) and warp-schedule weights (0 = defaults)
   int tune_grid = 0, tune_wp = 0, tune_wf = 0;
   int nsm = 0;                 // SM count of the pool's device
-  int fail_waits = 0;        // test hook: the step kernel's plane waits give up at once
+  int fail_waits = 0;        // test hook: 1 every bounded wait gives up at once, 2 only the conduction loop's
+  // conduction substep loop in one cooperative launch (map_set_conduction_loop): the switch,
+  // the grid barrier words, the CTAs that can be resident at once (-1: not asked yet) and
+  // whether every ghost region of the tree is a copy (-1: not checked for this tree)
+  int cond_loop = 1;
+  unsigned* gbar = nullptr;
+  int cond_cap = -1;
+  int cond_copies = -1;
   long long launches = 0;
   std::string err;
   // graph cache, one per starting buffer parity q and fill kind (2q + 1: residual fill)
@@ -235,7 +242,8 @@ int map_create_pool(const map_pool_desc* d, void* stream, map_pool** out) {
       cudaMalloc(&pool->err_word, sizeof(unsigned)) != cudaSuccess ||
       cudaMalloc(&pool->sums, sizeof(double) * kNV * pool->nprob) != cudaSuccess ||
       cudaMalloc(&pool->hsub, sizeof(double) * pool->nprob) != cudaSuccess ||
-      cudaMalloc(&pool->nsub, sizeof(int) * pool->nprob) != cudaSuccess)
+      cudaMalloc(&pool->nsub, sizeof(int) * pool->nprob) != cudaSuccess ||
+      cudaMalloc(&pool->gbar, 2 * sizeof(unsigned)) != cudaSuccess)
     return cleanup(MAP_ENOMEM, "cudaMalloc of the step constants failed");
   cudaMemsetAsync(pool->dyn, 0, sizeof(ProbDyn) * pool->nprob, pool->stream);
   cudaMemsetAsync(pool->err_word, 0, sizeof(unsigned), pool->stream);
@@ -254,6 +262,7 @@ int map_destroy_pool(map_pool* pool) {
   cudaFree(pool->dyn);
   cudaFree(pool->hsub);
   cudaFree(pool->nsub);
+  cudaFree(pool->gbar);
   cudaFree(pool->err_word);
   cudaFree(pool->sums);
   cudaFree(pool->staging);
@@ -300,6 +309,7 @@ int map_set_stream(map_pool* pool, void* stream) {
 static int install_tree(map_pool* pool, HostTree& t) {
   free_tree(pool);
   drop_graphs(pool);
+  pool->cond_copies = -1;
   DevTree& D = pool->dt;
   CK(upload(&D.geo, t.geo, pool->stream));
   CK(upload(&D.regions, t.regions, pool->stream));
@@ -777,7 +787,7 @@ static int step_launches(map_pool* pool, const map_params* p, bool fused) {
   S.riemann = p->riemann;
   S.w_pred = pool->tune_wp;
   S.w_face = pool->tune_wf;
-  S.fail_waits = pool->fail_waits;
+  S.fail_waits = pool->fail_waits == 1;
   S.err_word = pool->err_word;
   S.sums = fused ? pool->sums : nullptr;
   S.dyn_next = fused ? pool->dyn : nullptr;
@@ -856,6 +866,33 @@ static int step_launches(map_pool* pool, const map_params* p, bool fused) {
 // energy in place and refluxes it at coarse/fine faces.  Reads dt back to size the loop.
 static int conduction_substep(map_pool* pool, const map_params* p, int it, bool rf);
 
+// Whether this step's conduction substeps can run as one cooperative launch: switched on, a
+// single-level tree of the whole pool whose ghost regions are all copies (their first ghost
+// layer then reads interior cells of the source leaf), no energy reflux, leaf shapes the loop
+// kernel holds on chip, every leaf's CTA resident at once, and no stream capture under way.
+static bool cond_loop_usable(map_pool* pool, bool rf) {
+  if (!pool->cond_loop || rf || pool->partial || pool->tree.maxlev != 0) return false;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(pool->stream, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+    cudaGetLastError();
+    return false;
+  }
+  if (pool->cond_cap < 0)
+    pool->cond_cap = is64(pool) ? cond_loop_capacity_f64(kcfg(pool), pool->nsm) : cond_loop_capacity_f32(kcfg(pool), pool->nsm);
+  if (pool->tree.nleaves > pool->cond_cap) return false;
+  if (pool->cond_copies < 0) {
+    int ok = 1;
+    const HostTree& t = pool->tree;
+    for (int l = 0; l < t.nleaves && ok; ++l) {
+      const int id = t.leaf_to_block[l];
+      for (int r = 0; r < 27 && ok; ++r)
+        if (t.regions[(size_t)id * 27 + r].kind != 0) ok = 0;
+    }
+    pool->cond_copies = ok;
+  }
+  return pool->cond_copies == 1;
+}
+
 static int conduction_launches(map_pool* pool, const map_params* p) {
   const int np = pool->nprob;
   std::vector<ProbDyn> dyn(np);
@@ -875,6 +912,39 @@ static int conduction_launches(map_pool* pool, const map_params* p) {
   CK(cudaMemcpyAsync(pool->hsub, pool->hsub_h.data(), sizeof(double) * np, cudaMemcpyHostToDevice, pool->stream));
   CK(cudaMemcpyAsync(pool->nsub, pool->nsub_h.data(), sizeof(int) * np, cudaMemcpyHostToDevice, pool->stream));
   const bool rf = p->reflux != 0 && pool->dt.nrtasks > 0;
+  if (cond_loop_usable(pool, rf)) {
+    // the whole loop in one cooperative launch: a full fill first (as the first substep of
+    // the per-substep path does), then every substep on the ring regions kept on chip
+    int rc = fill_on(pool, pool->cur);
+    if (rc) return rc;
+    CK(cudaMemsetAsync(pool->gbar, 0, 2 * sizeof(unsigned), pool->stream));
+    CondLoopLaunch C;
+    C.u = pool->buf[pool->cur];
+    C.e_pp[0] = pool->buf[1 - pool->cur];
+    C.e_pp[1] = pool->buf[2];
+    C.blocks = pool->dt.all_leaves;
+    C.nblocks = pool->tree.nleaves;
+    C.geo = pool->dt.geo;
+    C.regions = pool->dt.regions;
+    C.gamma = p->gamma;
+    C.tau = fix_tau(pool, p);
+    C.kappa0 = p->kappa0;
+    C.grad_t_max = p->grad_t_max;
+    C.mode = p->conduction;
+    C.hsub = pool->hsub;
+    C.nsub = pool->nsub;
+    C.nmax = nmax;
+    C.bar = pool->gbar;
+    C.err_word = pool->err_word;
+    C.fail_waits = pool->fail_waits != 0;
+    if (DISPATCH(pool, cond_loop, C) == cudaSuccess) {
+      pool->pushed[pool->cur] = false;     // the energy ghosts are stale now
+      return MAP_OK;
+    }
+    // the device refused the cooperative launch: the per-substep path from now on
+    cudaGetLastError();
+    pool->cond_cap = 0;
+  }
   // The substep loop is launch-bound on small meshes (a fill and a conduction launch per
   // substep): the second time a (substep count, buffer, fill kind) recurs it is captured into
   // a graph, and later steps replay it.  Substep sizes and counts are read from device memory
@@ -1220,8 +1290,14 @@ int map_conservation(map_pool* pool, double* sums_out) {
 
 int map_test_fail_waits(map_pool* pool, int on) {
   if (!pool) return MAP_EINVAL;
-  pool->fail_waits = on ? 1 : 0;
+  pool->fail_waits = on == 2 ? 2 : (on ? 1 : 0);
   drop_graphs(pool);
+  return MAP_OK;
+}
+
+int map_set_conduction_loop(map_pool* pool, int on) {
+  if (!pool) return MAP_EINVAL;
+  pool->cond_loop = on ? 1 : 0;
   return MAP_OK;
 }
 

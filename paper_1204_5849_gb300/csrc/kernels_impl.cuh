@@ -67,6 +67,15 @@ cudaError_t launch_step_geo(const StepLaunch& L, cudaStream_t s) {
   return launch_step_one<T, NDIM, NB, SCH_WENO, 0, 2, FLX, RFX>(L, s);
 }
 
+#define MAPGB_GEO_DISPATCH_INT(KC, CALL)                          \
+  do {                                                            \
+    if ((KC).ndim == 2 && (KC).nb == 16) { CALL(2, 16); }         \
+    if ((KC).ndim == 3 && (KC).nb == 16) { CALL(3, 16); }         \
+    if ((KC).ndim == 3 && (KC).nb == 8) { CALL(3, 8); }           \
+    if ((KC).ndim == 2 && (KC).nb == 8) { CALL(2, 8); }           \
+    return 0;                                                     \
+  } while (0)
+
 #define MAPGB_GEO_DISPATCH(KC, CALL)                              \
   do {                                                            \
     if ((KC).ndim == 2 && (KC).nb == 16) { CALL(2, 16); }         \
@@ -215,6 +224,66 @@ cudaError_t launch_conduction_T(const KernelConfig& kc, const CondLaunch& L, cud
 #undef CALL_COND
 }
 
+// the conduction loop (cond_loop_kernel): the ring region of every variable but psi, T and
+// kappa in shared memory; 3D 16^3 leaves would need 233 KB and are left to the per-substep
+// kernels
+template <typename T, int NDIM, int NB>
+constexpr size_t cond_loop_smem() {
+  constexpr int R = NB + 2;
+  return (size_t)(NV + 1) * (NDIM == 3 ? R * R * R : R * R) * sizeof(T);
+}
+
+template <typename T, int NDIM, int NB>
+int cond_loop_capacity_one(int nsm) {
+  if constexpr (NDIM == 3 && NB == 16) {
+    (void)nsm;
+    return 0;
+  } else {
+    constexpr size_t smem = cond_loop_smem<T, NDIM, NB>();
+    auto kern = cond_loop_kernel<T, NDIM, NB>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+      cudaGetLastError();
+      return 0;
+    }
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, smem) != cudaSuccess) {
+      cudaGetLastError();
+      return 0;
+    }
+    return per_sm * nsm;
+  }
+}
+
+template <typename T, int NDIM, int NB>
+cudaError_t launch_cond_loop_one(const CondLoopLaunch& L, cudaStream_t s) {
+  if constexpr (NDIM == 3 && NB == 16) {
+    (void)L;
+    (void)s;
+    return cudaErrorInvalidValue;
+  } else {
+    CondLoopLaunch A = L;
+    void* args[] = {&A};
+    return cudaLaunchCooperativeKernel((const void*)cond_loop_kernel<T, NDIM, NB>, dim3(L.nblocks), dim3(256), args,
+                                       cond_loop_smem<T, NDIM, NB>(), s);
+  }
+}
+
+template <typename T>
+int cond_loop_capacity_T(const KernelConfig& kc, int nsm) {
+#define CALL_CAP(ND, NBV) return cond_loop_capacity_one<T, ND, NBV>(nsm)
+  MAPGB_GEO_DISPATCH_INT(kc, CALL_CAP);
+#undef CALL_CAP
+}
+
+template <typename T>
+cudaError_t launch_cond_loop_T(const KernelConfig& kc, const CondLoopLaunch& L, cudaStream_t s, long long* cnt) {
+  if (L.nblocks <= 0) return cudaSuccess;
+  if (cnt) ++*cnt;
+#define CALL_LOOP(ND, NBV) return launch_cond_loop_one<T, ND, NBV>(L, s)
+  MAPGB_GEO_DISPATCH(kc, CALL_LOOP);
+#undef CALL_LOOP
+}
+
 template <typename T>
 cudaError_t launch_cfl_partial_T(const KernelConfig& kc, const void* u, int nblocks, double gamma, double* partial,
                                  cudaStream_t s) {
@@ -244,6 +313,8 @@ cudaError_t launch_cfl_partial_T(const KernelConfig& kc, const void* u, int nblo
   cudaError_t launch_regrid_##SUFFIX(const KernelConfig& k, const RegridLaunch& l, cudaStream_t s, long long* c) { return launch_regrid_T<T>(k, l, s, c); } \
   cudaError_t launch_reflux_##SUFFIX(const KernelConfig& k, const RefluxLaunch& l, cudaStream_t s, long long* c) { return launch_reflux_T<T>(k, l, s, c); } \
   cudaError_t launch_conduction_##SUFFIX(const KernelConfig& k, const CondLaunch& l, cudaStream_t s, long long* c) { return launch_conduction_T<T>(k, l, s, c); } \
+  int cond_loop_capacity_##SUFFIX(const KernelConfig& k, int nsm) { return cond_loop_capacity_T<T>(k, nsm); } \
+  cudaError_t launch_cond_loop_##SUFFIX(const KernelConfig& k, const CondLoopLaunch& l, cudaStream_t s, long long* c) { return launch_cond_loop_T<T>(k, l, s, c); } \
   size_t step_smem_##SUFFIX(const KernelConfig& k, int scheme, int res) { return step_smem_T<T>(k, scheme, res); } \
   cudaError_t launch_cfl_partial_##SUFFIX(const KernelConfig& k, const void* u, int n, double g, double* part, cudaStream_t s) { return launch_cfl_partial_T<T>(k, u, n, g, part, s); } \
   }

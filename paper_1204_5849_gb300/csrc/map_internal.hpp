@@ -220,6 +220,27 @@ struct CondLaunch {
   const RefluxLeaf* refl;
 };
 
+// The whole conduction substep loop of one step in one cooperative launch (single-level
+// meshes whose ghost regions are all copies): each CTA keeps its leaf's ring region in
+// shared memory and exchanges the energy of its interior through e_pp[it & 1] (the energy
+// slices of two spare state buffers), one bounded grid barrier per substep.
+struct CondLoopLaunch {
+  void* u;                 // the state: the ring region is read, the interior energy written
+  void* e_pp[2];           // two state buffers whose energy slices carry the exchange
+  const int* blocks;       // leaves, one CTA each
+  int nblocks;
+  const BlockGeo* geo;
+  const GhostRegion* regions;
+  double gamma, tau, kappa0, grad_t_max;
+  int mode;                // 1 isotropic, 2 along B
+  const double* hsub;
+  const int* nsub;
+  int nmax;                // substeps of the problem with the most
+  unsigned* bar;           // grid barrier words (zeroed before the launch)
+  unsigned* err_word;
+  int fail_waits;          // test hook: the barrier gives up at once
+};
+
 struct FillLaunch {
   void* u;
   const int* blocks;
@@ -308,6 +329,8 @@ struct KernelConfig {
   cudaError_t launch_regrid_##SUFFIX(const KernelConfig&, const RegridLaunch&, cudaStream_t, long long*); \
   cudaError_t launch_reflux_##SUFFIX(const KernelConfig&, const RefluxLaunch&, cudaStream_t, long long*); \
   cudaError_t launch_conduction_##SUFFIX(const KernelConfig&, const CondLaunch&, cudaStream_t, long long*); \
+  int cond_loop_capacity_##SUFFIX(const KernelConfig&, int nsm); \
+  cudaError_t launch_cond_loop_##SUFFIX(const KernelConfig&, const CondLoopLaunch&, cudaStream_t, long long*); \
   size_t step_smem_##SUFFIX(const KernelConfig&, int scheme, int resistive); \
   cudaError_t launch_cfl_partial_##SUFFIX(const KernelConfig&, const void* u, int nblocks, double gamma, \
                                           double* partial, cudaStream_t);

@@ -442,6 +442,82 @@ def test_fp32_conduction_l1(gpulib):
     assert rel_l1(pool.read_leaves(), orc.get_state()).max() <= 1e-5
 
 
+# the single-launch conduction loop (map_set_conduction_loop) against one fill and one kernel
+# per substep: single-level meshes whose ghost regions are all copies
+_LOOP_MESHES = {
+    "2d16_periodic": lambda: w.uniform_mesh(2, 16, (3, 2)),
+    "2d16_outflow": lambda: w.uniform_mesh(2, 16, (2, 3), bc=w.mesh.OUTFLOW),
+    "2d8_periodic": lambda: w.uniform_mesh(2, 8, (3, 3)),
+    "3d8_periodic": lambda: w.uniform_mesh(3, 8, (2, 2, 3)),
+    "3d8_outflow": lambda: w.uniform_mesh(3, 8, (2, 2, 2), bc=w.mesh.OUTFLOW),
+}
+
+
+@pytest.mark.parametrize("geom", sorted(_LOOP_MESHES))
+@pytest.mark.parametrize("mode", ["isotropic", "aligned"])
+@pytest.mark.parametrize("prec", [0, 1])
+def test_conduction_loop_equals_per_substep_path(gpulib, geom, mode, prec):
+    """Three steps with several substeps each (the subcycle), both paths: bitwise the same
+    state, and the loop launches fewer kernels."""
+    mesh = _LOOP_MESHES[geom]()
+    U0 = _hot_state(mesh)
+    p = P(scheme="lf", conduction=mode, kappa0=5e-3, subcycle=1, grad_t_max=0.0 if mode == "isotropic" else 0.5)
+    out, launches = {}, {}
+    for loop in (True, False):
+        pool = pool_for(mesh, prec, U0)
+        pool.set_conduction_loop(loop)
+        k0 = pool.kernel_launches()
+        for _ in range(3):
+            pool.fill_ghosts(); pool.cfl_dt(p); pool.step(p)
+        launches[loop] = pool.kernel_launches() - k0
+        out[loop] = pool.read_leaves()
+        assert pool.check() == 0
+        _, nsub = pool.last_conduction()
+        assert int(nsub.max()) > 1                   # several substeps per step
+        pool.close()
+    np.testing.assert_array_equal(out[True], out[False])
+    assert launches[True] < launches[False], launches
+
+
+def test_conduction_loop_keeps_amr_meshes_on_the_per_substep_path(gpulib):
+    """A mesh with coarse/fine faces (prolonged ghosts) is not eligible: the launch counts of
+    both settings agree."""
+    mesh = _COND_MESHES["2d_amr"]()
+    U0 = _hot_state(mesh)
+    p = P(scheme="lf", conduction="isotropic", kappa0=5e-3)
+    counts = []
+    for loop in (True, False):
+        pool = pool_for(mesh, 0, U0)
+        pool.set_conduction_loop(loop)
+        k0 = pool.kernel_launches()
+        pool.fill_ghosts(); pool.cfl_dt(p); pool.step(p)
+        counts.append(pool.kernel_launches() - k0)
+        pool.close()
+    assert counts[0] == counts[1], counts
+
+
+def test_conduction_loop_barrier_timeout_is_reported(gpulib):
+    """The loop's grid barrier giving up (test hook, as one that waited about a second would)
+    sets the timeout bit: map_check reports MAP_ETIMEOUT; with normal waits and the state
+    written again the pool steps as one that never failed."""
+    from paper_1204_5849_gb300 import MAP_FP32_FIX64
+    from paper_1204_5849_gb300.binding import STATUS
+    mesh = _LOOP_MESHES["2d16_periodic"]()
+    U0 = _hot_state(mesh)
+    p = P(scheme="lf", conduction="aligned", kappa0=5e-3)
+    pool = pool_for(mesh, MAP_FP32_FIX64, U0)
+    pool.test_fail_waits(2)
+    pool.fill_ghosts(); pool.cfl_dt(p); pool.step(p)
+    assert STATUS.get(pool.check()) == "MAP_ETIMEOUT"
+    pool.test_fail_waits(False)
+    pool.write_leaves(U0)
+    pool.advance(p, 2)
+    ref = pool_for(mesh, MAP_FP32_FIX64, U0)
+    ref.advance(p, 2)
+    np.testing.assert_array_equal(pool.read_leaves(), ref.read_leaves())
+    assert pool.check() == 0
+
+
 def test_conduction_needs_kappa0(gpulib):
     from paper_1204_5849_gb300 import MAP_FP64, MapError
     mesh = w.uniform_mesh(2, 16, (2, 2))
