@@ -743,11 +743,14 @@ __global__ void __launch_bounds__(256) conduction_kernel(CondLaunch L) {
 // thread 0 of each CTA arrives on bar[0]; the last arrival resets it and opens the barrier by
 // storing k + 1 in bar[1]; the others wait for that value, giving up after ~2^31 clock cycles
 // (about a second).  Returns false when this CTA gave up (give_up: the test hook, at once).
+// Ordering: the CTA barrier orders the CTA's stores before thread 0's device-scope fence and
+// release (cumulative), and thread 0's acquire before the CTA's later loads; only thread 0
+// fences.
 __device__ __forceinline__ bool grid_barrier_bounded(unsigned* bar, unsigned nblocks, unsigned k, int give_up) {
   __shared__ int ok_s;
-  __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) {
+    __threadfence();
     int ok = 1;
     if (give_up) {
       ok = 0;
@@ -767,10 +770,10 @@ __device__ __forceinline__ bool grid_barrier_bounded(unsigned* bar, unsigned nbl
         }
       }
     }
+    __threadfence();
     ok_s = ok;
   }
   __syncthreads();
-  __threadfence();                                  // loads after the barrier see the others' stores
   return ok_s != 0;
 }
 
