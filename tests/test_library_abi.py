@@ -39,3 +39,13 @@ def test_binding_fails_loudly_without_library(tmp_path):
         binding._lib = None
         binding.load(str(tmp_path / "missing.so"))
     binding._lib = None
+
+
+def test_pool_setters_reject_a_null_pool():
+    """The host-side setters check their pool before touching CUDA (no GPU needed)."""
+    import ctypes
+    from paper_1204_5849_gb300 import _build
+    lib = ctypes.CDLL(_build.build())
+    assert lib.map_set_conduction_loop(None, 1) == -1          # MAP_EINVAL
+    assert lib.map_test_fail_waits(None, 1) == -1
+    assert lib.map_set_launch(None, 0, 0, 0) == -1
