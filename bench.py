@@ -539,6 +539,11 @@ def main():
     b1 = torch.cuda.Event(enable_timing=True)
     nb_ = min(ne, 20)
     bout = outs[0].numpy()
+    for _ in range(2):                          # untimed: first use of the blocking path
+        pool.write_leaves_ptr(pinned.data_ptr())
+        pool.advance(params, 1)
+        pool.read_leaves(out=bout)
+        pool.speeds()
     t0 = time.perf_counter()
     b0.record(stream)
     for _ in range(nb_):
