@@ -249,7 +249,8 @@ typedef struct {
                          block count = one per block, else a persistent grid */
   int w_pred, w_face; /* warp-schedule cost of a predictor unit and of a face unit */
   double ms_default;  /* step launches with the default shape (grid 0, default
-                         weights: 3:1 for 3D LF, 3:2 for 3D MMC, 7:4 in 2D, 1:1 for WENO) */
+                         weights: 3:1 for 3D LF on 16^3, 4:1 on 8^3, 3:2 for 3D MMC, 7:4 in
+                         2D, 1:1 for WENO) */
   double ms_best;     /* with the chosen shape */
   int trials;
 } map_tune_result;

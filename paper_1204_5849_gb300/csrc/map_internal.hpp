@@ -144,11 +144,11 @@ std::string build_regrid(const HostTree& old_t, const HostTree& new_t,
 
 // Default warp-schedule weights (predictor unit : face unit) of the step kernel's per-plane
 // work list, from step times measured on GB300 over the weight ratio (map_autotune searches
-// around them): 3:1 for 3D LF (16^3 and the resistive 8^3), 3:2 for 3D MMC, 7:4 for 2D LF and
-// MMC (the predictor and the faces run in separate barrier intervals there), 1:1 for WENO,
-// whose only predictor work is the resistive current.
+// around them): 3:1 for 3D LF on 16^3 blocks, 4:1 on 8^3 (the resistive Harris-sheet octree:
+// 2.5 % on its step launches), 3:2 for 3D MMC, 7:4 for 2D LF and MMC (the predictor and the
+// faces run in separate barrier intervals there), 1:1 for WENO, whose only predictor work is
+// the resistive current.
 inline void default_schedule_weights(int ndim, int nb, int scheme, int* w_pred, int* w_face) {
-  (void)nb;
   *w_pred = 1;
   *w_face = 1;
   if (scheme == MAP_WENO) return;
@@ -156,7 +156,7 @@ inline void default_schedule_weights(int ndim, int nb, int scheme, int* w_pred, 
     *w_pred = 7;
     *w_face = 4;
   } else if (scheme == MAP_LF) {
-    *w_pred = 3;
+    *w_pred = nb == 8 ? 4 : 3;
     *w_face = 1;
   } else {
     *w_pred = 3;
