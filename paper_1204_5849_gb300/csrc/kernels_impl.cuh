@@ -246,7 +246,7 @@ int cond_loop_capacity_one(int nsm) {
       return 0;
     }
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, smem) != cudaSuccess) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 512, smem) != cudaSuccess) {
       cudaGetLastError();
       return 0;
     }
@@ -263,7 +263,7 @@ cudaError_t launch_cond_loop_one(const CondLoopLaunch& L, cudaStream_t s) {
   } else {
     CondLoopLaunch A = L;
     void* args[] = {&A};
-    return cudaLaunchCooperativeKernel((const void*)cond_loop_kernel<T, NDIM, NB>, dim3(L.nblocks), dim3(256), args,
+    return cudaLaunchCooperativeKernel((const void*)cond_loop_kernel<T, NDIM, NB>, dim3(L.nblocks), dim3(512), args,
                                        cond_loop_smem<T, NDIM, NB>(), s);
   }
 }
