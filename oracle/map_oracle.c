@@ -14,10 +14,13 @@
  *   Sec. 4.5 regrid error estimator.
  * Readings where the paper is silent or garbled are stated at the place they are used.
  *
- * Parity unpinned: the MMC multi-D face speeds (one u-speed and one u~-speed per face,
- * used for every split term of that face's flux) and long-time AMR runs.  The rest of MMC
- * is pinned where the speed is constant (every reading then coincides): unlimited, it is
- * Lax-Wendroff on the linear GLM pair.
+ * Parity unpinned: which local range the MMC multi-D face speeds come from (here one u-speed
+ * and one u~-speed per face, from its two cells, used for every split term of that face's
+ * flux), and long-time AMR runs.  That the speeds are local is pinned: one step changes
+ * nothing beyond two cells of a perturbed one (a global speed moves every cell), and the
+ * mirror and transpose symmetries exclude one-sided speeds.  The rest of MMC is pinned where
+ * the speed is constant (every reading then coincides): unlimited, it is Lax-Wendroff on the
+ * linear GLM pair.
  */
 #include "map_oracle.h"
 

@@ -11,8 +11,9 @@
  * layers).  Leaf interiors cross this API as [9][nz][nb][nb] with nz = nb (3D) or 1 (2D).
  *
  * Parity unpinned (no value printed by the paper or fixed by a closed form or invariant
- * reaches them on their own): the MMC multi-dimensional face-speed reading and the
- * long-time AMR results; these are checked only through invariants.
+ * reaches them on their own): which local range the MMC multi-dimensional face speeds are
+ * taken from (their locality and symmetry are pinned) and the long-time AMR results; these
+ * are checked only through invariants.
  */
 #ifndef MAP_ORACLE_H
 #define MAP_ORACLE_H

@@ -703,3 +703,44 @@ def test_mmc_unlimited_is_lax_wendroff_on_the_glm_pair(sign, mode):
     want = np.real(G * A * np.exp(1j * (theta * j + phi0)))
     np.testing.assert_allclose(wnew, want, rtol=0, atol=1e-14)
     np.testing.assert_allclose(wother, 0.0, rtol=0, atol=1e-15)
+
+
+# --- domain of dependence: the face speeds are local ---------------------------------------
+
+@pytest.mark.parametrize("scheme,limiter", [("mmc", "minmod"), ("mmc", "vanleer"), ("lf", "vanleer"),
+                                            ("weno", "minmod")])
+@pytest.mark.parametrize("at", [(7, 9), (15, 16), (0, 31)])
+def test_one_step_domain_of_dependence(scheme, limiter, at):
+    """One step with dt, c_h and c_p fixed: raising the pressure of one cell, so that its
+    signal speed becomes the largest in the domain, changes the new state only within two
+    cells of it (Chebyshev distance, across block edges and the periodic wrap) and leaves every
+    other cell bitwise as it was.  Two ghost layers bound every stencil of the schemes (Sec.
+    3.1-3.3, 3.7), and the MMC speeds taken from the relevant range of u and u~ (Sec. 3.1) are
+    pinned to a local range: a global speed, or one gathered farther out, would move cells
+    beyond it.  For WENO-RK2 the bound is twice two cells (two stages)."""
+    m = w.uniform_mesh(2, 16, (2, 2))                     # 32 x 32, periodic
+    U0 = w.evaluate_on_mesh(m, orszag_tang)
+    p = P(scheme=scheme, limiter=limiter, dt_override=2e-3, ch_mode="fixed", ch=1.5, cp_mode="fixed", cp=0.5)
+
+    def one_step(U):
+        o = Oracle(m, U)
+        o.fill_ghosts()
+        o.cfl(p)
+        assert o.step(p) == 0
+        return to_global(m, o.get_state())
+
+    U1 = U0.copy()
+    gi, gj = at
+    bl = [k for k in range(m.nleaves) if tuple(m.leaves[k][2:4]) == (gi // 16, gj // 16)][0]
+    U1[bl, 7, 0, gj % 16, gi % 16] += 4.0                 # e: p about 27x, the largest speed
+    A, B = one_step(U0), one_step(U1)
+    moved = np.abs(A - B).max(axis=0)[0]                  # [y][x]
+    n = 32
+    y, x = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+    dxp = np.minimum(np.abs(x - gi), n - np.abs(x - gi))
+    dyp = np.minimum(np.abs(y - gj), n - np.abs(y - gj))
+    reach = 4 if scheme == "weno" else 2
+    far = np.maximum(dxp, dyp) > reach
+    assert np.all(moved[far] == 0.0), np.argwhere(far & (moved != 0.0))[:5]
+    assert moved[gj, gi] > 0.0
+    assert np.count_nonzero(moved[~far]) > 5
