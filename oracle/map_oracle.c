@@ -14,13 +14,17 @@
  *   Sec. 4.5 regrid error estimator.
  * Readings where the paper is silent or garbled are stated at the place they are used.
  *
- * Parity unpinned: which local range the MMC multi-D face speeds come from (here one u-speed
- * and one u~-speed per face, from its two cells, used for every split term of that face's
- * flux), and long-time AMR runs.  That the speeds are local is pinned: one step changes
- * nothing beyond two cells of a perturbed one (a global speed moves every cell), and the
- * mirror and transpose symmetries exclude one-sided speeds.  The rest of MMC is pinned where
- * the speed is constant (every reading then coincides): unlimited, it is Lax-Wendroff on the
- * linear GLM pair.
+ * MMC's face speeds (Sec. 3.1, "the relevant range of u and u~"; here one u-speed and one
+ * u~-speed per face, from its two cells, used for every split term of that face's flux) are
+ * pinned where the mathematics fixes them, on states whose speed varies along every axis:
+ * with phi = 0 the scheme is Rusanov's with the speed of the face's two cells, and with
+ * phi = 1 its flux is a closed four-flux form whose alpha~ comes from u~_i, u~_{i+1}.  With a
+ * constant speed it is Sweby's flux-limited Lax-Wendroff (minmod, van Leer, the literal
+ * phi(r)).  Locality is pinned too: one step changes nothing beyond two cells of a perturbed
+ * cell, and the mirror and transpose symmetries exclude one-sided speeds.
+ * Parity unpinned: which speeds the two neighbouring g terms inside the limiter's ratio use
+ * when the speed varies (here the face's own; a reading the paper leaves open), and
+ * long-time AMR runs.
  */
 #include "map_oracle.h"
 
@@ -269,12 +273,14 @@ static double minmod(double a, double b) {
 /* Limiter as a function of two differences.
  * kind 0 minmod, 1 van Leer (harmonic mean when a, b agree in sign, else 0), 2 the
  * literal form of Sec. 3.1, phi(r) b with phi(r) = r for |r| <= 1 and 1 otherwise, 3 no
- * limiting, phi = 1 (returns b; a test option that turns MMC into its unlimited form).
+ * limiting, phi = 1 (returns b; a test option that turns MMC into its unlimited form), 4
+ * phi = 0 (returns 0; a test option that leaves MMC with its first-order part h alone).
  * For MMC, phi(r) g with r = a/b equals this function of (a, b) (division free); a zero
- * denominator gives 0.  Kinds 2 and 3 are MMC options only. */
+ * denominator gives 0.  Kinds 2, 3 and 4 are MMC options only. */
 double orc_limiter(int kind, double a, double b) {
   if (kind == 0) return minmod(a, b);
   if (kind == 3) return b;
+  if (kind == 4) return 0.0;
   if (kind == 1) {
     FLOPS(1);
     if (!(a * b > 0.0)) return 0.0;

@@ -11,9 +11,11 @@
  * layers).  Leaf interiors cross this API as [9][nz][nb][nb] with nz = nb (3D) or 1 (2D).
  *
  * Parity unpinned (no value printed by the paper or fixed by a closed form or invariant
- * reaches them on their own): which local range the MMC multi-dimensional face speeds are
- * taken from (their locality and symmetry are pinned) and the long-time AMR results; these
- * are checked only through invariants.
+ * reaches them on their own): which speeds the two neighbouring g terms inside MMC's limiter
+ * ratio use where the speed varies (the face speeds of h and of the face's own g terms are
+ * pinned by closed forms, the ratio's structure by Sweby's form at constant speed, and the
+ * speeds' locality and symmetry by invariants) and the long-time AMR results; these are
+ * checked only through invariants.
  */
 #ifndef MAP_ORACLE_H
 #define MAP_ORACLE_H
@@ -31,7 +33,7 @@ typedef struct {
   double eta;       /* uniform resistivity */
   int eglm;         /* 1: EGLM non-conservative sources on; 0: GLM */
   int scheme;       /* 0 MMC, 1 LF, 2 WENO */
-  int limiter;      /* 0 minmod, 1 van Leer, 2 literal Roe form, 3 none (2, 3: MMC only) */
+  int limiter;      /* 0 minmod, 1 van Leer, 2 literal Roe form, 3 phi = 1, 4 phi = 0 (2-4: MMC only) */
   double dt_override; /* > 0: use this dt */
   int reflux;       /* 1: coarse fluxes at coarse/fine faces replaced by the fine ones */
   int riemann;      /* interface flux of LF and WENO: 0 f_m (Lax-Friedrichs), 1 HLLC */

@@ -16,7 +16,7 @@ from . import build as _build
 SCHEMES = {"mmc": 0, "lf": 1, "weno": 2}
 RIEMANN = {"lf": 0, "hllc": 1}
 CONDUCTION = {"off": 0, "isotropic": 1, "aligned": 2}
-LIMITERS = {"minmod": 0, "vanleer": 1, "roe": 2, "none": 3}
+LIMITERS = {"minmod": 0, "vanleer": 1, "roe": 2, "none": 3, "zero": 4}
 CH_MODES = {"auto": 0, "paper": 1, "fixed": 2}
 CP_MODES = {"cd": 0, "fixed": 1}
 REFINE_VARS = {"rho": 1, "p": 2, "j": 4}

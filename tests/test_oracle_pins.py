@@ -705,6 +705,220 @@ def test_mmc_unlimited_is_lax_wendroff_on_the_glm_pair(sign, mode):
     np.testing.assert_allclose(wother, 0.0, rtol=0, atol=1e-15)
 
 
+# --- MMC with a varying speed: phi = 0 is Rusanov, phi = 1 a closed four-flux form --------
+
+def _np_flux(d, U, gamma, ch):
+    """EGLM-MHD flux along d (eqs. MHD-1 to MHD-5 without their sources), written out here
+    from the equations on global arrays U[9, nz, ny, nx], independently of the oracle."""
+    rho, m, B, e, psi = U[0], U[1:4], U[4:7], U[7], U[8]
+    v = m / rho
+    b2 = (B * B).sum(axis=0)
+    p = (gamma - 1.0) * (e - 0.5 * (m * v).sum(axis=0) - 0.5 * b2)
+    pt = p + 0.5 * b2
+    F = np.empty_like(U)
+    F[0] = m[d]
+    for j in range(3):
+        F[1 + j] = m[j] * v[d] - B[j] * B[d] + (pt if j == d else 0.0)
+        F[4 + j] = psi if j == d else v[d] * B[j] - v[j] * B[d]
+    F[7] = (e + pt) * v[d] - B[d] * (B * v).sum(axis=0)
+    F[8] = ch * ch * B[d]
+    return F
+
+
+def _np_speed(d, U, gamma):
+    """|v_d| plus the fast magnetosonic speed along d (reading Q2), from its closed form."""
+    rho, m, B, e = U[0], U[1:4], U[4:7], U[7]
+    b2 = (B * B).sum(axis=0)
+    p = np.maximum((gamma - 1.0) * (e - 0.5 * (m * m).sum(axis=0) / rho - 0.5 * b2), 0.0)
+    a2, va2, vd2 = gamma * p / rho, b2 / rho, B[d] ** 2 / rho
+    s = a2 + va2
+    cf = np.sqrt(0.5 * (s + np.sqrt(np.maximum(s * s - 4.0 * a2 * vd2, 0.0))))
+    return np.abs(m[d] / rho) + cf
+
+
+def _nxt(A, d):
+    return np.roll(A, -1, axis=A.ndim - 1 - d)        # value at i+1 along d (periodic)
+
+
+def _prv(A, d):
+    return np.roll(A, 1, axis=A.ndim - 1 - d)
+
+
+def _per_component(d, a, ch):
+    """A face speed for every component: c_h for the (B_d, psi) pair (Q4), else a."""
+    A = np.broadcast_to(a, (9,) + a.shape).copy()
+    A[4 + d] = ch
+    A[8] = ch
+    return A
+
+
+def _varying_state(X, Y, Z, gamma=5.0 / 3.0, ndim=2, **_):
+    """A smooth periodic state in which every variable, and so the signal speed along every
+    axis, varies in every direction."""
+    t = 2.0 * math.pi
+    Z = Z * (1.0 if ndim == 3 else 0.0)
+    rho = 1.0 + 0.3 * np.sin(t * X) * np.cos(t * Y) + 0.15 * np.cos(t * (Z + X))
+    vx = 0.2 + 0.4 * np.sin(t * (Y + Z))
+    vy = -0.1 + 0.3 * np.sin(t * (X - Z) + 0.4)
+    vz = 0.25 * np.cos(t * (X + Y))
+    bx = 0.7 + 0.2 * np.cos(t * Y)
+    by = 0.4 * np.sin(t * (X + Z) + 1.0)
+    bz = 0.3 * np.cos(t * (X - Y))
+    p = 0.6 + 0.25 * np.cos(t * (X + 2.0 * Y + Z))
+    psi = 0.05 * np.sin(t * (X + Y + Z))
+    return conserved_from_primitive(rho, vx, vy, vz, bx, by, bz, p, gamma, psi)
+
+
+def _mmc_one_step(ndim, limiter, ch, dt):
+    nb = 16 if ndim == 2 else 8
+    m = w.uniform_mesh(ndim, nb, (2, 2, 2))
+    U0 = w.evaluate_on_mesh(m, _varying_state, ndim=ndim)
+    o = Oracle(m, U0)
+    p = P(scheme="mmc", limiter=limiter, eglm=0, ch_mode="fixed", ch=ch, cp_mode="fixed", cp=0.0,
+          dt_override=dt)
+    o.fill_ghosts()
+    o.cfl(p)
+    assert o.step(p) == 0
+    return to_global(m, U0), to_global(m, o.get_state()), 1.0 / (2 * nb)
+
+
+def _update(U, F, lam):
+    return U - sum(lam * (F[d] - _prv(F[d], d)) for d in range(len(F)))
+
+
+@pytest.mark.parametrize("ndim", (2, 3))
+def test_mmc_first_order_part_is_rusanov(ndim):
+    """MMC's flux is h plus limited g terms (Sec. 3.1); with phi = 0 (an oracle test option)
+    only h = f+_i + f-_{i+1} remains, and with f+- = (f +- alpha u)/2 sharing the face's speed
+    that is, by hand, the Rusanov (local Lax-Friedrichs) flux
+    (f(u_i) + f(u_{i+1}))/2 - alpha (u_{i+1} - u_i)/2.  On a state whose speed varies along
+    every axis, the step equals that textbook scheme with alpha = max(alpha_d(u_i),
+    alpha_d(u_{i+1})) per face and axis (c_h for the (B_d, psi) pair): the speeds of h are the
+    face's two cells.  Per-cell speeds, or the maximum over the face's four-cell stencil,
+    move the result by orders of magnitude more than the tolerance (checked here)."""
+    gamma, ch = 5.0 / 3.0, 2.5
+    dt = 2e-3
+    U, got, dx = _mmc_one_step(ndim, "zero", ch, dt)
+    lam = dt / dx
+
+    def rusanov(speed):
+        F = []
+        for d in range(ndim):
+            Ur = _nxt(U, d)
+            A = _per_component(d, speed(d, U, Ur), ch)
+            F.append(0.5 * (_np_flux(d, U, gamma, ch) + _np_flux(d, Ur, gamma, ch)) - 0.5 * A * (Ur - U))
+        return _update(U, F, lam)
+
+    face = lambda d, Ul, Ur: np.maximum(_np_speed(d, Ul, gamma), _np_speed(d, Ur, gamma))
+    want = rusanov(face)
+    np.testing.assert_allclose(got, want, rtol=0, atol=1e-13)
+    # the readings this excludes
+    stencil = lambda d, Ul, Ur: np.maximum(face(d, _prv(Ul, d), Ul), face(d, Ur, _nxt(Ur, d)))
+    assert np.abs(rusanov(stencil) - got).max() > 1e-6
+    per_cell = [rusanov(lambda d, Ul, Ur: _np_speed(d, Ul, gamma)), rusanov(lambda d, Ul, Ur: _np_speed(d, Ur, gamma))]
+    assert min(np.abs(r - got).max() for r in per_cell) > 1e-6
+
+
+@pytest.mark.parametrize("ndim", (2, 3))
+def test_mmc_unlimited_flux_closed_form_with_varying_speed(ndim):
+    """With phi = 1 (Sec. 3.1, an oracle test option) the MMC face flux h + (g+ - g-)/2, with
+    g+_{i+1/2} = f~+_{i+1} - f+_i and g-_{i+1/2} = f-_{i+1} - f~-_i, collapses by hand to
+    (f_i + f_{i+1} + f~_i + f~_{i+1})/4 - alpha (u_{i+1} - u_i)/4 + alpha~ (u~_{i+1} - u~_i)/4,
+    u~ the Rusanov predictor of the whole (unsplit) step.  On a state whose speed varies
+    along every axis, the step equals that form with alpha from u_i, u_{i+1} and alpha~ from
+    u~_i, u~_{i+1} (reading Q3'): alpha~ taken from u, alpha~ = alpha, or a predictor over
+    half the step each miss it by far more than the tolerance (checked here)."""
+    gamma, ch = 5.0 / 3.0, 2.5
+    dt = 2e-3
+    U, got, dx = _mmc_one_step(ndim, "none", ch, dt)
+    lam = dt / dx
+
+    def face(d, Ul, Ur):
+        return np.maximum(_np_speed(d, Ul, gamma), _np_speed(d, Ur, gamma))
+
+    def step(pred_dt, tilde_speed_from_u=False, tilde_speed_is_alpha=False):
+        H = []
+        for d in range(ndim):
+            Ur = _nxt(U, d)
+            A = _per_component(d, face(d, U, Ur), ch)
+            H.append(0.5 * (_np_flux(d, U, gamma, ch) + _np_flux(d, Ur, gamma, ch)) - 0.5 * A * (Ur - U))
+        Ut = _update(U, H, pred_dt / dx)
+        F = []
+        for d in range(ndim):
+            Ur, Utr = _nxt(U, d), _nxt(Ut, d)
+            A = _per_component(d, face(d, U, Ur), ch)
+            if tilde_speed_is_alpha:
+                At = A
+            else:
+                At = _per_component(d, face(d, U, Ur) if tilde_speed_from_u else face(d, Ut, Utr), ch)
+            F.append(0.25 * (_np_flux(d, U, gamma, ch) + _np_flux(d, Ur, gamma, ch) + _np_flux(d, Ut, gamma, ch)
+                             + _np_flux(d, Utr, gamma, ch)) - 0.25 * A * (Ur - U) + 0.25 * At * (Utr - Ut))
+        return _update(U, F, lam)
+
+    want = step(dt)
+    np.testing.assert_allclose(got, want, rtol=0, atol=1e-13)
+    for wrong in (step(dt, tilde_speed_from_u=True), step(dt, tilde_speed_is_alpha=True), step(dt / 2)):
+        assert np.abs(wrong - got).max() > 1e-8
+
+
+def _sweby_phi(kind, th):
+    if kind == "minmod":
+        return np.maximum(0.0, np.minimum(1.0, th))
+    if kind == "vanleer":
+        return (th + np.abs(th)) / (1.0 + np.abs(th))
+    return np.where(np.abs(th) <= 1.0, th, 1.0)       # Sec. 3.1's phi(r)
+
+
+@pytest.mark.parametrize("limiter", ("minmod", "vanleer", "roe"))
+@pytest.mark.parametrize("sign", (1, -1))
+def test_mmc_limited_is_sweby_flux_limited_lax_wendroff_on_the_glm_pair(limiter, sign):
+    """With a constant speed MMC's limited flux is, by hand, Sweby's flux-limited
+    Lax-Wendroff flux (LeVeque, Finite Volume Methods, Sec. 6.12): on the (B_x, psi) pair,
+    linear with the fixed speed c_h (Q4), the characteristic variable w = psi + sign c_h B_x
+    is advected at sign c_h, h is the upwind flux, g = c_h (1 - nu)(w_{i+1} - w_i) on the
+    upwind side and zero on the other, and r is the ratio of the upwind neighbour's jump to
+    the face's, so fhat = c w_up + c (1 - nu) phi(theta)(w_{i+1} - w_i)/2.  A ratio taken
+    from the wrong neighbour, a g with the wrong sign, or phi(r) applied as phi(1/r) fails
+    it on this profile with extrema, jumps and a plateau."""
+    n, nb, ch = 64, 16, 2.0
+    m = w.uniform_mesh(2, nb, (n // nb, 1), lo=(0, 0, 0), hi=(1, nb / n, 1))
+    dx = 1.0 / n
+    nu = 0.4
+    dt = nu * dx / ch
+    A = 1e-2
+
+    def profile(j):
+        return A * (np.cos(2 * math.pi * 3 * j / n + 0.3) + 0.8 * ((j >= 20) & (j < 34)) - 0.5 * ((j >= 44) & (j < 52)))
+
+    def ic(X, Y, Z, **_):
+        j = np.rint(X / dx - 0.5)
+        wv = profile(j)
+        U = conserved_from_primitive(np.ones_like(X), 0.0, 0.0, 0.0, wv / (2 * sign * ch), 0.0, 0.0, 1.0, 5 / 3)
+        U[8] = wv / 2
+        return U
+
+    o = Oracle(m, w.evaluate_on_mesh(m, ic))
+    p = P(scheme="mmc", limiter=limiter, eglm=0, ch_mode="fixed", ch=ch, cp_mode="fixed", cp=0.0,
+          dt_override=dt)
+    o.fill_ghosts()
+    o.cfl(p)
+    assert o.step(p) == 0
+    U = o.get_state()
+    got = assemble_uniform(m, U, 8)[0, 0] + sign * ch * assemble_uniform(m, U, 4)[0, 0]
+    other = assemble_uniform(m, U, 8)[0, 0] - sign * ch * assemble_uniform(m, U, 4)[0, 0]
+
+    w0 = profile(np.arange(n).astype(float))
+    jump = np.roll(w0, -1) - w0                                   # w_{i+1} - w_i at face i+1/2
+    up = np.roll(jump, 1) if sign > 0 else np.roll(jump, -1)      # the upwind neighbour's jump
+    safe = np.where(jump == 0.0, 1.0, jump)
+    lim = np.where(jump == 0.0, 0.0, _sweby_phi(limiter, up / safe) * jump)
+    F = (ch * w0 if sign > 0 else -ch * np.roll(w0, -1)) + 0.5 * ch * (1 - nu) * lim
+    want = w0 - dt / dx * (F - np.roll(F, 1))
+    np.testing.assert_allclose(got, want, rtol=0, atol=1e-15)
+    np.testing.assert_allclose(other, 0.0, rtol=0, atol=1e-15)
+    assert np.abs(lim).max() > 0 and np.count_nonzero(lim != jump) > 4   # the limiter acts
+
+
 # --- domain of dependence: the face speeds are local ---------------------------------------
 
 @pytest.mark.parametrize("scheme,limiter", [("mmc", "minmod"), ("mmc", "vanleer"), ("lf", "vanleer"),
