@@ -14,8 +14,8 @@
  * reaches them on their own): which speeds the two neighbouring g terms inside MMC's limiter
  * ratio use where the speed varies (the face speeds of h and of the face's own g terms are
  * pinned by closed forms, the ratio's structure by Sweby's form at constant speed, and the
- * speeds' locality and symmetry by invariants) and the long-time AMR results; these are
- * checked only through invariants.
+ * speeds' locality and symmetry by invariants) and long runs that regrid as they go (each
+ * regrid is pinned; their long-time combination is checked through conservation).
  */
 #ifndef MAP_ORACLE_H
 #define MAP_ORACLE_H
