@@ -72,3 +72,34 @@ def quadratic_estimate(a, b, c, h, eps, refine, X, Y):
     first = B * du / (np.abs(u) + eps)
     second = (1.0 - B) * d2u / (du + F * (np.abs(u) + eps))
     return first, first + second
+
+
+def two_level_mesh(n, ny_blocks, lo, hi, fine):
+    """A periodic 2D mesh of n/16 x ny_blocks base blocks of 16^2 in which the blocks with
+    fine(i, j, n/16) are split once (a static two-level mesh)."""
+    import workloads as w
+    nbx = n // 16
+    prob = w.Problem((nbx, ny_blocks, 1), lo, hi)
+    leaves = []
+    for j in range(ny_blocks):
+        for i in range(nbx):
+            if fine(i, j, nbx):
+                leaves += [(0, 1, 2 * i + di, 2 * j + dj, 0) for dj in range(2) for di in range(2)]
+            else:
+                leaves.append((0, 0, i, j, 0))
+    return w.Mesh(2, 16, [prob], np.asarray(leaves, dtype=np.int32))
+
+
+def advection_strip(n, refined):
+    """The 1D advection strip of Table 1 (x in [-0.5, 0.5], one block high), with the middle
+    half refined once when ``refined``."""
+    return two_level_mesh(n, 1, (-0.5, 0, 0), (0.5, 16.0 / n, 1),
+                          lambda i, j, nbx: refined and nbx // 4 <= i < 3 * nbx // 4)
+
+
+def advection_1d(X, Y, Z, t=0.0, **_):
+    """Table 1's density wave, (sin 2 pi (x - t) + 2) / 3 at unit speed, exact at time t."""
+    from workloads.problems import conserved_from_primitive
+    rho = (np.sin(2 * math.pi * (X - t)) + 2) / 3
+    return conserved_from_primitive(rho, 1.0, 0.0, 0.0, 0.0, 0.0, 0.0, 1.0, 1.4)
+

@@ -18,7 +18,8 @@ from workloads.problems import (advection_2d, alfven_wave, brio_wu, conserved_fr
                                 divb_bump, ensemble_problem, field_loop, orszag_tang, uniform_state)
 from oracle import Oracle
 from oracle import oracle as O
-from tests.helpers import assemble_uniform, l1, quadratic_estimate, run_to_time
+from tests.helpers import (advection_1d, advection_strip, assemble_uniform, l1, quadratic_estimate,
+                           run_to_time, two_level_mesh)
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 SCHEMES = ("mmc", "lf", "weno")
@@ -199,20 +200,6 @@ def test_table2_2d_advection(scheme):
 
 # --- 5b. long runs on a static two-level mesh ----------------------------------------------
 
-def _two_level_mesh(n, ny_blocks, lo, hi, fine):
-    """Base n/16 x ny_blocks blocks of 16^2 (periodic); blocks with fine(i, j) split once."""
-    nbx = n // 16
-    prob = w.Problem((nbx, ny_blocks, 1), lo, hi)
-    leaves = []
-    for j in range(ny_blocks):
-        for i in range(nbx):
-            if fine(i, j, nbx):
-                leaves += [(0, 1, 2 * i + di, 2 * j + dj, 0) for dj in range(2) for di in range(2)]
-            else:
-                leaves.append((0, 0, i, j, 0))
-    return w.Mesh(2, 16, [prob], np.asarray(leaves, dtype=np.int32))
-
-
 def _amr_advection(m, ic, params, T):
     """L1(rho) against the exact solution, area-weighted over the leaves, and the relative
     change of the total mass, after a run to time T."""
@@ -238,15 +225,8 @@ def test_long_run_on_a_static_two_level_strip(scheme):
     a ghost-fill mistake confined to the interface cells (a flipped prolongation slope,
     restriction by injection) moves the L1 error only at second order and is left to the
     ghost-fill pins above, which fail on either."""
-    def ic(X, Y, Z, t=0.0, **_):
-        rho = (np.sin(2 * math.pi * (X - t)) + 2) / 3
-        return conserved_from_primitive(rho, 1.0, 0.0, 0.0, 0.0, 0.0, 0.0, 1.0, 1.4)
-
+    ic, strip = advection_1d, advection_strip
     params = P(gamma=1.4, c_cfl=0.8, scheme=scheme)
-
-    def strip(n, refined):
-        return _two_level_mesh(n, 1, (-0.5, 0, 0), (0.5, 16.0 / n, 1),
-                               lambda i, j, nbx: refined and nbx // 4 <= i < 3 * nbx // 4)
 
     e_coarse = _amr_advection(strip(64, False), ic, params, 1.0)[0]
     e_fine = _amr_advection(strip(128, False), ic, params, 1.0)[0]
@@ -275,9 +255,9 @@ def test_long_run_on_a_static_two_level_square(scheme):
     params = P(gamma=1.4, scheme=scheme)
 
     def square(n, refined):
-        return _two_level_mesh(n, n // 16, (-0.5, -s3 / 2, 0), (0.5, s3 / 2, 1),
-                               lambda i, j, nbx: refined and nbx // 4 <= i < 3 * nbx // 4
-                               and nbx // 4 <= j < 3 * nbx // 4)
+        return two_level_mesh(n, n // 16, (-0.5, -s3 / 2, 0), (0.5, s3 / 2, 1),
+                              lambda i, j, nbx: refined and nbx // 4 <= i < 3 * nbx // 4
+                              and nbx // 4 <= j < 3 * nbx // 4)
 
     u32 = _amr_advection(square(32, False), advection_2d, params, 0.5)[0]
     u64 = _amr_advection(square(64, False), advection_2d, params, 0.5)[0]
