@@ -158,7 +158,7 @@ def test_long_run_on_a_static_two_level_strip(gpulib, scheme):
     the run the FP64 GPU state stays within 1e-9 of the oracle's and keeps the mass to
     round-off; the FP32 batched form (graph-replayed steps) ends with the FP64 error against
     the exact solution to 1 % and the mass to 1e-6."""
-    from paper_1204_5849_gb300 import MAP_FP32, MAP_FP64
+    from paper_1204_5849_gb300 import MAP_FP32_FIX64, MAP_FP64
     mesh = advection_strip(64, True)
     U0 = w.evaluate_on_mesh(mesh, advection_1d)
     nsteps = 1000
@@ -178,9 +178,9 @@ def test_long_run_on_a_static_two_level_strip(gpulib, scheme):
     assert abs(pool.conservation()[0, 0] - s0) <= 1e-14 * s0
     assert pool.check() == 0
     exact = w.evaluate_on_mesh(mesh, advection_1d, t=1.0)[:, 0]
-    area = np.array([np.prod(mesh.leaf_dx(b)[:2]) for b in range(mesh.nleaves)])[:, None, None]
+    area = np.array([np.prod(mesh.leaf_dx(b)[:2]) for b in range(mesh.nleaves)])[:, None, None, None]
     e64 = float((np.abs(R[:, 0] - exact) * area).sum())
-    p32 = pool_for(mesh, MAP_FP32, U0)
+    p32 = pool_for(mesh, MAP_FP32_FIX64, U0)
     p32.advance(p, nsteps)
     e32 = float((np.abs(p32.read_leaves()[:, 0] - exact) * area).sum())
     assert abs(e32 - e64) <= 0.01 * e64, (e32, e64)
