@@ -259,10 +259,134 @@ void orc_hllc_flux(int d, const double* a, const double* b, double gamma, double
   FLOPS(11);
 }
 
-/* Interface flux of LF and WENO: f_m (Equ:LFFlux) or HLLC. */
+/* HLLD flux for MHD (Miyoshi & Kusano, J. Comput. Phys. 208, 2005), which the paper names
+ * among the approximate Riemann solvers of MAP for LF and WENO and compares with HLLC on the
+ * Brio-Wu tube (Sec. 3.2, Sec. 5), without printing it.  It resolves five waves: the fast
+ * waves S_L, S_R, the rotational (Alfven) waves S*_L, S*_R and the contact S_M, with the
+ * normal velocity S_M, the total pressure p_T* and the normal field constant inside the fan.
+ * Steps 1-3 are those of orc_hllc_flux: the (B_d, psi) pair keeps the exact upwind flux of
+ * its linear system, both states take the interface normal field B_n = B_m at unchanged gas
+ * pressure, and the fast-wave bounds are S_L = min(u - c_f), S_R = max(u + c_f).  Then, with
+ * d_K = S_K - u_K for the sides K = L (a), R (b):
+ * 4. S_M = (d_R rho_R u_R - d_L rho_L u_L - p_T,R + p_T,L) / (d_R rho_R - d_L rho_L),
+ *    p_T* = (d_R rho_R p_T,L - d_L rho_L p_T,R + rho_L rho_R d_R d_L (u_R - u_L))
+ *           / (d_R rho_R - d_L rho_L).
+ * 5. Outer states U*_K: rho* = rho_K d_K/(S_K - S_M), normal velocity S_M, and with
+ *    D_K = rho_K d_K (S_K - S_M) - B_n^2, for each tangential direction t,
+ *      v*_t = v_t - B_n B_t (S_M - u_K)/D_K,  B*_t = B_t (rho_K d_K^2 - B_n^2)/D_K
+ *    (v and B unchanged where D_K vanishes, the fast and Alfven waves then coinciding),
+ *      E* = (d_K E_K - p_T,K u_K + p_T* S_M + B_n (v_K.B_K - v*.B*))/(S_K - S_M).
+ * 6. Inner states U**_K (sigma = sign B_n, r_K = sqrt(rho*_K); the density is rho*_K):
+ *      v**_t = (r_L v*_t,L + r_R v*_t,R + sigma (B*_t,R - B*_t,L))/(r_L + r_R),
+ *      B**_t = (r_L B*_t,R + r_R B*_t,L + sigma r_L r_R (v*_t,R - v*_t,L))/(r_L + r_R),
+ *      E**_L = E*_L - sigma r_L (v*_L.B*_L - v**.B**),  E**_R = E*_R + sigma r_R (v*_R.B*_R - v**.B**).
+ * 7. With S*_L = S_M - |B_n|/r_L and S*_R = S_M + |B_n|/r_R the flux is that of the region
+ *    holding the interface: F_L, F_L + S_L (U*_L - U_L), that + S*_L (U**_L - U*_L), the
+ *    mirror images on the right, or F_R.  With B_n = 0 the inner region has no width and the
+ *    solver is HLLC's. */
+void orc_hlld_flux(int d, const double* a, const double* b, double gamma, double ch, double* f) {
+  double bm;
+  if (ch > 0.0) bm = 0.5 * (a[BX + d] + b[BX + d]) - (b[PSI] - a[PSI]) / (2.0 * ch);
+  else bm = 0.5 * (a[BX + d] + b[BX + d]);
+  double w[2][NV], F[2][NV], u[2], cf[2], pt[2];
+  for (int k = 0; k < 2; ++k) {
+    const double* q = k ? b : a;
+    for (int v = 0; v < NV; ++v) w[k][v] = q[v];
+    const double p = pressure(q, gamma);
+    w[k][BX + d] = bm;
+    w[k][EN] = q[EN] + 0.5 * (bm * bm - q[BX + d] * q[BX + d]);
+    orc_flux(d, w[k], gamma, ch, F[k]);
+    u[k] = w[k][MX + d] / w[k][RHO];
+    cf[k] = fast_speed(d, w[k], gamma);
+    pt[k] = p + 0.5 * (w[k][BX] * w[k][BX] + w[k][BY] * w[k][BY] + w[k][BZ] * w[k][BZ]);
+    FLOPS(15);
+  }
+  const double sl = fmin(u[0] - cf[0], u[1] - cf[1]);
+  const double sr = fmax(u[0] + cf[0], u[1] + cf[1]);
+  FLOPS(4);
+  if (sl >= 0.0) {
+    for (int v = 0; v < NV; ++v) f[v] = F[0][v];
+  } else if (sr <= 0.0) {
+    for (int v = 0; v < NV; ++v) f[v] = F[1][v];
+  } else {
+    const int tt[2] = {d == 0 ? 1 : 0, d == 2 ? 1 : 2};      /* tangential dimensions */
+    const double sk[2] = {sl, sr};
+    const double dl = sl - u[0], dr = sr - u[1];
+    const double ra = w[0][RHO], rb = w[1][RHO];
+    const double den = dr * rb - dl * ra;
+    const double sm = (dr * rb * u[1] - dl * ra * u[0] - pt[1] + pt[0]) / den;
+    const double pts = (dr * rb * pt[0] - dl * ra * pt[1] + ra * rb * dr * dl * (u[1] - u[0])) / den;
+    double us[2][NV], uss[2][NV], vs[2][3], bs[2][3], rs[2], vbs[2];
+    for (int k = 0; k < 2; ++k) {
+      const double* wk = w[k];
+      const double rho = wk[RHO], dk = sk[k] - u[k], ds = sk[k] - sm;
+      rs[k] = rho * dk / ds;
+      const double D = rho * dk * ds - bm * bm;
+      const int flat = fabs(D) <= 1e-12 * (fabs(rho * dk * ds) + bm * bm);
+      double vb = 0.0;
+      for (int j = 0; j < 3; ++j) vb += (wk[MX + j] / rho) * wk[BX + j];
+      vs[k][d] = sm;
+      bs[k][d] = bm;
+      for (int t = 0; t < 2; ++t) {
+        const int j = tt[t];
+        const double vt = wk[MX + j] / rho, bt = wk[BX + j];
+        vs[k][j] = flat ? vt : vt - bm * bt * (sm - u[k]) / D;
+        bs[k][j] = flat ? bt : bt * (rho * dk * dk - bm * bm) / D;
+      }
+      vbs[k] = vs[k][0] * bs[k][0] + vs[k][1] * bs[k][1] + vs[k][2] * bs[k][2];
+      us[k][RHO] = rs[k];
+      for (int j = 0; j < 3; ++j) {
+        us[k][MX + j] = rs[k] * vs[k][j];
+        us[k][BX + j] = bs[k][j];
+      }
+      us[k][EN] = (dk * wk[EN] - pt[k] * u[k] + pts * sm + bm * (vb - vbs[k])) / ds;
+      us[k][PSI] = wk[PSI];
+      FLOPS(6 + 6 + 2 * 8 + 5 + 6 + 10);
+    }
+    const double sgn = bm > 0.0 ? 1.0 : (bm < 0.0 ? -1.0 : 0.0);
+    const double rl = sqrt(rs[0]), rr = sqrt(rs[1]);
+    const double ssl = sm - fabs(bm) / rl, ssr = sm + fabs(bm) / rr;
+    double vss[3], bss[3];
+    vss[d] = sm;
+    bss[d] = bm;
+    for (int t = 0; t < 2; ++t) {
+      const int j = tt[t];
+      vss[j] = (rl * vs[0][j] + rr * vs[1][j] + sgn * (bs[1][j] - bs[0][j])) / (rl + rr);
+      bss[j] = (rl * bs[1][j] + rr * bs[0][j] + sgn * rl * rr * (vs[1][j] - vs[0][j])) / (rl + rr);
+    }
+    const double vbss = vss[0] * bss[0] + vss[1] * bss[1] + vss[2] * bss[2];
+    for (int k = 0; k < 2; ++k) {
+      uss[k][RHO] = rs[k];
+      for (int j = 0; j < 3; ++j) {
+        uss[k][MX + j] = rs[k] * vss[j];
+        uss[k][BX + j] = bss[j];
+      }
+      uss[k][EN] = k == 0 ? us[0][EN] - sgn * rl * (vbs[0] - vbss) : us[1][EN] + sgn * rr * (vbs[1] - vbss);
+      uss[k][PSI] = w[k][PSI];
+    }
+    FLOPS(2 + 4 + 2 * 16 + 5 + 2 * 8);
+    if (ssl >= 0.0) {
+      for (int v = 0; v < NV; ++v) f[v] = F[0][v] + sl * (us[0][v] - w[0][v]);
+    } else if (sm >= 0.0) {
+      for (int v = 0; v < NV; ++v) f[v] = F[0][v] + sl * (us[0][v] - w[0][v]) + ssl * (uss[0][v] - us[0][v]);
+    } else if (ssr >= 0.0) {
+      for (int v = 0; v < NV; ++v) f[v] = F[1][v] + sr * (us[1][v] - w[1][v]) + ssr * (uss[1][v] - us[1][v]);
+    } else {
+      for (int v = 0; v < NV; ++v) f[v] = F[1][v] + sr * (us[1][v] - w[1][v]);
+    }
+    FLOPS(5 * NV);
+  }
+  /* the (B_d, psi) pair: exact upwind flux of the linear GLM subsystem (as in f_m) */
+  f[BX + d] = 0.5 * ((a[PSI] + b[PSI]) - ch * (b[BX + d] - a[BX + d]));
+  f[PSI] = 0.5 * ((ch * ch * a[BX + d] + ch * ch * b[BX + d]) - ch * (b[PSI] - a[PSI]));
+  FLOPS(11);
+}
+
+/* Interface flux of LF and WENO: f_m (Equ:LFFlux), HLLC or HLLD. */
 static void riemann_flux(int riemann, int d, const double* a, const double* b, double gamma, double ch,
                          double* f) {
   if (riemann == 1) orc_hllc_flux(d, a, b, gamma, ch, f);
+  else if (riemann == 2) orc_hlld_flux(d, a, b, gamma, ch, f);
   else orc_lf_flux(d, a, b, gamma, ch, f);
 }
 
@@ -434,7 +558,7 @@ typedef struct {
   double gamma, ch, dt, eta;
   int eglm, limiter;
   double dx[3];
-  int riemann;    /* interface flux of LF and WENO: 0 f_m (Lax-Friedrichs), 1 HLLC */
+  int riemann;    /* interface flux of LF and WENO: 0 f_m (Lax-Friedrichs), 1 HLLC, 2 HLLD */
   double* freg;   /* face register of the block (reflux), or NULL */
   double fw;      /* weight of this update's fluxes in the register (1, or 1/2 per RK2 stage) */
 } stepctx;

@@ -36,7 +36,7 @@ typedef struct {
   int limiter;      /* 0 minmod, 1 van Leer, 2 literal Roe form, 3 phi = 1, 4 phi = 0 (2-4: MMC only) */
   double dt_override; /* > 0: use this dt */
   int reflux;       /* 1: coarse fluxes at coarse/fine faces replaced by the fine ones */
-  int riemann;      /* interface flux of LF and WENO: 0 f_m (Lax-Friedrichs), 1 HLLC */
+  int riemann;      /* interface flux of LF and WENO: 0 f_m (Lax-Friedrichs), 1 HLLC, 2 HLLD */
   int conduction;   /* thermal conduction: 0 off, 1 isotropic, 2 along B (kappa0 T^(5/2)) */
   double kappa0;
   int subcycle;     /* 1: conduction subcycled within each step; 0: it bounds dt */
@@ -94,6 +94,7 @@ int orc_block_step(int ndim, int nb, const orc_params* p, const double* dx, doub
 void orc_flux(int d, const double* w, double gamma, double ch, double* f);
 double orc_alpha(int d, const double* w, double gamma);
 void orc_hllc_flux(int d, const double* a, const double* b, double gamma, double ch, double* f);
+void orc_hlld_flux(int d, const double* a, const double* b, double gamma, double ch, double* f);
 void orc_lf_flux(int d, const double* a, const double* b, double gamma, double ch, double* f);
 double orc_limiter(int kind, double a, double b);
 void orc_weno_faces(double um, double u0, double up, double* minus_right, double* plus_left);

@@ -14,7 +14,7 @@ import numpy as np
 from . import build as _build
 
 SCHEMES = {"mmc": 0, "lf": 1, "weno": 2}
-RIEMANN = {"lf": 0, "hllc": 1}
+RIEMANN = {"lf": 0, "hllc": 1, "hlld": 2}
 CONDUCTION = {"off": 0, "isotropic": 1, "aligned": 2}
 LIMITERS = {"minmod": 0, "vanleer": 1, "roe": 2, "none": 3, "zero": 4}
 CH_MODES = {"auto": 0, "paper": 1, "fixed": 2}
@@ -90,6 +90,7 @@ def _declare(L):
         L.orc_alpha.argtypes = [C.c_int, dp, C.c_double]
         L.orc_lf_flux.argtypes = [C.c_int, dp, dp, C.c_double, C.c_double, dp]
         L.orc_hllc_flux.argtypes = [C.c_int, dp, dp, C.c_double, C.c_double, dp]
+        L.orc_hlld_flux.argtypes = [C.c_int, dp, dp, C.c_double, C.c_double, dp]
         L.orc_limiter.restype = C.c_double
         L.orc_limiter.argtypes = [C.c_int, C.c_double, C.c_double]
         L.orc_weno_faces.argtypes = [C.c_double, C.c_double, C.c_double, dp, dp]
@@ -271,6 +272,14 @@ def hllc_flux(d: int, a, b, gamma: float, ch: float) -> np.ndarray:
     b = np.ascontiguousarray(b, dtype=np.float64)
     f = np.zeros(9)
     lib().orc_hllc_flux(d, _dp(a), _dp(b), gamma, ch, _dp(f))
+    return f
+
+
+def hlld_flux(d: int, a, b, gamma: float, ch: float) -> np.ndarray:
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    f = np.zeros(9)
+    lib().orc_hlld_flux(d, _dp(a), _dp(b), gamma, ch, _dp(f))
     return f
 
 
