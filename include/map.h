@@ -45,9 +45,10 @@ typedef enum {
 enum { MAP_FP64 = 0, MAP_FP32_FIX64 = 1 };   /* pool precision */
 enum { MAP_MMC = 0, MAP_LF = 1, MAP_WENO = 2 };
 enum { MAP_MINMOD = 0, MAP_VANLEER = 1 };
-/* Interface flux of LF and WENO (Sec. 3.2-3.3): the Lax-Friedrichs f_m (Equ:LFFlux) or the
- * HLLC approximate Riemann solver for MHD the paper uses in 2D and 3D. */
-enum { MAP_RIEMANN_LF = 0, MAP_RIEMANN_HLLC = 1 };
+/* Interface flux of LF and WENO (Sec. 3.2-3.3): the Lax-Friedrichs f_m (Equ:LFFlux), the
+ * HLLC approximate Riemann solver for MHD the paper uses in 2D and 3D, or the HLLD solver
+ * (Miyoshi & Kusano) it also names and compares on the Brio-Wu tube (Sec. 5). */
+enum { MAP_RIEMANN_LF = 0, MAP_RIEMANN_HLLC = 1, MAP_RIEMANN_HLLD = 2 };
 /* Thermal conduction (Sec. 3.6): off, isotropic, or along the field (the form of the paper's
  * conduction test, Sec. 5), kappa = kappa0 T^(5/2) with T = p / rho. */
 enum { MAP_COND_OFF = 0, MAP_COND_ISOTROPIC = 1, MAP_COND_ALIGNED = 2 };
@@ -104,11 +105,12 @@ typedef struct {
   int reflux;         /* 1: at every coarse/fine face the coarse leaf's flux is replaced by
                          the mean of the fine fluxes covering it (Sec. 4.2, boundary step
                          (2)), so the face carries one flux on both sides; 0: off */
-  int riemann;        /* MAP_RIEMANN_LF or MAP_RIEMANN_HLLC (LF and WENO; MMC takes only
-                         MAP_RIEMANN_LF, else MAP_EINVAL).  HLLC: the (B_d, psi) pair keeps
-                         the exact upwind flux of its linear system, which also fixes the
-                         interface normal field; the other seven components come from the
-                         HLLC star states with Davis speed bounds */
+  int riemann;        /* MAP_RIEMANN_LF, _HLLC or _HLLD (LF and WENO; MMC takes only
+                         MAP_RIEMANN_LF, else MAP_EINVAL).  HLLC and HLLD: the (B_d, psi)
+                         pair keeps the exact upwind flux of its linear system, which also
+                         fixes the interface normal field; the other seven components come
+                         from the solver's intermediate states with Davis speed bounds (HLLD
+                         adds the two Alfven waves to HLLC's contact) */
   int conduction;     /* MAP_COND_*: after each step the energy takes the conduction update
                          e += h sum_d dF_d/dx_d, F = sqrt(kappa_l kappa_r)(T_r - T_l)/dx (along
                          B: times b_d (b . grad T)/|grad_d T| with b from the face-mean B) */

@@ -31,6 +31,10 @@ UNITS = {
     "kernels_f32_rfx.cu": ["-ftz=true", "-prec-div=false", "-prec-sqrt=false"],
     "kernels_f64_hllc_rfx.cu": ["-fmad=false"],
     "kernels_f32_hllc_rfx.cu": ["-ftz=true", "-prec-div=false", "-prec-sqrt=false"],
+    "kernels_f64_hlld.cu": ["-fmad=false"],
+    "kernels_f32_hlld.cu": ["-ftz=true", "-prec-div=false", "-prec-sqrt=false"],
+    "kernels_f64_hlld_rfx.cu": ["-fmad=false"],
+    "kernels_f32_hlld_rfx.cu": ["-ftz=true", "-prec-div=false", "-prec-sqrt=false"],
     "common.cu": ["-fmad=false"],
     "noalloc.cu": ["-fmad=false"],
 }

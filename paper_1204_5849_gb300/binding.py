@@ -21,7 +21,7 @@ STATUS = {0: "MAP_OK", -1: "MAP_EINVAL", -2: "MAP_ENOMEM", -3: "MAP_ECUDA", -4: 
 MAP_FP64, MAP_FP32_FIX64 = 0, 1
 SCHEMES = {"mmc": 0, "lf": 1, "weno": 2}
 LIMITERS = {"minmod": 0, "vanleer": 1}
-RIEMANN = {"lf": 0, "hllc": 1}
+RIEMANN = {"lf": 0, "hllc": 1, "hlld": 2}
 CONDUCTION = {"off": 0, "isotropic": 1, "aligned": 2}
 CH_MODES = {"auto": 0, "paper": 1, "fixed": 2}
 CP_MODES = {"cd": 0, "fixed": 1}

@@ -670,12 +670,13 @@ const char* mapgb::params_problem(const map_params* p) {
   if (p->ch_mode < 0 || p->ch_mode > 2 || p->cp_mode < 0 || p->cp_mode > 1) return "bad c_h / c_p mode";
   if (p->cp_mode == MAP_CP_FROM_CD && !(p->c_d > 0.0 && p->c_d < 1.0)) return "c_d must lie in (0,1)";
   if (!(p->eta >= 0.0)) return "eta must be >= 0";
-  if (p->riemann != MAP_RIEMANN_LF && p->riemann != MAP_RIEMANN_HLLC) return "bad riemann";
+  if (p->riemann != MAP_RIEMANN_LF && p->riemann != MAP_RIEMANN_HLLC && p->riemann != MAP_RIEMANN_HLLD)
+    return "bad riemann";
   if (p->conduction < MAP_COND_OFF || p->conduction > MAP_COND_ALIGNED) return "bad conduction mode";
   if (p->conduction && !(p->kappa0 > 0.0)) return "conduction needs kappa0 > 0";
   if (!(p->grad_t_max >= 0.0)) return "grad_t_max must be >= 0";
-  if (p->riemann == MAP_RIEMANN_HLLC && p->scheme == MAP_MMC)
-    return "HLLC is an interface flux of LF and WENO; MMC takes MAP_RIEMANN_LF";
+  if (p->riemann != MAP_RIEMANN_LF && p->scheme == MAP_MMC)
+    return "HLLC and HLLD are interface fluxes of LF and WENO; MMC takes MAP_RIEMANN_LF";
   return nullptr;
 }
 

@@ -48,8 +48,8 @@ cudaError_t launch_step_one(const StepLaunch& L, cudaStream_t s) {
 }
 
 // Each (FLX, RFX) pair is instantiated in its own translation unit (kernels_<prec>.cu,
-// _hllc.cu, _rfx.cu, _hllc_rfx.cu).  FLX = FLX_HLLC covers LF and WENO only (MMC has no
-// interface Riemann problem).
+// _hllc.cu, _hlld.cu, _rfx.cu, _hllc_rfx.cu, _hlld_rfx.cu).  FLX = FLX_HLLC and FLX_HLLD
+// cover LF and WENO only (MMC has no interface Riemann problem).
 template <typename T, int NDIM, int NB, int FLX, bool RFX>
 cudaError_t launch_step_geo(const StepLaunch& L, cudaStream_t s) {
   const int lim = L.limiter ? 1 : 0;
@@ -302,6 +302,7 @@ cudaError_t launch_cfl_partial_T(const KernelConfig& kc, const void* u, int nblo
   namespace mapgb {                                                                                \
   cudaError_t launch_step_##SUFFIX(const KernelConfig& k, const StepLaunch& l, cudaStream_t s, long long* c) { \
     const bool rfx = l.freg != nullptr;                                                          \
+    if (l.riemann == 2) return rfx ? launch_step_hlld_rfx_##SUFFIX(k, l, s, c) : launch_step_hlld_##SUFFIX(k, l, s, c); \
     if (l.riemann) return rfx ? launch_step_hllc_rfx_##SUFFIX(k, l, s, c) : launch_step_hllc_##SUFFIX(k, l, s, c); \
     return rfx ? launch_step_rfx_##SUFFIX(k, l, s, c) : launch_step_T<T, FLX_LF, false>(k, l, s, c); } \
   cudaError_t launch_fill_##SUFFIX(const KernelConfig& k, const FillLaunch& l, cudaStream_t s, long long* c) { return launch_fill_T<T>(k, l, s, c); } \

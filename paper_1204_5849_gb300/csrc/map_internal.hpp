@@ -178,7 +178,7 @@ struct StepLaunch {
   double* sums;            // optional FP64 conservation sums [nprob][9] of the output
   ProbDyn* dyn_next;       // optional: max alpha of the output into dyn_next[p].alpha_bits
   int grid;                // CTAs (0 = one per block)
-  int riemann;             // interface flux of LF and WENO: 0 f_m, 1 HLLC
+  int riemann;             // interface flux of LF and WENO: 0 f_m, 1 HLLC, 2 HLLD
   int w_pred = 0, w_face = 0;  // warp-schedule weights (0: default_schedule_weights)
   int fail_waits = 0;          // test hook (map_test_fail_waits)
   const PushEntry* pushes; // optional: write boundary layers into same-level neighbours' ghosts
@@ -344,6 +344,10 @@ cudaError_t launch_step_rfx_f64(const KernelConfig&, const StepLaunch&, cudaStre
 cudaError_t launch_step_rfx_f32(const KernelConfig&, const StepLaunch&, cudaStream_t, long long*);
 cudaError_t launch_step_hllc_rfx_f64(const KernelConfig&, const StepLaunch&, cudaStream_t, long long*);
 cudaError_t launch_step_hllc_rfx_f32(const KernelConfig&, const StepLaunch&, cudaStream_t, long long*);
+cudaError_t launch_step_hlld_f64(const KernelConfig&, const StepLaunch&, cudaStream_t, long long*);
+cudaError_t launch_step_hlld_f32(const KernelConfig&, const StepLaunch&, cudaStream_t, long long*);
+cudaError_t launch_step_hlld_rfx_f64(const KernelConfig&, const StepLaunch&, cudaStream_t, long long*);
+cudaError_t launch_step_hlld_rfx_f32(const KernelConfig&, const StepLaunch&, cudaStream_t, long long*);
 
 cudaError_t launch_finalize(const FinalizeLaunch&, cudaStream_t, long long*);
 cudaError_t launch_zero_alpha(ProbDyn* dyn, int nprob, cudaStream_t, long long*);

@@ -237,6 +237,139 @@ __device__ __forceinline__ void hllc_flux(const T* a, const T* b, const Phys<T>&
   f[PSI] = T(0.5) * ((ch * ch * a[BX + D] + ch * ch * b[BX + D]) - ch * (b[PSI] - a[PSI]));
 }
 
+// HLLD interface flux for MHD (Miyoshi & Kusano 2005, which the paper names among MAP's
+// approximate Riemann solvers for LF and WENO and compares with HLLC on the Brio-Wu tube,
+// Sec. 3.2, Sec. 5).  Five waves: the fast bounds S_L, S_R, the rotational (Alfven) waves
+// S*_L = S_M - |B_n|/sqrt(rho*_L), S*_R = S_M + |B_n|/sqrt(rho*_R) and the contact S_M, with
+// the normal velocity, total pressure and normal field constant inside the fan.
+// 1-3. As in hllc_flux: the (B_d, psi) pair keeps its exact upwind flux and fixes the
+//      interface normal field B_n = B_m, both states take it at unchanged gas pressure, and
+//      the fast bounds are S_L = min(u - c_f), S_R = max(u + c_f).
+// 4. S_M and p_T* from mass and normal momentum across S_L and S_R together.
+// 5. Outer states on each side: rho* = rho d/(S - S_M) (d = S - u), tangential velocity and
+//    field from the jump conditions across S, which divide by D = rho d (S - S_M) - B_n^2
+//    (velocity and field kept where D vanishes: the fast and Alfven waves coincide there),
+//    energy from the energy jump.
+// 6. Inner states: tangential velocity and field as the sqrt(rho*)-weighted combination of
+//    the two outer states, which the jump conditions across both Alfven waves fix; energy
+//    from the energy jump across each Alfven wave.
+// 7. The flux of the region holding the interface: F_K + S_K (U*_K - U_K), plus
+//    S*_K (U**_K - U*_K) in the inner region, K the side of the contact.  Only that side's
+//    states are built; the inner states need both sides' outer velocity, field and density.
+template <typename T, int D>
+__device__ __forceinline__ void hlld_flux(const T* a, const T* b, const Phys<T>& P, T* f) {
+  const T ch = P.ch;
+  const T bm = ch > T(0) ? T(0.5) * (a[BX + D] + b[BX + D]) - (b[PSI] - a[PSI]) / (T(2) * ch)
+                         : T(0.5) * (a[BX + D] + b[BX + D]);
+  T w[2][NV], F[2][NV], u[2], cf[2], pt[2];
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const T* q = k ? b : a;
+    const T p = pressure<T>(q, P);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) w[k][v] = q[v];
+    w[k][BX + D] = bm;
+    w[k][EN] = q[EN] + T(0.5) * (bm * bm - q[BX + D] * q[BX + D]);
+    const T pw = pressure<T>(w[k], P);
+    flux_p<T, D>(w[k], pw, P, F[k]);
+    u[k] = w[k][MX + D] / w[k][RHO];
+    cf[k] = fast_speed<T, D>(w[k], pw, P);
+    pt[k] = p + T(0.5) * (w[k][BX] * w[k][BX] + w[k][BY] * w[k][BY] + w[k][BZ] * w[k][BZ]);
+  }
+  const T sl = fmin(u[0] - cf[0], u[1] - cf[1]);
+  const T sr = fmax(u[0] + cf[0], u[1] + cf[1]);
+  if (sl >= T(0)) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) f[v] = F[0][v];
+  } else if (sr <= T(0)) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) f[v] = F[1][v];
+  } else {
+    constexpr int T1 = D == 0 ? 1 : 0, T2 = D == 2 ? 1 : 2;   // tangential dimensions
+    const T dl = sl - u[0], dr = sr - u[1];
+    const T ra = w[0][RHO], rb = w[1][RHO];
+    const T den = dr * rb - dl * ra;
+    const T sm = (dr * rb * u[1] - dl * ra * u[0] - pt[1] + pt[0]) / den;
+    const T pts = (dr * rb * pt[0] - dl * ra * pt[1] + ra * rb * dr * dl * (u[1] - u[0])) / den;
+    // outer-state velocity and field (absolute components), density, v*.B*, both sides
+    T vs[2][3], bs[2][3], rs[2], vbs[2];
+    const T tiny = sizeof(T) == 4 ? T(1e-6) : T(1e-12);
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      const T rho = w[k][RHO], dk = (k ? sr : sl) - u[k], ds = (k ? sr : sl) - sm;
+      rs[k] = rho * dk / ds;
+      const T Dk = rho * dk * ds - bm * bm;
+      const bool flat = fabs(Dk) <= tiny * (fabs(rho * dk * ds) + bm * bm);
+      vs[k][D] = sm;
+      bs[k][D] = bm;
+#pragma unroll
+      for (int t = 0; t < 2; ++t) {
+        const int j = t ? T2 : T1;
+        const T vt = w[k][MX + j] / rho, bt = w[k][BX + j];
+        vs[k][j] = flat ? vt : vt - bm * bt * (sm - u[k]) / Dk;
+        bs[k][j] = flat ? bt : bt * (rho * dk * dk - bm * bm) / Dk;
+      }
+      vbs[k] = vs[k][0] * bs[k][0] + vs[k][1] * bs[k][1] + vs[k][2] * bs[k][2];
+    }
+    const int k = sm >= T(0) ? 0 : 1;
+    const T sk = k ? sr : sl;
+    T wk[NV], Fk[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      wk[v] = k ? w[1][v] : w[0][v];
+      Fk[v] = k ? F[1][v] : F[0][v];
+    }
+    const T uk = k ? u[1] : u[0], ptk = k ? pt[1] : pt[0];
+    const T dk = sk - uk, ds = sk - sm;
+    const T rsk = k ? rs[1] : rs[0], vbsk = k ? vbs[1] : vbs[0];
+    T vb = T(0);
+#pragma unroll
+    for (int j = 0; j < 3; ++j) vb += (wk[MX + j] / wk[RHO]) * wk[BX + j];
+    T us[NV];
+    us[RHO] = rsk;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      us[MX + j] = rsk * (k ? vs[1][j] : vs[0][j]);
+      us[BX + j] = k ? bs[1][j] : bs[0][j];
+    }
+    us[EN] = (dk * wk[EN] - ptk * uk + pts * sm + bm * (vb - vbsk)) / ds;
+    us[PSI] = wk[PSI];
+    const T sgn = bm > T(0) ? T(1) : (bm < T(0) ? T(-1) : T(0));
+    const T rl = sqrt(rs[0]), rr = sqrt(rs[1]);
+    const T ssk = k ? sm + fabs(bm) / rr : sm - fabs(bm) / rl;
+    // left of the contact the inner region lies right of S*_L, right of it left of S*_R
+    const bool inner = k ? ssk >= T(0) : ssk < T(0);
+    if (inner) {
+      T vss[3], bss[3];
+      vss[D] = sm;
+      bss[D] = bm;
+#pragma unroll
+      for (int t = 0; t < 2; ++t) {
+        const int j = t ? T2 : T1;
+        vss[j] = (rl * vs[0][j] + rr * vs[1][j] + sgn * (bs[1][j] - bs[0][j])) / (rl + rr);
+        bss[j] = (rl * bs[1][j] + rr * bs[0][j] + sgn * rl * rr * (vs[1][j] - vs[0][j])) / (rl + rr);
+      }
+      const T vbss = vss[0] * bss[0] + vss[1] * bss[1] + vss[2] * bss[2];
+      T uss[NV];
+      uss[RHO] = rsk;
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        uss[MX + j] = rsk * vss[j];
+        uss[BX + j] = bss[j];
+      }
+      uss[EN] = k ? us[EN] + sgn * rr * (vbsk - vbss) : us[EN] - sgn * rl * (vbsk - vbss);
+      uss[PSI] = wk[PSI];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) f[v] = Fk[v] + sk * (us[v] - wk[v]) + ssk * (uss[v] - us[v]);
+    } else {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) f[v] = Fk[v] + sk * (us[v] - wk[v]);
+    }
+  }
+  f[BX + D] = T(0.5) * ((a[PSI] + b[PSI]) - ch * (b[BX + D] - a[BX + D]));
+  f[PSI] = T(0.5) * ((ch * ch * a[BX + D] + ch * ch * b[BX + D]) - ch * (b[PSI] - a[PSI]));
+}
+
 // Dissipation speed of component v in direction D: the (B_d, psi) pair uses c_h.
 template <int D>
 __device__ __forceinline__ bool glm_pair(int v) { return v == BX + D || v == PSI; }

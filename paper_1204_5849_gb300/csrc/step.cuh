@@ -31,7 +31,7 @@ namespace mapgb {
 
 enum { SCH_MMC = 0, SCH_LF = 1, SCH_WENO = 2 };
 static_assert(SCH_MMC == MAP_MMC && SCH_LF == MAP_LF && SCH_WENO == MAP_WENO, "scheme codes follow map.h");
-enum { FLX_LF = 0, FLX_HLLC = 1 };   // interface flux of LF and WENO: f_m or HLLC
+enum { FLX_LF = 0, FLX_HLLC = 1, FLX_HLLD = 2 };   // interface flux of LF and WENO: f_m, HLLC or HLLD
 
 template <typename T>
 struct StepArgsT {
@@ -732,6 +732,7 @@ step_kernel(StepArgsT<T> A) {
         exch_xy(yd, a);
         exch_xy(yd, b);
         if (FLX == FLX_HLLC) hllc_flux<T, 0>(a, b, P, F);
+        else if (FLX == FLX_HLLD) hlld_flux<T, 0>(a, b, P, F);
         else lf_flux<T, 0>(a, b, P, F);
       }
       exch_xy(yd, F);
@@ -817,6 +818,7 @@ step_kernel(StepArgsT<T> A) {
           }
         }
         if (FLX == FLX_HLLC) hllc_flux<T, 2>(a, b, P, F);
+        else if (FLX == FLX_HLLD) hlld_flux<T, 2>(a, b, P, F);
         else lf_flux<T, 2>(a, b, P, F);
       }
     };

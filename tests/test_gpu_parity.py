@@ -344,16 +344,17 @@ def test_last_sums_needs_an_advance_step(gpulib):
     np.testing.assert_allclose(pool.last_sums(), pool.conservation(), rtol=1e-13, atol=1e-15)
 
 
-# --- HLLC interface flux for LF and WENO (Sec. 3.2-3.3) -----------------------------------
+# --- HLLC and HLLD interface fluxes for LF and WENO (Sec. 3.2-3.3, Sec. 5) -----------------
 
+@pytest.mark.parametrize("rs", ["hllc", "hlld"])
 @pytest.mark.parametrize("scheme,limiter", [("lf", "minmod"), ("lf", "vanleer"), ("weno", "minmod")])
 @pytest.mark.parametrize("geom", [(2, 16, (3, 2, 1)), (3, 8, (2, 3, 2)), (3, 16, (2, 1, 2))])
-def test_fp64_hllc_matches_oracle(gpulib, scheme, limiter, geom):
+def test_fp64_riemann_solver_matches_oracle(gpulib, scheme, limiter, geom, rs):
     from paper_1204_5849_gb300 import MAP_FP64
     ndim, nb, nbase = geom
     mesh = w.uniform_mesh(ndim, nb, nbase)
     U0 = w.evaluate_on_mesh(mesh, _smooth_2d if ndim == 2 else _smooth_3d)
-    p = P(scheme=scheme, limiter=limiter, riemann="hllc")
+    p = P(scheme=scheme, limiter=limiter, riemann=rs)
     pool = pool_for(mesh, MAP_FP64, U0)
     orc = Oracle(mesh, U0)
     lockstep(pool, orc, p, 2)
@@ -361,37 +362,41 @@ def test_fp64_hllc_matches_oracle(gpulib, scheme, limiter, geom):
     assert pool.check() == 0
 
 
+@pytest.mark.parametrize("rs", ["hllc", "hlld"])
 @pytest.mark.parametrize("scheme", ["lf", "weno"])
-def test_fp64_hllc_amr_reflux_matches_oracle(gpulib, scheme):
+def test_fp64_riemann_solver_amr_reflux_matches_oracle(gpulib, scheme, rs):
     from paper_1204_5849_gb300 import MAP_FP64
     mesh = _REFLUX_MESHES["3d_nb8_periodic"]()
     U0 = _mixed_state(mesh)
-    p = P(scheme=scheme, riemann="hllc")
+    p = P(scheme=scheme, riemann=rs)
     pool = pool_for(mesh, MAP_FP64, U0)
     orc = Oracle(mesh, U0)
     lockstep(pool, orc, p, 3)
     assert rel_max(pool.read_leaves(), orc.get_state()).max() <= 1e-12
 
 
-def test_fp64_hllc_brio_wu_matches_oracle(gpulib):
-    """Strong shocks exercise every branch (supersonic sides, both star states)."""
+@pytest.mark.parametrize("rs", ["hllc", "hlld"])
+def test_fp64_riemann_solver_brio_wu_matches_oracle(gpulib, rs):
+    """Strong shocks exercise every branch (supersonic sides, both star states; HLLD's
+    inner states behind its Alfven waves, B_x = 0.75)."""
     from paper_1204_5849_gb300 import MAP_FP64
     n = 256
     mesh = w.uniform_mesh(2, 16, (n // 16, 1), lo=(-0.5, 0, 0), hi=(0.5, 16.0 / n, 1),
                           bc=((w.mesh.OUTFLOW, w.mesh.OUTFLOW), (0, 0), (0, 0)))
     U0 = w.evaluate_on_mesh(mesh, w.problems.brio_wu)
-    p = P(gamma=2.0, scheme="lf", riemann="hllc")
+    p = P(gamma=2.0, scheme="lf", riemann=rs)
     pool = pool_for(mesh, MAP_FP64, U0)
     orc = Oracle(mesh, U0)
     lockstep(pool, orc, p, 40)
     assert rel_max(pool.read_leaves(), orc.get_state()).max() <= 1e-10
 
 
-def test_fp32_hllc_alfven_l1(gpulib):
+@pytest.mark.parametrize("rs", ["hllc", "hlld"])
+def test_fp32_riemann_solver_alfven_l1(gpulib, rs):
     from paper_1204_5849_gb300 import MAP_FP32_FIX64
     mesh = w.uniform_mesh(3, 16, (2, 2, 2))
     U0 = w.evaluate_on_mesh(mesh, _smooth_3d)
-    p = P(scheme="lf", limiter="vanleer", riemann="hllc")
+    p = P(scheme="lf", limiter="vanleer", riemann=rs)
     pool = pool_for(mesh, MAP_FP32_FIX64, U0)
     pool.advance(p, 10)
     orc = Oracle(mesh, U0)
@@ -400,14 +405,40 @@ def test_fp32_hllc_alfven_l1(gpulib):
     assert pool.check() == 0
 
 
-def test_hllc_rejected_for_mmc(gpulib):
+@pytest.mark.parametrize("rs", ["hllc", "hlld"])
+def test_riemann_solvers_rejected_for_mmc(gpulib, rs):
     from paper_1204_5849_gb300 import MAP_FP64, MapError
     mesh = w.uniform_mesh(2, 16, (2, 2))
     pool = pool_for(mesh, MAP_FP64, _mixed_state(mesh))
     pool.fill_ghosts()
     with pytest.raises(MapError) as ei:
-        pool.cfl_dt(P(scheme="mmc", riemann="hllc"))
+        pool.cfl_dt(P(scheme="mmc", riemann=rs))
     assert ei.value.code == -1
+
+
+def test_fp64_hlld_rotational_discontinuity_at_rest_stays_put(gpulib):
+    """Two states joined by rotational discontinuities at rest (x = 0 and the periodic wrap),
+    the case HLLD resolves exactly and HLLC smears: ten LF steps on the GPU move no cell by
+    more than round-off and equal the oracle's."""
+    from paper_1204_5849_gb300 import MAP_FP64
+    from tests.test_hlld_pins import _rotational
+    mesh = w.uniform_mesh(2, 8, (8, 1), lo=(-0.5, 0, 0), hi=(0.5, 0.125, 1))
+    c = (0.2, -0.15)
+    a = _rotational(0, 1.7, 0.8, -1, (0.9, 0.3), c)
+    b = _rotational(0, 1.7, 0.8, -1, (-0.3, 0.9), c)
+
+    def ic(X, Y, Z, **_):
+        return np.where((X < 0.0)[None], a.reshape(9, 1, 1, 1), b.reshape(9, 1, 1, 1)) + 0.0 * X
+
+    U0 = w.evaluate_on_mesh(mesh, ic)
+    p = P(scheme="lf", limiter="minmod", riemann="hlld")
+    pool = pool_for(mesh, MAP_FP64, U0)
+    orc = Oracle(mesh, U0)
+    lockstep(pool, orc, p, 10)
+    G = pool.read_leaves()
+    assert np.abs(G - U0).max() <= 1e-12
+    assert rel_max(G, orc.get_state()).max() <= TOL1
+    assert pool.check() == 0
 
 
 # --- thermal conduction with subcycle (Sec. 3.6) -------------------------------------------
