@@ -23,11 +23,11 @@
  * phi(r)).  Locality is pinned too: one step changes nothing beyond two cells of a perturbed
  * cell, and the mirror and transpose symmetries exclude one-sided speeds.
  * Long runs on a static two-level mesh are pinned by conservation, by an error between the
- * all-coarse and all-fine meshes' and by the convergence order.
+ * all-coarse and all-fine meshes' and by the convergence order; a long run that regrids as
+ * it goes by conservation through every regrid and an error within 25 % of the mesh refined
+ * everywhere.
  * Parity unpinned: which speeds the two neighbouring g terms inside the limiter's ratio use
- * when the speed varies (here the face's own; a reading the paper leaves open), and runs
- * that regrid as they go (each regrid is pinned, their long-time combination only through
- * conservation).
+ * when the speed varies (here the face's own; a reading the paper leaves open).
  */
 #include "map_oracle.h"
 

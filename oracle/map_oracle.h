@@ -14,8 +14,7 @@
  * reaches them on their own): which speeds the two neighbouring g terms inside MMC's limiter
  * ratio use where the speed varies (the face speeds of h and of the face's own g terms are
  * pinned by closed forms, the ratio's structure by Sweby's form at constant speed, and the
- * speeds' locality and symmetry by invariants) and long runs that regrid as they go (each
- * regrid is pinned; their long-time combination is checked through conservation).
+ * speeds' locality and symmetry by invariants).
  */
 #ifndef MAP_ORACLE_H
 #define MAP_ORACLE_H
