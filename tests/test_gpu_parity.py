@@ -903,6 +903,67 @@ def test_regrid_matches_oracle(gpulib):
     assert rel_max(pool.read_leaves(), orc2.get_state()).max() <= 1e-12
 
 
+@pytest.mark.parametrize("scheme", ["mmc", "lf", "weno"])
+def test_long_run_that_regrids_as_it_goes_matches_oracle(gpulib, scheme):
+    """A narrow density pulse crosses the periodic strip once (1500 steps at one fixed dt)
+    with a refinement cycle every 4 steps.  FP64: at every cycle the GPU's flags equal the
+    oracle's, both move to the oracle's plan, and after the period the state is within 1e-9
+    of the oracle's with the mass to round-off.  FP32 (its own map_adapt cycles, graph-replayed
+    steps): the error against the exact pulse within 5 % of FP64's, and the mass to 1e-4.  An
+    FP32 update rounds each cell a few times per step at half an ulp of rho (< 2), at most
+    about 2e-7 of the mass per step here, 3e-4 over the run (measured 1.4e-5 to 3.4e-5, each
+    regrid below 4e-9); without the reflux the mass moves by 5e-4 to 1e-3."""
+    from paper_1204_5849_gb300 import MAP_FP32_FIX64, MAP_FP64
+    from tests.test_oracle_pins import _pulse
+    m0 = w.uniform_mesh(2, 8, (8, 1), lo=(-0.5, 0, 0), hi=(0.5, 1.0 / 8, 1))
+    nsteps, every = 1500, 4
+    p = P(gamma=1.4, scheme=scheme, dt_override=1.0 / nsteps)
+    refine = dict(vars=("rho",), thr=0.05, coarsen=0.02, max_level=2)
+
+    def area(mesh):
+        return np.array([np.prod(mesh.leaf_dx(b)[:2]) for b in range(mesh.nleaves)])[:, None, None, None]
+
+    U0 = w.evaluate_on_mesh(m0, _pulse)
+    pool = pool_for(m0, MAP_FP64, U0)
+    orc = Oracle(m0, U0)
+    mesh, changes = m0, 0
+    s0 = pool.conservation()[0, 0]
+    for s in range(nsteps):
+        if s % every == 0:
+            pool.fill_ghosts()
+            orc.fill_ghosts()
+            fo, _ = orc.flags(p, refine)
+            fg, _ = pool.flag_refine(p, refine)
+            np.testing.assert_array_equal(fg, fo)
+            new = w.Mesh(2, mesh.nb, mesh.problems, np.asarray(O.plan_regrid(mesh, fo, 2), dtype=np.int32))
+            if not (new.nleaves == mesh.nleaves and np.array_equal(new.leaves, mesh.leaves)):
+                pool.regrid(new)
+                orc = orc.regrid(new)
+                mesh = new
+                changes += 1
+        pool.fill_ghosts()
+        pool.cfl_dt(p)
+        pool.step(p)
+        orc.fill_ghosts()
+        orc.cfl(p)
+        orc.step(p)
+    assert changes >= 20, changes
+    G, R = pool.read_leaves(), orc.get_state()
+    assert rel_max(G, R).max() <= 1e-9, rel_max(G, R)
+    assert abs(pool.conservation()[0, 0] - s0) <= 1e-13 * s0
+    assert pool.check() == 0
+    e64 = float((np.abs(R[:, 0] - w.evaluate_on_mesh(mesh, _pulse, t=1.0)[:, 0]) * area(mesh)).sum())
+    p32 = pool_for(m0, MAP_FP32_FIX64, U0)
+    for s in range(0, nsteps, every):
+        p32.adapt(p, refine)
+        p32.advance(p, every)
+    m32 = p32.mesh
+    e32 = float((np.abs(p32.read_leaves()[:, 0] - w.evaluate_on_mesh(m32, _pulse, t=1.0)[:, 0]) * area(m32)).sum())
+    assert abs(e32 - e64) <= 0.05 * e64, (e32, e64)
+    assert abs(p32.conservation()[0, 0] - s0) <= 1e-4 * s0
+    assert p32.check() == 0
+
+
 def test_error_word_negative_pressure(gpulib):
     from paper_1204_5849_gb300 import MAP_FP64
     mesh = w.uniform_mesh(2, 16, (2, 2))
