@@ -478,6 +478,23 @@ def main():
                               "achieved_tflops": tflops, "cells": ncells, "gpu_launches": launches}))
         return
 
+    # -------- the interface fluxes on the same workload (Sec. 3.2-3.3, Sec. 5): the step with
+    # HLLC and with HLLD in place of f_m, graph-replayed like the value (untimed by the line's
+    # value; the state moves on, and the end-to-end loop below writes its own) --------------
+    riemann_ms = {"f_m": ms / args.steps}
+    nr = min(args.steps, 20)
+    for rs in ("hllc", "hlld"):
+        pr = dict(params, riemann=rs)
+        for _ in range(2):                          # eager run, then the capture per buffer
+            pool.advance(pr, 1)
+        r0, r1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        r0.record(stream)
+        pool.advance(pr, nr)
+        r1.record(stream)
+        torch.cuda.synchronize()
+        riemann_ms[rs] = r0.elapsed_time(r1) / nr
+    assert pool.check() == 0, "device error word set by the interface-flux runs"
+
     # -------- end to end through the public API: pinned H2D of the inputs, D2H result ----
     # every step copies the host state in (map_write_leaves_async[_f32]: its own copy stream
     # and two staging buffers, so the copy for step k+1 overlaps step k), reads the step's
@@ -659,6 +676,9 @@ def main():
         "error_fp32_without_fix_vs_fp64": {"steps": nacc, **error_table(G32n, G64)},
         "error_fp32_vs_fp64_over_wave_amplitude": {"l1": wave, "linf": wave_inf},
         "error_vs_closed_form": closed,
+        "riemann_solvers": {"unit": "ms_per_step", "steps": nr, **riemann_ms,
+                            "note": "the same FP32 batched step with the interface flux f_m (the value), "
+                                    "HLLC or HLLD"},
     }
     if cpu is not None:
         line["cpu_baseline"] = cpu
