@@ -282,8 +282,9 @@ void orc_hllc_flux(int d, const double* a, const double* b, double gamma, double
  *      E**_L = E*_L - sigma r_L (v*_L.B*_L - v**.B**),  E**_R = E*_R + sigma r_R (v*_R.B*_R - v**.B**).
  * 7. With S*_L = S_M - |B_n|/r_L and S*_R = S_M + |B_n|/r_R the flux is that of the region
  *    holding the interface: F_L, F_L + S_L (U*_L - U_L), that + S*_L (U**_L - U*_L), the
- *    mirror images on the right, or F_R.  With B_n = 0 the inner region has no width and the
- *    solver is HLLC's. */
+ *    mirror images on the right, or F_R.  With B_n = 0 the inner region has no width and three
+ *    waves remain; their star field B_t (S - u)/(S - S_M) follows the density, where
+ *    orc_hllc_flux takes the HLL state's, so the two agree only when B = 0. */
 void orc_hlld_flux(int d, const double* a, const double* b, double gamma, double ch, double* f) {
   double bm;
   if (ch > 0.0) bm = 0.5 * (a[BX + d] + b[BX + d]) - (b[PSI] - a[PSI]) / (2.0 * ch);
