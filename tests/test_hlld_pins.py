@@ -71,6 +71,31 @@ def test_hlld_exact_for_an_isolated_contact(d, u0, bn):
     np.testing.assert_allclose(O.hlld_flux(d, a, b, G53, ch), O.flux(d, up, G53, ch), rtol=1e-13, atol=1e-14)
 
 
+@pytest.mark.parametrize("d", [0, 1, 2])
+def test_hlld_carries_the_tangential_field_with_the_mass_when_bn_is_zero(d):
+    """With no normal field the tangential field is frozen into the fluid: B_t / rho is carried
+    with the mass.  HLLD's outer star states scale B_t with the density, so in every region of
+    its fan the induction flux is (B_t / rho of the side upwind of the contact) times the mass
+    flux, to round-off; the HLLC here (HLL-state field) does not do so."""
+    rng = np.random.default_rng(91 + d)
+    hllc_off = 0.0
+    for trial in range(200):
+        a, b = _rand_state(rng, True, False), _rand_state(rng, True, False)
+        for U in (a, b):
+            U[7] -= 0.5 * U[4 + d] ** 2                    # remove B_d at unchanged pressure
+            U[4 + d] = 0.0
+        f = O.hlld_flux(d, a, b, G53, 1.0)
+        # the side upwind of the contact: the mass flux's direction fixes it where it is nonzero
+        up = a if f[0] > 0 else b
+        t = [j for j in range(3) if j != d]
+        for j in t:
+            np.testing.assert_allclose(f[4 + j], up[4 + j] / up[0] * f[0], rtol=1e-11, atol=1e-13)
+        g = O.hllc_flux(d, a, b, G53, 1.0)
+        hllc_off = max(hllc_off, max(abs(g[4 + j] - (a if g[0] > 0 else b)[4 + j] / (a if g[0] > 0 else b)[0] * g[0])
+                                     for j in t))
+    assert hllc_off > 1e-2
+
+
 def _rotational(d, rho, bn, s, bt, c, p=1.0, gamma=G53):
     """A state on one side of a rotational discontinuity at rest along d: normal velocity
     u = s B_n / sqrt(rho) (the discontinuity moves at u - s B_n / sqrt(rho) = 0), tangential
